@@ -1,0 +1,333 @@
+"""Benchmark: whole IB-LBM time steps on the 2048 x 4096 D2Q9 cavity.
+
+Workload: D2Q9 closed cavity 2048 x 4096, 10681 circles d = 10 (31 points each,
+solid fraction 0.1), 4-point delta, drs = 2.6, 3 MDF iterations, density ratio 1.2,
+gravity 1e-5, FP32 PDFs, FP64 particles; seeded synthetic placement (no dataset).
+A step is one pass of the whole hot path: moments, MDF interpolation/spreading,
+interior momentum, fused collide+stream, pair search + contacts, particle update.
+
+Metric: MLUPS = N_grid * steps / (1e6 * seconds) (Eq. 52), whole job over all ranks.
+Also reported: the roofline of the dominant kernel (lbm_step) against the measured
+HBM copy bandwidth, an end-to-end number through the C ABI with host buffers, and
+the FP64 CPU oracle timed on a bounded sample on the host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+(N > 1: launch with torchrun; each rank runs an independent replica.)
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PHI = 0.1
+WORKLOAD = "cavity2d_2048x4096_phi0.1"
+METRIC = "MLUPS"
+
+
+def _workload():
+    from paper_2002_08855_gb300 import inputs
+    return inputs.cavity_2d_large(PHI)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _flagged_nodes(w, X):
+    """Nodes within R + 2 sqrt(2) of a centre (where the IB force may be non-zero)."""
+    R = 0.5 * w.diameter + 2.0 * math.sqrt(2.0) + 1e-9
+    mask = np.zeros((w.ny, w.nx), dtype=bool)
+    r = int(math.ceil(R)) + 1
+    oy, ox = np.mgrid[-r:r + 1, -r:r + 1]
+    for x, y in X:
+        cx, cy = int(round(x)), int(round(y))
+        gx, gy = cx + ox, cy + oy
+        sel = ((gx - x) ** 2 + (gy - y) ** 2 <= R * R) & (gx >= 0) & (gx < w.nx) & (gy >= 0) & (gy < w.ny)
+        mask[gy[sel], gx[sel]] = True
+    return int(mask.sum())
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("lbm.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2002_08855_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(n_grid):
+    """DRAM bytes per lbm_step launch from the committed ncu summary, scaled to this
+    lattice, or None when the kernel changed since the counters were taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "lbm_step_traffic.json")) as fh:
+            d = json.load(fh)
+        if d.get("kernel_hash") != _kernel_hash():
+            return None
+        return float(d["dram_bytes_per_node"]) * n_grid
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as fh:
+                for line in fh:
+                    p = [s.strip() for s in line.split(",")]
+                    if len(p) >= 9 and p[1].replace(".", "").isdigit():
+                        rows.append(p)
+        except Exception:
+            pass
+        if self.path and os.path.exists(self.path):
+            os.remove(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(seconds_target=15.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: one
+    512 x 1024 sub-cavity at the same solid fraction, timed for whole steps until
+    about seconds_target have passed.  Single threaded."""
+    import oracle
+    from paper_2002_08855_gb300 import inputs
+
+    w = _workload()
+    sw = w.with_(nx=512, ny=1024, n_particles=inputs.n_particles_for_fraction(2, 512 * 1024, w.diameter, PHI),
+                 seed=w.seed + 50)
+    X = inputs.place_particles(sw)
+    sim = oracle.Sim(sw.as_dict(), X)
+    sim.step(1)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        sim.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_target or steps >= 200:
+            break
+    sim.close()
+    return {"value": sw.n_grid * steps / (1e6 * el), "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} whole steps of a 512x1024 sub-cavity, {sw.n_particles} particles "
+                      f"(same solid fraction and particle parameters), FP64, {el:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2002_08855_gb300 import inputs
+
+    w = _workload()
+    sw = w.with_(nx=512, ny=1024, n_particles=inputs.n_particles_for_fraction(2, 512 * 1024, w.diameter, PHI),
+                 seed=w.seed + 50)
+    X = inputs.place_particles(sw)
+    sim = oracle.Sim(sw.as_dict(), X)
+    for _ in range(args.warmup):
+        sim.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.step(1)
+    el = time.perf_counter() - t0
+    v = sw.n_grid * args.steps / (1e6 * el)
+    sample = f"{args.steps} whole FP64 oracle steps of a 512x1024 sub-cavity at the workload's density"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "512x1024 sub-cavity"},
+        "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run(args):
+    import torch
+
+    from paper_2002_08855_gb300 import binding, build
+
+    world, rank, local = _dist()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = _workload()
+    X = None
+    from paper_2002_08855_gb300 import inputs
+    X = inputs.place_particles(w)
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline()
+
+    sim = binding.Simulation(w, X, device=str(dev))
+    stream = sim.stream
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # warm-up (the first step is eager; graphs are captured on the next two)
+    sim.step(args.warmup)
+    sim.sync()
+
+    # timed region: K whole steps, device time with events on the run's stream
+    launches0 = sim.launch_count()
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        sim.step(args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        sim.sync()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = sim.launch_count() - launches0
+    clocks = clk.summary()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    mlups = world * w.n_grid * args.steps / (1e3 * ms_max)
+
+    # per-part device times (eager launches, CUDA events on the same stream)
+    parts = sim.time_parts(max(3, min(args.steps, 50)))
+    nparts = max(3, min(args.steps, 50))
+    t_lbm = parts["collide_stream"] / nparts * 1e-3
+    nflag = _flagged_nodes(w, sim.get_particles()["X"])
+    bytes_lbm = 72.0 * w.n_grid + 16.0 * nflag  # PDFs read + written; f_IB read + cleared
+    peak, peak_kind = _peaks()
+    achieved = bytes_lbm / t_lbm / 1e9
+    traffic = _traffic(w.n_grid)
+
+    # end to end through the C ABI with host buffers: init from host centres, then per
+    # step one ibm_lbm_step and a read of the particle state into pinned host memory
+    sim.close()
+    del sim
+    torch.cuda.synchronize(dev)
+    pin_x = torch.empty((w.n_particles, 2), dtype=torch.float64, pin_memory=True).numpy()
+    pin_u = torch.empty((w.n_particles, 2), dtype=torch.float64, pin_memory=True).numpy()
+    centres = torch.from_numpy(np.ascontiguousarray(X)).pin_memory().numpy()
+    e2e_steps = max(args.steps // 2, 3)
+    barrier()
+    t0 = time.perf_counter()
+    sim2 = binding.Simulation(w, centres, device=str(dev))
+    for _ in range(e2e_steps):
+        sim2.step(1)
+        import ctypes as C
+        binding._check(binding.lib().ibm_lbm_get_particles(
+            sim2.h, binding._ptr(pin_x, C.c_double), binding._ptr(pin_u, C.c_double), None, None,
+            None, None), "get_particles")
+    sim2.sync()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    sim2.close()
+    e2e = world * w.n_grid * e2e_steps / (1e6 * e2e_s)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": mlups, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": "D2Q9 2048x4096", "particles": w.n_particles,
+                       "points_per_particle": w.n_lag, "mdf_iters": w.mdf_iters,
+                       "pdf_storage": "fp32", "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (302 MB of PDFs per step)"},
+            "roofline": {"bound": "hbm", "kernel": "lbm_step", "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "algorithmic_bytes": bytes_lbm,
+                         "flagged_nodes": nflag, "ms_per_launch": t_lbm * 1e3},
+            "parts_ms_per_step": {k: v / nparts for k, v in parts.items()},
+            "clocks": clocks, "gpu_launches": launches,
+            "e2e": {"value": e2e, "unit": METRIC, "h2d_bytes_per_step": int(X.nbytes / e2e_steps),
+                    "d2h_bytes_per_step": int(pin_x.nbytes + pin_u.nbytes)},
+            "cpu_baseline": base,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * ibmlbm.h - C ABI of the GB300 IB-LBM hot path (libibmlbm.so).
+ *
+ * One time step of the immersed boundary - lattice Boltzmann method for
+ * particle-laden flow of Jiang, Li & Liu ("Efficient implementation of immersed
+ * boundary-lattice Boltzmann method for massive particle-laden flows, Part I"):
+ *   1. macroscopic velocity u* = sum_a e_a f_a on the nodes near particles (Eq. 5)
+ *   2. multi-direct forcing: interpolation u_b = D_I u (Eq. 9, 12, 47), boundary
+ *      force dF_b = 2 rho_f (U_b - u_b)/dt (Eq. 10), spreading f = D_E dF_b
+ *      (Eq. 11, 13, 48), repeated M times
+ *   3. fused SRT-LBGK collision with Guo split forcing and in-place streaming with
+ *      halfway bounce-back at walls (Eq. 1, 4, 6-8, 17-18)
+ *   4. cell-list pair search and the short-range repulsive force (Eq. 16, Sec. 5)
+ *   5. Newton-Euler update of the particles (Eq. 14-15) in double precision.
+ * Lattices: D2Q9 (Eq. 2) and D3Q19 (Eq. 3, with e_9 = (-1, 0, 1), the entry the
+ * printed matrix drops).  Units are lattice units: dh = dt = 1, cs^2 = 1/3,
+ * rho_0 = rho_f = 1.
+ *
+ * Conventions for every call
+ *   - Every call returns an int status: IBMLBM_OK (0) or a negative IBMLBM_ERR_*.
+ *     No call aborts, traps or exits; ibm_lbm_last_error() describes the last
+ *     failure of the calling thread.
+ *   - Node (x, y, z), 0 <= x < nx etc., has index n = x + nx*(y + ny*z); N = nx*ny*nz
+ *     (nz = 1 in 2D).  Node x sits at coordinate x; walls of a non-periodic axis
+ *     lie halfway, at -1/2 and n-1/2.
+ *   - PDFs are [q][N] float; vector fields [dim][N]; per-particle vectors are
+ *     [n_particles][dim]; angular quantities [n_particles][1] in 2D (the z
+ *     component) and [n_particles][3] in 3D; per-point vectors [n_particles*n_lag][dim]
+ *     with the points of particle i at rows i*n_lag .. i*n_lag + n_lag - 1.
+ *   - Host pointers are plain CPU memory; "device" pointers are CUDA global memory
+ *     on the current device.  The library never frees memory it did not allocate.
+ *   - A stream argument is a cudaStream_t passed as void*; 0 is the legacy stream.
+ */
+#ifndef IBMLBM_H
+#define IBMLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IBMLBM_OK 0
+#define IBMLBM_ERR_INVALID_ARG (-1)   /* bad pointer, size or configuration value */
+#define IBMLBM_ERR_UNSUPPORTED (-2)   /* valid request outside what this build does */
+#define IBMLBM_ERR_WORKSPACE (-3)     /* workspace missing, misaligned or too small */
+#define IBMLBM_ERR_CUDA (-4)          /* a CUDA runtime call failed */
+#define IBMLBM_ERR_NONFINITE (-5)     /* NaN/Inf in a particle state (device check) */
+#define IBMLBM_ERR_OUT_OF_DOMAIN (-6) /* a particle centre left the fluid domain */
+#define IBMLBM_ERR_CAPACITY (-7)      /* a fixed-capacity list overflowed */
+
+/* Problem statement of one run (Sec. 2, Sec. 6.2 and Table 7 of the paper). */
+typedef struct ibm_lbm_config {
+  uint32_t struct_size;   /* must equal sizeof(ibm_lbm_config)                           */
+  int32_t dim;            /* 2: D2Q9, 3: D3Q19                                           */
+  int32_t nx, ny, nz;     /* fluid nodes per axis (nz = 1 when dim = 2)                  */
+  int32_t periodic[3];    /* per axis: 1 periodic, 0 halfway bounce-back walls           */
+  double tau;             /* relaxation time of Eq. 1, tau > 1/2                         */
+  double body_force[3];   /* uniform fluid body force, added to the IB force (Eq. 7-8)  */
+  int32_t n_particles;    /* N_p, rigid circles (2D) or spheres (3D), >= 0               */
+  int32_t n_lag;          /* N_L Lagrangian points per particle (Sec. 2.2)               */
+  double diameter;        /* D_p                                                         */
+  int32_t delta_kind;     /* regularised delta function of Fig. 2b: 4 (4-point)          */
+  double drs;             /* solid-shell thickness of Eq. 13 (2.6 for the 4-point delta) */
+  int32_t mdf_iters;      /* M >= 0 multi-direct-forcing iterations; 1 is BTDF (Eq. 9-11)*/
+  double density_ratio;   /* rho_p / rho_f                                               */
+  double gravity[3];      /* g acting on the particles (Eq. 14, weight less buoyancy)    */
+  double zeta;            /* range of the repulsive force of Eq. 16                      */
+  double eps_pp, E_pp;    /* stiffness parameters of Eq. 16 (E_pp < eps_pp)              */
+  int32_t fixed_particles;/* 1: particles keep centre and velocity (static bodies)       */
+  int32_t max_neighbors;  /* capacity of each particle's contact list; 0 selects 32      */
+} ibm_lbm_config;
+
+typedef struct ibm_lbm_handle ibm_lbm_handle;
+
+/* Device bytes the run needs for the configuration.  The caller allocates them
+ * (any CUDA allocator, 256-byte aligned) and passes them to ibm_lbm_init.
+ * Errors: IBMLBM_ERR_INVALID_ARG for a configuration ibm_lbm_init would reject. */
+int ibm_lbm_workspace_size(const ibm_lbm_config* cfg, size_t* bytes);
+
+/* Create a run.  d_workspace: device memory of at least ibm_lbm_workspace_size
+ * bytes, borrowed (not owned) until ibm_lbm_destroy.  stream: every kernel and
+ * copy of the run is ordered on it.  h_centres: host [n_particles][dim] particle
+ * centres (may be NULL when n_particles = 0).  The fluid starts at rest with
+ * p = 0 (every PDF zero, the deviation gauge of the incompressible model) and the
+ * particles with U = Omega = 0.  Copies the centres to the device and waits for
+ * the stream.  Errors: INVALID_ARG (configuration, pointers, a centre outside
+ * the domain), WORKSPACE, UNSUPPORTED (delta_kind other than 4), CUDA. */
+int ibm_lbm_init(const ibm_lbm_config* cfg, void* d_workspace, size_t bytes, void* stream,
+                 const double* h_centres, ibm_lbm_handle** out);
+
+/* Enqueue n_steps time steps on the run's stream and return without waiting.
+ * Steps after the first replay a captured CUDA graph.  Device-side failures
+ * (NONFINITE, OUT_OF_DOMAIN, CAPACITY) are recorded in a status word that
+ * ibm_lbm_sync reports.  Errors: INVALID_ARG (n_steps < 0), CUDA. */
+int ibm_lbm_step(ibm_lbm_handle* h, int32_t n_steps);
+
+/* Wait for the stream and report the device status word (first failure wins),
+ * then clear it. */
+int ibm_lbm_sync(ibm_lbm_handle* h);
+
+/* Replace the PDFs with d_f: device [q][N] floats in canonical layout
+ * (d_f[a*N + n] = f_a at node n, pre-collision at the current time).  Ordered on
+ * the run's stream; returns after enqueueing. */
+int ibm_lbm_set_pdfs(ibm_lbm_handle* h, const float* d_f);
+
+/* Copy the current PDFs into device [q][N] floats d_f, canonical layout. */
+int ibm_lbm_get_pdfs(ibm_lbm_handle* h, float* d_f);
+
+/* Set every node to the equilibrium of Eq. 4 for pressure d_p [N] and velocity
+ * d_u [dim][N] (device doubles). */
+int ibm_lbm_set_fields(ibm_lbm_handle* h, const double* d_p, const double* d_u);
+
+/* Pressure (Eq. 6 with u = u*) and velocity u* (Eq. 5) of the current PDFs, without
+ * a force correction, into device doubles d_p [N] and d_u [dim][N]; either may be NULL. */
+int ibm_lbm_get_fields(ibm_lbm_handle* h, double* d_p, double* d_u);
+
+/* Set particle centres X [n][dim], velocities U [n][dim] and angular velocities
+ * Omega (2D [n][1], 3D [n][3]); NULL leaves a quantity unchanged.  Host doubles.
+ * Regenerates the Lagrangian points; synchronous. */
+int ibm_lbm_set_particles(ibm_lbm_handle* h, const double* X, const double* U,
+                          const double* Omega);
+
+/* Particle state after the last step (host doubles, any pointer may be NULL;
+ * synchronous):
+ * X, U, Omega as above; F_h = -sum_b F_b dV and T_h = -sum_b r_b x F_b dV of the
+ * last step (Eq. 14-15); F_c the contact force of Eq. 16 (walls included). */
+int ibm_lbm_get_particles(ibm_lbm_handle* h, double* X, double* U, double* Omega,
+                          double* F_h, double* T_h, double* F_c);
+
+/* Lagrangian data of the last step (host, any pointer may be NULL): X_b (double),
+ * U_b, F_b = sum over MDF iterations of dF_b, and u_b* = D_I u* (floats). */
+int ibm_lbm_get_lagrangian(ibm_lbm_handle* h, double* X_b, float* U_b, float* F_b,
+                           float* u_b_star);
+
+/* Momentum [n][dim] and angular momentum (2D [n][1], 3D [n][3]) of the fluid at the
+ * nodes strictly inside each particle, from the last step (host doubles). */
+int ibm_lbm_get_interior_momentum(ibm_lbm_handle* h, double* P, double* L);
+
+/* Contact pairs of the last step: (i, j) with i < j and
+ * |X_i - X_j|^2 < (D_p + zeta)^2 (squared distance summed in axis order in double
+ * precision without fused multiply-add; nearest image on periodic axes), sorted by
+ * (i, j), written as pairs[2k], pairs[2k+1] (host int32).  *n receives the count;
+ * IBMLBM_ERR_CAPACITY if it exceeds cap (nothing is written then). */
+int ibm_lbm_get_pairs(ibm_lbm_handle* h, int32_t* pairs, int64_t cap, int64_t* n);
+
+/* Kernels this run has launched so far (eager launches plus graph kernel nodes). */
+int ibm_lbm_get_launch_count(ibm_lbm_handle* h, int64_t* n);
+
+/* Time n_steps steps part by part with CUDA events on the run's stream (eager
+ * launches, no graph) and return the total milliseconds of each part in
+ * ms[IBMLBM_PART_COUNT], in the order of enum ibm_lbm_part; the parts follow the
+ * per-part timing of Sec. 6.2 (Fig. 10, Fig. 16). */
+enum ibm_lbm_part {
+  IBMLBM_PART_MACRO = 0,      /* lbm_moments on the flagged nodes                */
+  IBMLBM_PART_IBM = 1,        /* interpolation, spreading, interior momentum     */
+  IBMLBM_PART_COLLIDE = 2,    /* fused collision + streaming + bounce-back       */
+  IBMLBM_PART_PAIRS = 3,      /* cell lists, pair search and contact force       */
+  IBMLBM_PART_PARTICLES = 4,  /* Newton-Euler update, point regeneration, marks  */
+  IBMLBM_PART_COUNT = 5
+};
+int ibm_lbm_time_parts(ibm_lbm_handle* h, int32_t n_steps, double* ms);
+
+/* Release the handle's host state.  The workspace stays owned by the caller.
+ * Never fails; NULL is ignored. */
+void ibm_lbm_destroy(ibm_lbm_handle* h);
+
+/* Text of the calling thread's last failure ("" if none).  Valid until the next
+ * call on the same thread. */
+const char* ibm_lbm_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Standalone pair search (Sec. 5): device cell lists built by a counting sort on
+ * the cell key, then a scan of the 3^dim neighbouring cells of each particle.
+ *   dim, n_nodes[3], periodic[3]: the domain as in ibm_lbm_config
+ *   diameter, zeta: pair rule |X_i - X_j|^2 < (diameter + zeta)^2
+ *   d_X: device [n][dim] double centres (inside the domain)
+ *   max_neighbors: per-particle list capacity (0 selects 32)
+ *   d_scratch / scratch_bytes: device scratch of ibm_lbm_pair_search_scratch_size bytes
+ *   d_pairs: device int32 [cap][2] output, sorted by (i, j)
+ *   h_count: host; receives the number of pairs (also when it exceeds cap, in which
+ *            case IBMLBM_ERR_CAPACITY is returned and only the first cap are valid)
+ * Synchronises the stream before returning.  IBMLBM_ERR_CAPACITY also reports a
+ * particle with more than max_neighbors partners. */
+int ibm_lbm_pair_search_scratch_size(int32_t dim, const int32_t* n_nodes, double diameter,
+                                     double zeta, int32_t n, int32_t max_neighbors,
+                                     size_t* bytes);
+int ibm_lbm_pair_search(int32_t dim, const int32_t* n_nodes, const int32_t* periodic,
+                        double diameter, double zeta, int32_t n, const double* d_X,
+                        int32_t max_neighbors, void* d_scratch, size_t scratch_bytes,
+                        int32_t* d_pairs, int64_t cap, int64_t* h_count, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBMLBM_H */

@@ -1,0 +1,314 @@
+"""ctypes binding of ``libibmlbm.so`` (C ABI in ``include/ibmlbm.h``).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  PyTorch provides the device memory (the workspace and device-side
+field buffers) and the CUDA stream the run is ordered on.  There is no CPU path:
+if the library is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libibmlbm.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "ibmlbm.h")
+
+OK = 0
+ERRORS = {
+    -1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "WORKSPACE", -4: "CUDA", -5: "NONFINITE",
+    -6: "OUT_OF_DOMAIN", -7: "CAPACITY",
+}
+PARTS = ("macro", "ibm", "collide_stream", "pairs", "particles")
+
+
+class IbmLbmError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {ERRORS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+class Config(C.Structure):
+    """Mirror of ``ibm_lbm_config``."""
+
+    _fields_ = [
+        ("struct_size", C.c_uint32), ("dim", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32),
+        ("nz", C.c_int32), ("periodic", C.c_int32 * 3), ("tau", C.c_double),
+        ("body_force", C.c_double * 3), ("n_particles", C.c_int32), ("n_lag", C.c_int32),
+        ("diameter", C.c_double), ("delta_kind", C.c_int32), ("drs", C.c_double),
+        ("mdf_iters", C.c_int32), ("density_ratio", C.c_double), ("gravity", C.c_double * 3),
+        ("zeta", C.c_double), ("eps_pp", C.c_double), ("E_pp", C.c_double),
+        ("fixed_particles", C.c_int32), ("max_neighbors", C.c_int32),
+    ]
+
+
+def make_config(w, max_neighbors: int = 0) -> Config:
+    """``ibm_lbm_config`` from a workload (``inputs.Workload`` or a dict of its fields)."""
+    get = w.get if isinstance(w, dict) else (lambda k, d=None: getattr(w, k, d))
+    c = Config()
+    c.struct_size = C.sizeof(Config)
+    c.dim = int(get("dim", 2))
+    c.nx, c.ny = int(get("nx")), int(get("ny"))
+    c.nz = int(get("nz", 1)) if c.dim == 3 else 1
+    for k, v in enumerate((list(get("periodic", (0, 0, 0))) + [0, 0, 0])[:3]):
+        c.periodic[k] = int(v)
+    c.tau = float(get("tau", 0.6))
+    for k, v in enumerate((list(get("body_force", (0, 0, 0))) + [0, 0, 0])[:3]):
+        c.body_force[k] = float(v)
+    c.n_particles = int(get("n_particles", 0))
+    c.n_lag = int(get("n_lag", 0))
+    c.diameter = float(get("diameter", 0.0))
+    c.delta_kind = int(get("delta_kind", 4))
+    c.drs = float(get("drs", 2.6))
+    c.mdf_iters = int(get("mdf_iters", 3))
+    c.density_ratio = float(get("density_ratio", 1.5))
+    for k, v in enumerate((list(get("gravity", (0, 0, 0))) + [0, 0, 0])[:3]):
+        c.gravity[k] = float(v)
+    c.zeta = float(get("zeta", 2.0))
+    c.eps_pp = float(get("eps_pp", 1e-2))
+    c.E_pp = float(get("E_pp", 1e-4))
+    c.fixed_particles = int(get("fixed_particles", 0))
+    c.max_neighbors = int(max_neighbors)
+    return c
+
+
+_lock = threading.Lock()
+_lib = None
+_vp, _dp, _fp, _ip, _i64p = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_float), \
+    C.POINTER(C.c_int32), C.POINTER(C.c_int64)
+SIGNATURES = {
+    "ibm_lbm_workspace_size": (C.c_int, [C.POINTER(Config), C.POINTER(C.c_size_t)]),
+    "ibm_lbm_init": (C.c_int, [C.POINTER(Config), _vp, C.c_size_t, _vp, _dp, C.POINTER(_vp)]),
+    "ibm_lbm_step": (C.c_int, [_vp, C.c_int32]),
+    "ibm_lbm_sync": (C.c_int, [_vp]),
+    "ibm_lbm_set_pdfs": (C.c_int, [_vp, _vp]),
+    "ibm_lbm_get_pdfs": (C.c_int, [_vp, _vp]),
+    "ibm_lbm_set_fields": (C.c_int, [_vp, _vp, _vp]),
+    "ibm_lbm_get_fields": (C.c_int, [_vp, _vp, _vp]),
+    "ibm_lbm_set_particles": (C.c_int, [_vp, _dp, _dp, _dp]),
+    "ibm_lbm_get_particles": (C.c_int, [_vp, _dp, _dp, _dp, _dp, _dp, _dp]),
+    "ibm_lbm_get_lagrangian": (C.c_int, [_vp, _dp, _fp, _fp, _fp]),
+    "ibm_lbm_get_interior_momentum": (C.c_int, [_vp, _dp, _dp]),
+    "ibm_lbm_get_pairs": (C.c_int, [_vp, _ip, C.c_int64, _i64p]),
+    "ibm_lbm_get_launch_count": (C.c_int, [_vp, _i64p]),
+    "ibm_lbm_time_parts": (C.c_int, [_vp, C.c_int32, _dp]),
+    "ibm_lbm_destroy": (None, [_vp]),
+    "ibm_lbm_last_error": (C.c_char_p, []),
+    "ibm_lbm_pair_search_scratch_size": (C.c_int, [C.c_int32, _ip, C.c_double, C.c_double,
+                                                   C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
+    "ibm_lbm_pair_search": (C.c_int, [C.c_int32, _ip, _ip, C.c_double, C.c_double, C.c_int32,
+                                      _vp, C.c_int32, _vp, C.c_size_t, _vp, C.c_int64, _i64p,
+                                      _vp]),
+}
+
+
+def lib():
+    """Load the CUDA library; raise if it has not been built (there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "paper_2002_08855_gb300.build.build() (there is no CPU path)")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise IbmLbmError(rc, where, lib().ibm_lbm_last_error().decode())
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def workspace_size(w, max_neighbors: int = 0) -> int:
+    cfg = make_config(w, max_neighbors)
+    n = C.c_size_t(0)
+    _check(lib().ibm_lbm_workspace_size(C.byref(cfg), C.byref(n)), "workspace_size")
+    return n.value
+
+
+class Simulation:
+    """One run on one GPU: fluid cavity plus rigid particles (C ABI handle)."""
+
+    def __init__(self, w, centres=None, device: str = "cuda", stream=None,
+                 max_neighbors: int = 0):
+        import torch
+
+        self.torch = torch
+        self.cfg = make_config(w, max_neighbors)
+        self.dim = self.cfg.dim
+        self.q = 9 if self.dim == 2 else 19
+        self.N = self.cfg.nx * self.cfg.ny * self.cfg.nz
+        self.np = self.cfg.n_particles
+        self.nl = self.cfg.n_lag
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        nbytes = workspace_size(w, max_neighbors)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        self.h = C.c_void_p(None)
+        xc = None
+        if self.np > 0:
+            if centres is None:
+                raise ValueError("particle centres are required")
+            xc = np.ascontiguousarray(np.asarray(centres, dtype=np.float64).reshape(self.np, self.dim))
+        _check(lib().ibm_lbm_init(C.byref(self.cfg), C.c_void_p(self.workspace.data_ptr()),
+                                  nbytes, C.c_void_p(self.stream.cuda_stream),
+                                  _ptr(xc, C.c_double) if xc is not None else None,
+                                  C.byref(self.h)), "init")
+
+    # ------------------------------------------------------------ stepping
+    def step(self, n: int = 1):
+        _check(lib().ibm_lbm_step(self.h, int(n)), "step")
+
+    def sync(self):
+        _check(lib().ibm_lbm_sync(self.h), "sync")
+
+    def time_parts(self, n: int) -> dict:
+        ms = np.zeros(5)
+        _check(lib().ibm_lbm_time_parts(self.h, int(n), _ptr(ms, C.c_double)), "time_parts")
+        return dict(zip(PARTS, ms.tolist()))
+
+    def launch_count(self) -> int:
+        v = C.c_int64(0)
+        _check(lib().ibm_lbm_get_launch_count(self.h, C.byref(v)), "launch_count")
+        return v.value
+
+    # ------------------------------------------------------------ fields
+    def _wait_torch(self):
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+
+    def set_pdfs(self, f):
+        t = self.torch.as_tensor(f, dtype=self.torch.float32, device=self.device).reshape(self.q, self.N).contiguous()
+        self._wait_torch()
+        _check(lib().ibm_lbm_set_pdfs(self.h, C.c_void_p(t.data_ptr())), "set_pdfs")
+        self.stream.synchronize()
+
+    def get_pdfs(self):
+        t = self.torch.empty((self.q, self.N), dtype=self.torch.float32, device=self.device)
+        self._wait_torch()
+        _check(lib().ibm_lbm_get_pdfs(self.h, C.c_void_p(t.data_ptr())), "get_pdfs")
+        self.stream.synchronize()
+        return t
+
+    def set_fields(self, p, u):
+        tp = self.torch.as_tensor(p, dtype=self.torch.float64, device=self.device).reshape(self.N).contiguous()
+        tu = self.torch.as_tensor(u, dtype=self.torch.float64, device=self.device).reshape(self.dim, self.N).contiguous()
+        self._wait_torch()
+        _check(lib().ibm_lbm_set_fields(self.h, C.c_void_p(tp.data_ptr()), C.c_void_p(tu.data_ptr())), "set_fields")
+        self.stream.synchronize()
+
+    def get_fields(self):
+        tp = self.torch.empty(self.N, dtype=self.torch.float64, device=self.device)
+        tu = self.torch.empty((self.dim, self.N), dtype=self.torch.float64, device=self.device)
+        self._wait_torch()
+        _check(lib().ibm_lbm_get_fields(self.h, C.c_void_p(tp.data_ptr()), C.c_void_p(tu.data_ptr())), "get_fields")
+        self.stream.synchronize()
+        return tp, tu
+
+    # ------------------------------------------------------------ particles
+    def _rot(self):
+        return 1 if self.dim == 2 else 3
+
+    def set_particles(self, X=None, U=None, Omega=None):
+        def arr(a, cols):
+            if a is None:
+                return None
+            return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(self.np, cols))
+        X, U, Om = arr(X, self.dim), arr(U, self.dim), arr(Omega, self._rot())
+        _check(lib().ibm_lbm_set_particles(
+            self.h, *[(_ptr(a, C.c_double) if a is not None else None) for a in (X, U, Om)]),
+            "set_particles")
+
+    def get_particles(self) -> dict:
+        n, d, r = max(self.np, 1), self.dim, self._rot()
+        out = dict(X=np.zeros((n, d)), U=np.zeros((n, d)), Omega=np.zeros((n, r)),
+                   F_h=np.zeros((n, d)), T_h=np.zeros((n, r)), F_c=np.zeros((n, d)))
+        _check(lib().ibm_lbm_get_particles(self.h, *[_ptr(out[k], C.c_double) for k in
+                                                      ("X", "U", "Omega", "F_h", "T_h", "F_c")]),
+               "get_particles")
+        return {k: v[: self.np] for k, v in out.items()}
+
+    def get_lagrangian(self) -> dict:
+        m, d = max(self.np * self.nl, 1), self.dim
+        Xb = np.zeros((m, d))
+        Ub, Fb, us = (np.zeros((m, d), dtype=np.float32) for _ in range(3))
+        _check(lib().ibm_lbm_get_lagrangian(self.h, _ptr(Xb, C.c_double), _ptr(Ub, C.c_float),
+                                            _ptr(Fb, C.c_float), _ptr(us, C.c_float)),
+               "get_lagrangian")
+        k = self.np * self.nl
+        return dict(X_b=Xb[:k], U_b=Ub[:k], F_b=Fb[:k], u_b_star=us[:k])
+
+    def get_interior_momentum(self):
+        n = max(self.np, 1)
+        P, L = np.zeros((n, self.dim)), np.zeros((n, self._rot()))
+        _check(lib().ibm_lbm_get_interior_momentum(self.h, _ptr(P, C.c_double), _ptr(L, C.c_double)),
+               "get_interior_momentum")
+        return P[: self.np], L[: self.np]
+
+    def get_pairs(self) -> np.ndarray:
+        n = C.c_int64(0)
+        cap = max(16, self.np * 8)
+        while True:
+            buf = np.zeros(2 * cap, dtype=np.int32)
+            rc = lib().ibm_lbm_get_pairs(self.h, _ptr(buf, C.c_int32), cap, C.byref(n))
+            if rc == -7 and n.value > cap:
+                cap = int(n.value)
+                continue
+            _check(rc, "get_pairs")
+            return buf[: 2 * n.value].reshape(-1, 2)
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.stream.synchronize()
+            lib().ibm_lbm_destroy(self.h)
+            self.h = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pair_search(dim: int, n_nodes, periodic, diameter: float, zeta: float, X,
+                max_neighbors: int = 0, stream=None) -> np.ndarray:
+    """Standalone cell-list pair search on the GPU; returns the sorted (i, j) list."""
+    import torch
+
+    X = torch.as_tensor(np.asarray(X, dtype=np.float64), device="cuda").reshape(-1, dim).contiguous()
+    n = X.shape[0]
+    nn = np.ascontiguousarray((list(n_nodes) + [1, 1, 1])[:3], dtype=np.int32)
+    per = np.ascontiguousarray((list(periodic) + [0, 0, 0])[:3], dtype=np.int32)
+    sz = C.c_size_t(0)
+    _check(lib().ibm_lbm_pair_search_scratch_size(dim, _ptr(nn, C.c_int32), diameter, zeta, n,
+                                                  max_neighbors, C.byref(sz)), "pair_search_scratch_size")
+    scratch = torch.empty(max(sz.value, 1), dtype=torch.uint8, device="cuda")
+    s = stream if stream is not None else torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    cap = max(16, n * 8)
+    while True:
+        pairs = torch.empty((cap, 2), dtype=torch.int32, device="cuda")
+        cnt = C.c_int64(0)
+        rc = lib().ibm_lbm_pair_search(dim, _ptr(nn, C.c_int32), _ptr(per, C.c_int32), diameter,
+                                       zeta, n, C.c_void_p(X.data_ptr()), max_neighbors,
+                                       C.c_void_p(scratch.data_ptr()), sz.value,
+                                       C.c_void_p(pairs.data_ptr()), cap, C.byref(cnt),
+                                       C.c_void_p(s.cuda_stream))
+        if rc == -7 and cnt.value > cap:
+            cap = int(cnt.value)
+            continue
+        _check(rc, "pair_search")
+        return pairs[: cnt.value].cpu().numpy()

@@ -1,0 +1,864 @@
+// C ABI of libibmlbm.so (declared in include/ibmlbm.h): configuration checks,
+// workspace layout, the per-step kernel sequence and its CUDA-graph replay.
+//
+// One step (Sec. 3 step list, Sec. 6.2 part list; explicit particle coupling):
+//   lbm_moments -> [ibm_interp -> ibm_spread] x M -> interior_momentum -> lbm_step
+//   -> pair cells (count, scan, fill) -> pair contacts -> particle_update
+// All of it is enqueued on the caller's stream; after the first step each step
+// parity is captured once as a CUDA graph and replayed.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ibmlbm.h"
+#include "common.cuh"
+#include "launch.h"
+
+using namespace ibmlbm;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                \
+  do {                                                                                \
+    cudaError_t e_ = (expr);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(IBMLBM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Carver {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + (bytes ? bytes : 1));
+    return o;
+  }
+};
+
+struct Derived {
+  int D, Q;
+  Geo g;
+  long long npts;
+  int kmax;
+  int nc[3];
+  double H[3], L[3];
+  int box;
+  double radius, mark_radius, dV, Mp, meff, Ip, Kt, Kr, c_ij, thr2;
+};
+
+struct Layout {
+  size_t f, ustar, fib, mask;
+  size_t X, U, Om, Fh, Th, Fhp, Thp, acc, alp, Pint, Lint, Pprev, Lprev, Fc;
+  size_t ref, Xb0, Xb1, Ub0, Ub1, Fb, dFb, ubs;
+  size_t cell_count, cell_start, sorted, nbr, nbr_count, gt, pairs, status;
+  size_t total;
+};
+
+int check_config(const ibm_lbm_config* c) {
+  if (!c) return fail(IBMLBM_ERR_INVALID_ARG, "config is NULL");
+  if (c->struct_size != sizeof(ibm_lbm_config))
+    return fail(IBMLBM_ERR_INVALID_ARG, "config.struct_size does not match this library");
+  if (c->dim != 2 && c->dim != 3) return fail(IBMLBM_ERR_INVALID_ARG, "dim must be 2 or 3");
+  if (c->nx < 1 || c->ny < 1 || c->nz < 1 || (c->dim == 2 && c->nz != 1))
+    return fail(IBMLBM_ERR_INVALID_ARG, "node counts must be >= 1 (nz = 1 in 2D)");
+  if ((double)c->nx * c->ny * c->nz > 4.0e9)
+    return fail(IBMLBM_ERR_INVALID_ARG, "lattice larger than 4e9 nodes");
+  if (!(c->tau > 0.5) || !std::isfinite(c->tau))
+    return fail(IBMLBM_ERR_INVALID_ARG, "tau must be > 1/2");
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(c->body_force[k]) || !std::isfinite(c->gravity[k]))
+      return fail(IBMLBM_ERR_INVALID_ARG, "body force and gravity must be finite");
+  if (c->n_particles < 0) return fail(IBMLBM_ERR_INVALID_ARG, "n_particles < 0");
+  if (c->max_neighbors < 0 || c->max_neighbors > 64)
+    return fail(IBMLBM_ERR_INVALID_ARG, "max_neighbors must be in 0..64");
+  if (c->n_particles > 0) {
+    if (c->n_lag < 1) return fail(IBMLBM_ERR_INVALID_ARG, "n_lag must be >= 1");
+    if (!(c->diameter > 0.0)) return fail(IBMLBM_ERR_INVALID_ARG, "diameter must be > 0");
+    if (c->delta_kind != 4)
+      return fail(IBMLBM_ERR_UNSUPPORTED, "only the 4-point delta function is built");
+    if (!(c->drs > 0.0)) return fail(IBMLBM_ERR_INVALID_ARG, "drs must be > 0");
+    if (c->mdf_iters < 0) return fail(IBMLBM_ERR_INVALID_ARG, "mdf_iters must be >= 0");
+    if (!(c->density_ratio > 0.0))
+      return fail(IBMLBM_ERR_INVALID_ARG, "density_ratio must be > 0");
+    if (!(c->zeta > 0.0) || !(c->eps_pp > 0.0) || !(c->E_pp > 0.0))
+      return fail(IBMLBM_ERR_INVALID_ARG, "zeta, eps_pp and E_pp must be > 0");
+  }
+  return IBMLBM_OK;
+}
+
+void cell_grid(int D, const double* L, const int* per, double reach, int* nc, double* H) {
+  for (int k = 0; k < 3; ++k) {
+    nc[k] = 1;
+    H[k] = k < D ? L[k] : 1.0;
+    if (k >= D) continue;
+    int c = (int)std::floor(L[k] / reach);
+    if (c < 1) c = 1;
+    if (per[k] && c < 3) c = 1;
+    nc[k] = c;
+    H[k] = L[k] / c;
+  }
+}
+
+Derived derive(const ibm_lbm_config* c) {
+  Derived d{};
+  d.D = c->dim;
+  d.Q = c->dim == 2 ? 9 : 19;
+  d.g.nx = c->nx;
+  d.g.ny = c->ny;
+  d.g.nz = c->dim == 2 ? 1 : c->nz;
+  for (int k = 0; k < 3; ++k) d.g.per[k] = c->periodic[k] ? 1 : 0;
+  if (c->dim == 2) d.g.per[2] = 0;
+  d.g.rows = d.g.ny * d.g.nz;
+  d.g.wpr = (d.g.nx + 31) / 32;
+  d.g.N = (long long)d.g.nx * d.g.ny * d.g.nz;
+  d.npts = (long long)c->n_particles * c->n_lag;
+  d.kmax = c->max_neighbors ? c->max_neighbors : 32;
+  d.L[0] = c->nx;
+  d.L[1] = c->ny;
+  d.L[2] = d.g.nz;
+  const double Dp = c->diameter;
+  d.radius = 0.5 * Dp;
+  d.mark_radius = d.radius + 2.0 * std::sqrt((double)d.D) + 1e-9;
+  d.box = (int)std::ceil(Dp) + 6;
+  cell_grid(d.D, d.L, d.g.per, Dp + c->zeta, d.nc, d.H);
+  // Eq. 13 point volume: 2D ds * drs with ds = pi D / N_L; 3D (pi D^2 / N_L) * drs
+  if (c->n_lag > 0)
+    d.dV = (d.D == 2 ? kPi * Dp / c->n_lag : kPi * Dp * Dp / c->n_lag) * c->drs;
+  const double V = d.D == 2 ? kPi * Dp * Dp / 4.0 : kPi * Dp * Dp * Dp / 6.0;
+  d.Mp = c->density_ratio * V;
+  d.meff = d.Mp - V;
+  d.Ip = d.D == 2 ? d.Mp * Dp * Dp / 8.0 : d.Mp * Dp * Dp / 10.0;
+  d.Kt = c->n_lag * d.dV;
+  d.Kr = d.Kt * d.radius * d.radius * (d.D == 2 ? 1.0 : 2.0 / 3.0);
+  const double g2 = c->gravity[0] * c->gravity[0] + c->gravity[1] * c->gravity[1] +
+                    c->gravity[2] * c->gravity[2];
+  d.c_ij = std::fabs((c->density_ratio - 1.0) * V) * std::sqrt(g2);
+  const double thr = Dp + c->zeta;
+  d.thr2 = thr * thr;
+  return d;
+}
+
+Layout carve(const ibm_lbm_config* c, const Derived& d) {
+  Layout l{};
+  Carver cv;
+  const size_t N = (size_t)d.g.N, np = (size_t)c->n_particles, D = d.D;
+  const size_t npts = (size_t)d.npts;
+  l.f = cv.take(sizeof(float) * d.Q * N);
+  l.ustar = cv.take(sizeof(float) * D * N);
+  l.fib = cv.take(sizeof(float) * D * N);
+  l.mask = cv.take(sizeof(uint32_t) * (size_t)d.g.rows * d.g.wpr);
+  l.X = cv.take(sizeof(double) * np * D);
+  l.U = cv.take(sizeof(double) * np * D);
+  l.Om = cv.take(sizeof(double) * np * 3);
+  l.Fh = cv.take(sizeof(double) * np * D);
+  l.Th = cv.take(sizeof(double) * np * 3);
+  l.Fhp = cv.take(sizeof(double) * np * D);
+  l.Thp = cv.take(sizeof(double) * np * 3);
+  l.acc = cv.take(sizeof(double) * np * D);
+  l.alp = cv.take(sizeof(double) * np * 3);
+  l.Pint = cv.take(sizeof(double) * np * D);
+  l.Lint = cv.take(sizeof(double) * np * 3);
+  l.Pprev = cv.take(sizeof(double) * np * D);
+  l.Lprev = cv.take(sizeof(double) * np * 3);
+  l.Fc = cv.take(sizeof(double) * np * D);
+  l.ref = cv.take(sizeof(double) * (size_t)c->n_lag * D);
+  l.Xb0 = cv.take(sizeof(double) * npts * D);
+  l.Xb1 = cv.take(sizeof(double) * npts * D);
+  l.Ub0 = cv.take(sizeof(float) * npts * D);
+  l.Ub1 = cv.take(sizeof(float) * npts * D);
+  l.Fb = cv.take(sizeof(float) * npts * D);
+  l.dFb = cv.take(sizeof(float) * npts * D);
+  l.ubs = cv.take(sizeof(float) * npts * D);
+  const size_t ncells = (size_t)d.nc[0] * d.nc[1] * d.nc[2];
+  l.cell_count = cv.take(sizeof(int) * ncells);
+  l.cell_start = cv.take(sizeof(int) * (ncells + 1));
+  l.sorted = cv.take(sizeof(int) * np);
+  l.nbr = cv.take(sizeof(int) * np * d.kmax);
+  l.nbr_count = cv.take(sizeof(int) * np);
+  l.gt = cv.take(sizeof(int) * 2 * (np + 1));
+  l.pairs = cv.take(sizeof(int) * np * d.kmax);
+  l.status = cv.take(sizeof(uint32_t));
+  l.total = cv.off;
+  return l;
+}
+
+// Lagrangian point offsets from the centre: circle theta_k = 2 pi k / N_L (2D) and
+// the Fibonacci sphere z_k = 1 - (2k+1)/N_L, phi_k = k pi (3 - sqrt 5) (3D), radius D/2.
+std::vector<double> reference_points(int D, int nl, double R) {
+  std::vector<double> r((size_t)nl * D);
+  for (int k = 0; k < nl; ++k) {
+    if (D == 2) {
+      const double th = 2.0 * kPi * k / nl;
+      r[2 * k] = R * std::cos(th);
+      r[2 * k + 1] = R * std::sin(th);
+    } else {
+      const double zk = 1.0 - (2.0 * k + 1.0) / nl;
+      const double rho = std::sqrt(1.0 - zk * zk);
+      const double ph = k * kPi * (3.0 - std::sqrt(5.0));
+      r[3 * k] = R * rho * std::cos(ph);
+      r[3 * k + 1] = R * rho * std::sin(ph);
+      r[3 * k + 2] = R * zk;
+    }
+  }
+  return r;
+}
+
+}  // namespace
+
+struct ibm_lbm_handle {
+  ibm_lbm_config cfg;
+  Derived d;
+  Layout l;
+  char* ws;
+  cudaStream_t s;
+  long long step;
+  int have_prev;
+  int64_t launches;
+  bool graph_ok[2];
+  bool graph_tried[2];
+  cudaGraphExec_t graph[2];
+  int graph_kernels[2];
+
+  template <class T>
+  T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+
+  LbmArgs lbm() const {
+    LbmArgs a{};
+    a.g = d.g;
+    a.f = at<float>(l.f);
+    a.ustar = at<float>(l.ustar);
+    a.fib = at<float>(l.fib);
+    a.mask = at<uint32_t>(l.mask);
+    a.omega = (float)(1.0 / cfg.tau);
+    a.kforce = (float)(1.0 - 0.5 / cfg.tau);
+    for (int k = 0; k < 3; ++k) a.body[k] = (k < d.D) ? (float)cfg.body_force[k] : 0.0f;
+    return a;
+  }
+  IbmArgs ibm(int parity) const {
+    IbmArgs a{};
+    a.g = d.g;
+    a.D = d.D;
+    a.np = cfg.n_particles;
+    a.nl = cfg.n_lag;
+    a.npts = d.npts;
+    a.radius = d.radius;
+    a.dV = (float)d.dV;
+    a.box = d.box;
+    a.ustar = at<float>(l.ustar);
+    a.fib = at<float>(l.fib);
+    a.Xb = at<double>(parity ? l.Xb1 : l.Xb0);
+    a.Ub = at<float>(parity ? l.Ub1 : l.Ub0);
+    a.Fb = at<float>(l.Fb);
+    a.dFb = at<float>(l.dFb);
+    a.ubs = at<float>(l.ubs);
+    a.Xc = at<double>(l.X);
+    a.Pint = at<double>(l.Pint);
+    a.Lint = at<double>(l.Lint);
+    a.status = at<uint32_t>(l.status);
+    return a;
+  }
+  PartArgs part(int out_parity) const {
+    PartArgs a{};
+    a.g = d.g;
+    a.D = d.D;
+    a.np = cfg.n_particles;
+    a.nl = cfg.n_lag;
+    a.radius = d.radius;
+    a.mark_radius = d.mark_radius;
+    a.dV = d.dV;
+    a.Mp = d.Mp;
+    a.meff = d.meff;
+    a.Ip = d.Ip;
+    a.Kt = d.Kt;
+    a.Kr = d.Kr;
+    for (int k = 0; k < 3; ++k) a.grav[k] = cfg.gravity[k];
+    a.fixed = cfg.fixed_particles;
+    a.ref = at<double>(l.ref);
+    a.Fb = at<float>(l.Fb);
+    a.X = at<double>(l.X);
+    a.U = at<double>(l.U);
+    a.Om = at<double>(l.Om);
+    a.Fh = at<double>(l.Fh);
+    a.Th = at<double>(l.Th);
+    a.Fhp = at<double>(l.Fhp);
+    a.Thp = at<double>(l.Thp);
+    a.acc = at<double>(l.acc);
+    a.alp = at<double>(l.alp);
+    a.Pint = at<double>(l.Pint);
+    a.Lint = at<double>(l.Lint);
+    a.Pprev = at<double>(l.Pprev);
+    a.Lprev = at<double>(l.Lprev);
+    a.Fc = at<double>(l.Fc);
+    a.Xb_out = at<double>(out_parity ? l.Xb1 : l.Xb0);
+    a.Ub_out = at<float>(out_parity ? l.Ub1 : l.Ub0);
+    a.mask = at<uint32_t>(l.mask);
+    a.status = at<uint32_t>(l.status);
+    return a;
+  }
+  PairArgs pairs() const {
+    PairArgs a{};
+    a.g = d.g;
+    a.D = d.D;
+    a.n = cfg.n_particles;
+    for (int k = 0; k < 3; ++k) {
+      a.nc[k] = d.nc[k];
+      a.H[k] = d.H[k];
+      a.L[k] = d.L[k];
+    }
+    a.diam = cfg.diameter;
+    a.zeta = cfg.zeta;
+    a.thr2 = d.thr2;
+    a.c_ij = d.c_ij;
+    a.eps_pp = cfg.eps_pp;
+    a.E_pp = cfg.E_pp;
+    a.kmax = d.kmax;
+    a.X = at<double>(l.X);
+    a.cell_count = at<int>(l.cell_count);
+    a.cell_start = at<int>(l.cell_start);
+    a.sorted = at<int>(l.sorted);
+    a.nbr = at<int>(l.nbr);
+    a.nbr_count = at<int>(l.nbr_count);
+    a.Fc = at<double>(l.Fc);
+    a.gt_count = at<int>(l.gt);
+    a.status = at<uint32_t>(l.status);
+    return a;
+  }
+};
+
+namespace {
+
+// Enqueue one step of the given parity.  With ev != nullptr an event is recorded
+// after each part (for ibm_lbm_time_parts).  Returns the number of kernels launched.
+int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, int* nk) {
+  const cudaStream_t s = h->s;
+  const bool particles = h->cfg.n_particles > 0;
+  int k = 0;
+  const LbmArgs la = h->lbm();
+  const IbmArgs ia = h->ibm(parity);
+  if (ev) CUDA_TRY(cudaEventRecord(ev[0], s));
+  if (particles) {
+    CUDA_TRY(launch_lbm_moments(la, h->d.D, parity, s));
+    ++k;
+  }
+  if (ev) CUDA_TRY(cudaEventRecord(ev[1], s));
+  if (particles) {
+    for (int m = 1; m <= h->cfg.mdf_iters; ++m) {
+      CUDA_TRY(launch_ibm_interp(ia, m, s));
+      CUDA_TRY(launch_ibm_spread(ia, s));
+      k += 2;
+    }
+    CUDA_TRY(launch_interior_momentum(ia, s));
+    ++k;
+  }
+  if (ev) CUDA_TRY(cudaEventRecord(ev[2], s));
+  CUDA_TRY(launch_lbm_step(la, h->d.D, parity, s));
+  ++k;
+  if (ev) CUDA_TRY(cudaEventRecord(ev[3], s));
+  if (particles) {
+    const PairArgs pa = h->pairs();
+    CUDA_TRY(launch_pair_cells(pa, s));
+    CUDA_TRY(launch_pair_contacts(pa, s));
+    k += 4;
+  }
+  if (ev) CUDA_TRY(cudaEventRecord(ev[4], s));
+  if (particles) {
+    CUDA_TRY(launch_particle_update(h->part(1 - parity), 1, have_prev, s));
+    ++k;
+  }
+  if (ev) CUDA_TRY(cudaEventRecord(ev[5], s));
+  *nk = k;
+  return IBMLBM_OK;
+}
+
+int capture_graph(ibm_lbm_handle* h, int parity) {
+  cudaGraph_t graph = nullptr;
+  int nk = 0;
+  if (cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return IBMLBM_ERR_CUDA;
+  }
+  const int rc = enqueue_step(h, parity, 1, nullptr, &nk);
+  const cudaError_t e = cudaStreamEndCapture(h->s, &graph);
+  if (rc != IBMLBM_OK || e != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return IBMLBM_ERR_CUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return IBMLBM_ERR_CUDA;
+  }
+  cudaGraphDestroy(graph);
+  h->graph[parity] = exec;
+  h->graph_kernels[parity] = nk;
+  h->graph_ok[parity] = true;
+  return IBMLBM_OK;
+}
+
+int regenerate_points(ibm_lbm_handle* h) {
+  if (h->cfg.n_particles == 0) return IBMLBM_OK;
+  CUDA_TRY(launch_particle_update(h->part((int)(h->step & 1)), 0, 0, h->s));
+  h->launches += 1;
+  return IBMLBM_OK;
+}
+
+int check_handle(ibm_lbm_handle* h) {
+  if (!h) return fail(IBMLBM_ERR_INVALID_ARG, "handle is NULL");
+  return IBMLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ibm_lbm_workspace_size(const ibm_lbm_config* cfg, size_t* bytes) {
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  if (!bytes) return fail(IBMLBM_ERR_INVALID_ARG, "bytes is NULL");
+  const Derived d = derive(cfg);
+  *bytes = carve(cfg, d).total;
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_init(const ibm_lbm_config* cfg, void* d_workspace, size_t bytes, void* stream,
+                 const double* h_centres, ibm_lbm_handle** out) {
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  if (!out) return fail(IBMLBM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  const Derived d = derive(cfg);
+  const Layout l = carve(cfg, d);
+  if (!d_workspace) return fail(IBMLBM_ERR_WORKSPACE, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(d_workspace) % kAlign)
+    return fail(IBMLBM_ERR_WORKSPACE, "workspace is not 256-byte aligned");
+  if (bytes < l.total)
+    return fail(IBMLBM_ERR_WORKSPACE, "workspace smaller than ibm_lbm_workspace_size");
+  if (cfg->n_particles > 0 && !h_centres)
+    return fail(IBMLBM_ERR_INVALID_ARG, "centres are NULL");
+  for (int i = 0; i < cfg->n_particles; ++i)
+    for (int k = 0; k < d.D; ++k) {
+      const double x = h_centres[(size_t)i * d.D + k];
+      if (!std::isfinite(x) || x < -0.5 || x >= d.L[k] - 0.5)
+        return fail(IBMLBM_ERR_INVALID_ARG, "particle centre outside the domain");
+    }
+  if (cfg->n_particles > 0) {
+    const size_t smem = ibm_spread_smem(d.D, cfg->n_lag, d.box);
+    if (smem > 227 * 1024)
+      return fail(IBMLBM_ERR_UNSUPPORTED, "particle too large for the spreading box");
+  }
+  ibm_lbm_handle* h = new ibm_lbm_handle();
+  h->cfg = *cfg;
+  h->d = d;
+  h->l = l;
+  h->ws = static_cast<char*>(d_workspace);
+  h->s = static_cast<cudaStream_t>(stream);
+  h->step = 0;
+  h->have_prev = 0;
+  h->launches = 0;
+  h->graph_ok[0] = h->graph_ok[1] = false;
+  h->graph_tried[0] = h->graph_tried[1] = false;
+  auto bail = [&](int code) {
+    delete h;
+    return code;
+  };
+#define INIT_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return bail(fail(IBMLBM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_))); \
+  } while (0)
+  INIT_TRY(cudaMemsetAsync(h->ws, 0, l.total, h->s));
+  if (cfg->n_particles > 0) {
+    INIT_TRY(cudaMemcpyAsync(h->at<double>(l.X), h_centres,
+                             sizeof(double) * (size_t)cfg->n_particles * d.D,
+                             cudaMemcpyHostToDevice, h->s));
+    const std::vector<double> ref = reference_points(d.D, cfg->n_lag, d.radius);
+    INIT_TRY(cudaMemcpyAsync(h->at<double>(l.ref), ref.data(), sizeof(double) * ref.size(),
+                             cudaMemcpyHostToDevice, h->s));
+    INIT_TRY(prepare_ibm_spread(d.D, ibm_spread_smem(d.D, cfg->n_lag, d.box)));
+    if (regenerate_points(h) != IBMLBM_OK) return bail(IBMLBM_ERR_CUDA);
+  }
+  INIT_TRY(cudaStreamSynchronize(h->s));
+#undef INIT_TRY
+  *out = h;
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_step(ibm_lbm_handle* h, int32_t n_steps) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (n_steps < 0) return fail(IBMLBM_ERR_INVALID_ARG, "n_steps < 0");
+  for (int32_t t = 0; t < n_steps; ++t) {
+    const int parity = (int)(h->step & 1);
+    if (h->have_prev && !h->graph_tried[parity]) {
+      h->graph_tried[parity] = true;
+      capture_graph(h, parity);  // on failure the steps run as eager launches
+    }
+    if (h->have_prev && h->graph_ok[parity]) {
+      CUDA_TRY(cudaGraphLaunch(h->graph[parity], h->s));
+      h->launches += h->graph_kernels[parity];
+    } else {
+      int nk = 0;
+      rc = enqueue_step(h, parity, h->have_prev, nullptr, &nk);
+      if (rc) return rc;
+      h->launches += nk;
+    }
+    h->step += 1;
+    h->have_prev = 1;
+  }
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_sync(ibm_lbm_handle* h) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  uint32_t st = 0;
+  CUDA_TRY(cudaMemcpy(&st, h->at<uint32_t>(h->l.status), sizeof(st), cudaMemcpyDeviceToHost));
+  if (st) {
+    CUDA_TRY(cudaMemset(h->at<uint32_t>(h->l.status), 0, sizeof(uint32_t)));
+    if (st & ST_NONFINITE) return fail(IBMLBM_ERR_NONFINITE, "non-finite particle state");
+    if (st & ST_OUT_OF_DOMAIN)
+      return fail(IBMLBM_ERR_OUT_OF_DOMAIN, "a particle centre left the domain");
+    return fail(IBMLBM_ERR_CAPACITY, "a contact list or spreading box overflowed");
+  }
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_set_pdfs(ibm_lbm_handle* h, const float* d_f) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!d_f) return fail(IBMLBM_ERR_INVALID_ARG, "f is NULL");
+  CUDA_TRY(launch_lbm_put(h->lbm(), h->d.D, (int)(h->step & 1), d_f, h->s));
+  h->launches += 1;
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_get_pdfs(ibm_lbm_handle* h, float* d_f) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!d_f) return fail(IBMLBM_ERR_INVALID_ARG, "f is NULL");
+  CUDA_TRY(launch_lbm_get(h->lbm(), h->d.D, (int)(h->step & 1), d_f, h->s));
+  h->launches += 1;
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_set_fields(ibm_lbm_handle* h, const double* d_p, const double* d_u) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!d_p || !d_u) return fail(IBMLBM_ERR_INVALID_ARG, "p or u is NULL");
+  CUDA_TRY(launch_lbm_equilibrium(h->lbm(), h->d.D, (int)(h->step & 1), d_p, d_u, h->s));
+  h->launches += 1;
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_get_fields(ibm_lbm_handle* h, double* d_p, double* d_u) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!d_p && !d_u) return IBMLBM_OK;
+  CUDA_TRY(launch_lbm_fields(h->lbm(), h->d.D, (int)(h->step & 1), d_p, d_u, h->s));
+  h->launches += 1;
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_set_particles(ibm_lbm_handle* h, const double* X, const double* U,
+                          const double* Omega) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  const int np = h->cfg.n_particles, D = h->d.D;
+  if (np == 0) return IBMLBM_OK;
+  if (X) {
+    for (int i = 0; i < np; ++i)
+      for (int k = 0; k < D; ++k) {
+        const double x = X[(size_t)i * D + k];
+        if (!std::isfinite(x) || x < -0.5 || x >= h->d.L[k] - 0.5)
+          return fail(IBMLBM_ERR_INVALID_ARG, "particle centre outside the domain");
+      }
+    CUDA_TRY(cudaMemcpyAsync(h->at<double>(h->l.X), X, sizeof(double) * np * D,
+                             cudaMemcpyHostToDevice, h->s));
+  }
+  if (U)
+    CUDA_TRY(cudaMemcpyAsync(h->at<double>(h->l.U), U, sizeof(double) * np * D,
+                             cudaMemcpyHostToDevice, h->s));
+  if (Omega) {
+    if (D == 2)
+      CUDA_TRY(cudaMemcpy2DAsync(h->at<double>(h->l.Om) + 2, 3 * sizeof(double), Omega,
+                                 sizeof(double), sizeof(double), np, cudaMemcpyHostToDevice, h->s));
+    else
+      CUDA_TRY(cudaMemcpyAsync(h->at<double>(h->l.Om), Omega, sizeof(double) * np * 3,
+                               cudaMemcpyHostToDevice, h->s));
+  }
+  rc = regenerate_points(h);
+  if (rc) return rc;
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_get_particles(ibm_lbm_handle* h, double* X, double* U, double* Omega,
+                          double* F_h, double* T_h, double* F_c) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  const int np = h->cfg.n_particles, D = h->d.D;
+  if (np == 0) return IBMLBM_OK;
+  const size_t vb = sizeof(double) * np * D;
+  if (X) CUDA_TRY(cudaMemcpyAsync(X, h->at<double>(h->l.X), vb, cudaMemcpyDeviceToHost, h->s));
+  if (U) CUDA_TRY(cudaMemcpyAsync(U, h->at<double>(h->l.U), vb, cudaMemcpyDeviceToHost, h->s));
+  if (F_h) CUDA_TRY(cudaMemcpyAsync(F_h, h->at<double>(h->l.Fh), vb, cudaMemcpyDeviceToHost, h->s));
+  if (F_c) CUDA_TRY(cudaMemcpyAsync(F_c, h->at<double>(h->l.Fc), vb, cudaMemcpyDeviceToHost, h->s));
+  double* ang[2] = {Omega, T_h};
+  const size_t offs[2] = {h->l.Om, h->l.Th};
+  for (int q = 0; q < 2; ++q) {
+    if (!ang[q]) continue;
+    if (D == 2)
+      CUDA_TRY(cudaMemcpy2DAsync(ang[q], sizeof(double), h->at<double>(offs[q]) + 2,
+                                 3 * sizeof(double), sizeof(double), np, cudaMemcpyDeviceToHost, h->s));
+    else
+      CUDA_TRY(cudaMemcpyAsync(ang[q], h->at<double>(offs[q]), sizeof(double) * np * 3,
+                               cudaMemcpyDeviceToHost, h->s));
+  }
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_get_lagrangian(ibm_lbm_handle* h, double* X_b, float* U_b, float* F_b,
+                           float* u_b_star) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  const size_t npts = (size_t)h->d.npts, D = h->d.D;
+  if (npts == 0) return IBMLBM_OK;
+  // points used by the last step (before its update regenerated them)
+  const int last = h->step > 0 ? (int)((h->step - 1) & 1) : 0;
+  if (X_b)
+    CUDA_TRY(cudaMemcpyAsync(X_b, h->at<double>(last ? h->l.Xb1 : h->l.Xb0),
+                             sizeof(double) * npts * D, cudaMemcpyDeviceToHost, h->s));
+  if (U_b)
+    CUDA_TRY(cudaMemcpyAsync(U_b, h->at<float>(last ? h->l.Ub1 : h->l.Ub0),
+                             sizeof(float) * npts * D, cudaMemcpyDeviceToHost, h->s));
+  if (F_b)
+    CUDA_TRY(cudaMemcpyAsync(F_b, h->at<float>(h->l.Fb), sizeof(float) * npts * D,
+                             cudaMemcpyDeviceToHost, h->s));
+  if (u_b_star)
+    CUDA_TRY(cudaMemcpyAsync(u_b_star, h->at<float>(h->l.ubs), sizeof(float) * npts * D,
+                             cudaMemcpyDeviceToHost, h->s));
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_get_interior_momentum(ibm_lbm_handle* h, double* P, double* L) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  const int np = h->cfg.n_particles, D = h->d.D;
+  if (np == 0) return IBMLBM_OK;
+  if (P)
+    CUDA_TRY(cudaMemcpyAsync(P, h->at<double>(h->l.Pint), sizeof(double) * np * D,
+                             cudaMemcpyDeviceToHost, h->s));
+  if (L) {
+    if (D == 2)
+      CUDA_TRY(cudaMemcpy2DAsync(L, sizeof(double), h->at<double>(h->l.Lint) + 2,
+                                 3 * sizeof(double), sizeof(double), np, cudaMemcpyDeviceToHost, h->s));
+    else
+      CUDA_TRY(cudaMemcpyAsync(L, h->at<double>(h->l.Lint), sizeof(double) * np * 3,
+                               cudaMemcpyDeviceToHost, h->s));
+  }
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_get_pairs(ibm_lbm_handle* h, int32_t* pairs, int64_t cap, int64_t* n) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!n || (cap > 0 && !pairs)) return fail(IBMLBM_ERR_INVALID_ARG, "pairs or n is NULL");
+  const int np = h->cfg.n_particles;
+  *n = 0;
+  if (np == 0) return IBMLBM_OK;
+  const PairArgs pa = h->pairs();
+  const long long dev_cap = (long long)np * h->d.kmax / 2;
+  CUDA_TRY(launch_pair_compact(pa, h->at<int>(h->l.pairs), dev_cap, h->s));
+  h->launches += 2;
+  int total = 0;
+  CUDA_TRY(cudaMemcpyAsync(&total, h->at<int>(h->l.gt) + np, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  *n = total;
+  if (total > cap) return fail(IBMLBM_ERR_CAPACITY, "more pairs than cap");
+  if (total > 0)
+    CUDA_TRY(cudaMemcpy(pairs, h->at<int>(h->l.pairs), sizeof(int) * 2 * (size_t)total,
+                        cudaMemcpyDeviceToHost));
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_get_launch_count(ibm_lbm_handle* h, int64_t* n) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!n) return fail(IBMLBM_ERR_INVALID_ARG, "n is NULL");
+  *n = h->launches;
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_time_parts(ibm_lbm_handle* h, int32_t n_steps, double* ms) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!ms || n_steps < 0) return fail(IBMLBM_ERR_INVALID_ARG, "ms is NULL or n_steps < 0");
+  for (int p = 0; p < IBMLBM_PART_COUNT; ++p) ms[p] = 0.0;
+  cudaEvent_t ev[6];
+  for (int k = 0; k < 6; ++k) CUDA_TRY(cudaEventCreate(&ev[k]));
+  int out = IBMLBM_OK;
+  for (int32_t t = 0; t < n_steps && out == IBMLBM_OK; ++t) {
+    int nk = 0;
+    out = enqueue_step(h, (int)(h->step & 1), h->have_prev, ev, &nk);
+    if (out) break;
+    h->launches += nk;
+    h->step += 1;
+    h->have_prev = 1;
+    if (cudaEventSynchronize(ev[5]) != cudaSuccess) {
+      out = fail(IBMLBM_ERR_CUDA, "event synchronisation failed");
+      break;
+    }
+    for (int p = 0; p < IBMLBM_PART_COUNT; ++p) {
+      float v = 0.0f;
+      cudaEventElapsedTime(&v, ev[p], ev[p + 1]);
+      ms[p] += v;
+    }
+  }
+  for (int k = 0; k < 6; ++k) cudaEventDestroy(ev[k]);
+  return out;
+}
+
+void ibm_lbm_destroy(ibm_lbm_handle* h) {
+  if (!h) return;
+  for (int p = 0; p < 2; ++p)
+    if (h->graph_ok[p]) cudaGraphExecDestroy(h->graph[p]);
+  delete h;
+}
+
+const char* ibm_lbm_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------ standalone pair search
+namespace {
+struct PairScratch {
+  size_t cell_count, cell_start, sorted, nbr, nbr_count, gt, status, total;
+};
+
+PairScratch pair_scratch(int D, int n, int kmax, const int* nc) {
+  PairScratch p{};
+  Carver cv;
+  const size_t ncells = (size_t)nc[0] * nc[1] * nc[2];
+  (void)D;
+  p.cell_count = cv.take(sizeof(int) * ncells);
+  p.cell_start = cv.take(sizeof(int) * (ncells + 1));
+  p.sorted = cv.take(sizeof(int) * (size_t)n);
+  p.nbr = cv.take(sizeof(int) * (size_t)n * kmax);
+  p.nbr_count = cv.take(sizeof(int) * (size_t)n);
+  p.gt = cv.take(sizeof(int) * 2 * ((size_t)n + 1));
+  p.status = cv.take(sizeof(uint32_t));
+  p.total = cv.off;
+  return p;
+}
+
+int pair_domain(int32_t dim, const int32_t* n_nodes, const int32_t* periodic, double diameter,
+                double zeta, int32_t n, int32_t max_neighbors, double* L, int* per, int* nc,
+                double* H, int* kmax) {
+  if (dim != 2 && dim != 3) return fail(IBMLBM_ERR_INVALID_ARG, "dim must be 2 or 3");
+  if (!n_nodes) return fail(IBMLBM_ERR_INVALID_ARG, "n_nodes is NULL");
+  if (n < 0) return fail(IBMLBM_ERR_INVALID_ARG, "n < 0");
+  if (!(diameter > 0.0) || !(zeta > 0.0))
+    return fail(IBMLBM_ERR_INVALID_ARG, "diameter and zeta must be > 0");
+  if (max_neighbors < 0 || max_neighbors > 64)
+    return fail(IBMLBM_ERR_INVALID_ARG, "max_neighbors must be in 0..64");
+  for (int k = 0; k < 3; ++k) {
+    L[k] = k < dim ? (double)n_nodes[k] : 1.0;
+    per[k] = (k < dim && periodic) ? (periodic[k] ? 1 : 0) : 0;
+    if (k < dim && n_nodes[k] < 1) return fail(IBMLBM_ERR_INVALID_ARG, "n_nodes must be >= 1");
+  }
+  cell_grid(dim, L, per, diameter + zeta, nc, H);
+  *kmax = max_neighbors ? max_neighbors : 32;
+  return IBMLBM_OK;
+}
+}  // namespace
+
+int ibm_lbm_pair_search_scratch_size(int32_t dim, const int32_t* n_nodes, double diameter,
+                                     double zeta, int32_t n, int32_t max_neighbors,
+                                     size_t* bytes) {
+  double L[3], H[3];
+  int per[3], nc[3], kmax;
+  int rc = pair_domain(dim, n_nodes, nullptr, diameter, zeta, n, max_neighbors, L, per, nc, H, &kmax);
+  if (rc) return rc;
+  if (!bytes) return fail(IBMLBM_ERR_INVALID_ARG, "bytes is NULL");
+  *bytes = pair_scratch(dim, n, kmax, nc).total;
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_pair_search(int32_t dim, const int32_t* n_nodes, const int32_t* periodic,
+                        double diameter, double zeta, int32_t n, const double* d_X,
+                        int32_t max_neighbors, void* d_scratch, size_t scratch_bytes,
+                        int32_t* d_pairs, int64_t cap, int64_t* h_count, void* stream) {
+  double L[3], H[3];
+  int per[3], nc[3], kmax;
+  int rc = pair_domain(dim, n_nodes, periodic, diameter, zeta, n, max_neighbors, L, per, nc, H, &kmax);
+  if (rc) return rc;
+  if (!h_count) return fail(IBMLBM_ERR_INVALID_ARG, "count is NULL");
+  *h_count = 0;
+  if (n == 0) return IBMLBM_OK;
+  if (!d_X || (cap > 0 && !d_pairs)) return fail(IBMLBM_ERR_INVALID_ARG, "X or pairs is NULL");
+  const PairScratch ps = pair_scratch(dim, n, kmax, nc);
+  if (!d_scratch || scratch_bytes < ps.total || reinterpret_cast<uintptr_t>(d_scratch) % kAlign)
+    return fail(IBMLBM_ERR_WORKSPACE, "scratch missing, misaligned or too small");
+  char* sc = static_cast<char*>(d_scratch);
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PairArgs a{};
+  a.g.nx = (int)L[0];
+  a.g.ny = (int)L[1];
+  a.g.nz = (int)L[2];
+  for (int k = 0; k < 3; ++k) {
+    a.g.per[k] = per[k];
+    a.nc[k] = nc[k];
+    a.H[k] = H[k];
+    a.L[k] = L[k];
+  }
+  a.D = dim;
+  a.n = n;
+  a.diam = diameter;
+  a.zeta = zeta;
+  const double thr = diameter + zeta;
+  a.thr2 = thr * thr;
+  a.kmax = kmax;
+  a.X = d_X;
+  a.cell_count = reinterpret_cast<int*>(sc + ps.cell_count);
+  a.cell_start = reinterpret_cast<int*>(sc + ps.cell_start);
+  a.sorted = reinterpret_cast<int*>(sc + ps.sorted);
+  a.nbr = reinterpret_cast<int*>(sc + ps.nbr);
+  a.nbr_count = reinterpret_cast<int*>(sc + ps.nbr_count);
+  a.gt_count = reinterpret_cast<int*>(sc + ps.gt);
+  a.status = reinterpret_cast<uint32_t*>(sc + ps.status);
+  a.Fc = nullptr;
+  CUDA_TRY(cudaMemsetAsync(a.cell_count, 0, sizeof(int) * (size_t)nc[0] * nc[1] * nc[2], s));
+  CUDA_TRY(cudaMemsetAsync(a.status, 0, sizeof(uint32_t), s));
+  CUDA_TRY(launch_pair_cells(a, s));
+  CUDA_TRY(launch_pair_contacts(a, s));
+  CUDA_TRY(launch_pair_compact(a, d_pairs, cap, s));
+  int total = 0;
+  uint32_t st = 0;
+  CUDA_TRY(cudaMemcpyAsync(&total, a.gt_count + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(&st, a.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  *h_count = total;
+  if (st & ST_CAPACITY) return fail(IBMLBM_ERR_CAPACITY, "a particle has more than max_neighbors partners");
+  if (total > cap) return fail(IBMLBM_ERR_CAPACITY, "more pairs than cap");
+  return IBMLBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,368 @@
+// Lattice-Boltzmann kernels: fused SRT-LBGK collision with Guo split forcing and
+// in-place AA-pattern streaming with halfway bounce-back (Eq. 1, 4-8, 17-18), the
+// macroscopic velocity on flagged nodes (Eq. 5), and layout helpers.
+//
+// AA pattern, one PDF array a[Q][N]:
+//   even step (parity 0): node x reads f_a(x) from a[a][x] and writes the
+//     post-collision f*_a to a[opp(a)][x]          (purely local);
+//   odd step (parity 1): node x reads f_a(x) from a[opp(a)][x - e_a], or from a[a][x]
+//     when x - e_a lies beyond a wall (halfway bounce-back of the even step), and
+//     writes f*_a to a[a][x + e_a], or to a[opp(a)][x] when x + e_a lies beyond a wall.
+// Each node reads and writes the same set of slots, so no two nodes race and one
+// copy of the PDFs suffices (the role the swap algorithm of Sec. 3.3 plays on a CPU).
+#include "common.cuh"
+#include "launch.h"
+
+namespace ibmlbm {
+
+constexpr int kLbmBlock = 128;
+
+// index of the neighbour x - s*e_a (s = +1 for the pull source, -1 for the push
+// target); false if it lies beyond a wall
+template <class L>
+__device__ __forceinline__ bool neighbour(const Geo& g, int a, int s, int x, int y, int z,
+                                          long long n, long long& idx) {
+  idx = n;
+  const int ex = s * L::e(a, 0), ey = s * L::e(a, 1), ez = s * L::e(a, 2);
+  if (ex) {
+    const int t = x - ex;
+    if (t < 0 || t >= g.nx) {
+      if (!g.per[0]) return false;
+      idx += (t < 0) ? g.nx : -g.nx;
+    }
+    idx -= ex;
+  }
+  if (ey) {
+    const int t = y - ey;
+    if (t < 0 || t >= g.ny) {
+      if (!g.per[1]) return false;
+      idx += (long long)((t < 0) ? g.ny : -g.ny) * g.nx;
+    }
+    idx -= (long long)ey * g.nx;
+  }
+  if (L::dim == 3 && ez) {
+    const int t = z - ez;
+    const long long plane = (long long)g.nx * g.ny;
+    if (t < 0 || t >= g.nz) {
+      if (!g.per[2]) return false;
+      idx += ((t < 0) ? g.nz : -g.nz) * plane;
+    }
+    idx -= ez * plane;
+  }
+  return true;
+}
+
+// pre-collision PDFs f_a(x) of the current time under the layout of the given parity
+template <class L, int PARITY>
+__device__ __forceinline__ void load_pdfs(const Geo& g, const float* __restrict__ f, int x,
+                                          int y, int z, long long n, float (&fa)[L::Q]) {
+  const long long N = g.N;
+#pragma unroll
+  for (int a = 0; a < L::Q; ++a) {
+    if (PARITY == 0 || a == 0) {
+      fa[a] = f[a * N + n];
+    } else {
+      long long src;
+      if (neighbour<L>(g, a, 1, x, y, z, n, src))
+        fa[a] = f[opp<L>(a) * N + src];
+      else
+        fa[a] = f[a * N + n];
+    }
+  }
+}
+
+// inverse of load_pdfs: slot of f_a(x) under the layout of the given parity
+template <class L, int PARITY>
+__device__ __forceinline__ void put_pdfs(const Geo& g, float* __restrict__ f, int x, int y,
+                                         int z, long long n, const float (&fa)[L::Q]) {
+  const long long N = g.N;
+#pragma unroll
+  for (int a = 0; a < L::Q; ++a) {
+    if (PARITY == 0 || a == 0) {
+      f[a * N + n] = fa[a];
+    } else {
+      long long src;
+      if (neighbour<L>(g, a, 1, x, y, z, n, src))
+        f[opp<L>(a) * N + src] = fa[a];
+      else
+        f[a * N + n] = fa[a];
+    }
+  }
+}
+
+// post-collision store of the given parity (after which the opposite parity holds)
+template <class L, int PARITY>
+__device__ __forceinline__ void store_post(const Geo& g, float* __restrict__ f, int x, int y,
+                                           int z, long long n, const float (&fa)[L::Q]) {
+  const long long N = g.N;
+#pragma unroll
+  for (int a = 0; a < L::Q; ++a) {
+    if (a == 0) {
+      f[n] = fa[0];
+    } else if (PARITY == 0) {
+      f[opp<L>(a) * N + n] = fa[a];
+    } else {
+      long long dst;
+      if (neighbour<L>(g, a, -1, x, y, z, n, dst))
+        f[a * N + dst] = fa[a];
+      else
+        f[opp<L>(a) * N + n] = fa[a];
+    }
+  }
+}
+
+// Eq. 5 (u* = sum e f) and the sum of the moving populations used by Eq. 6
+template <class L>
+__device__ __forceinline__ void moments(const float (&f)[L::Q], float (&us)[3], float& s1) {
+  us[0] = us[1] = us[2] = 0.0f;
+  s1 = 0.0f;
+#pragma unroll
+  for (int a = 1; a < L::Q; ++a) {
+    s1 += f[a];
+#pragma unroll
+    for (int k = 0; k < L::dim; ++k) {
+      if (L::e(a, k) == 1) us[k] += f[a];
+      if (L::e(a, k) == -1) us[k] -= f[a];
+    }
+  }
+}
+
+// Eq. 6: p = cs^2/(1 - w0) (sum_{a>=1} f_a - rho0 w0 |u|^2 / (2 cs^2))
+template <class L>
+__device__ __forceinline__ float pressure(float s1, float uu) {
+  constexpr float w0 = L::w(0);
+  return s1 * (1.0f / (3.0f * (1.0f - w0))) - uu * (w0 / (2.0f * (1.0f - w0)));
+}
+
+// Eq. 4 equilibrium, Eq. 8 forcing term and the relaxation of Eq. 41-42, computed
+// for each opposite pair (a, a + H) from one shared even part (Eq. 38, Eq. 40).
+template <class L>
+__device__ __forceinline__ void collide(float (&f)[L::Q], const float (&F)[3], float omega,
+                                        float kforce) {
+  float us[3], s1;
+  moments<L>(f, us, s1);
+  float u[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) u[k] = (k < L::dim) ? us[k] + 0.5f * F[k] : 0.0f;  // Eq. 7
+  const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+  const float p = pressure<L>(s1, uu);
+  {
+    constexpr float w0 = L::w(0);
+    const float feq = 3.0f * (w0 - 1.0f) * p - 1.5f * w0 * uu;
+    const float Fa = -3.0f * kforce * w0 * uF;
+    f[0] = f[0] - omega * (f[0] - feq) + Fa;
+  }
+#pragma unroll
+  for (int a = 1; a <= L::H; ++a) {
+    const float w = L::w(a);
+    float eu = 0.0f, eF = 0.0f;
+#pragma unroll
+    for (int k = 0; k < L::dim; ++k) {
+      if (L::e(a, k) == 1) {
+        eu += u[k];
+        eF += F[k];
+      }
+      if (L::e(a, k) == -1) {
+        eu -= u[k];
+        eF -= F[k];
+      }
+    }
+    const float eq_even = w * (3.0f * p + 4.5f * eu * eu - 1.5f * uu);
+    const float eq_odd = 3.0f * w * eu;
+    const float F_even = kforce * w * (9.0f * eu * eF - 3.0f * uF);
+    const float F_odd = 3.0f * kforce * w * eF;
+    const int b = a + L::H;
+    f[a] = f[a] - omega * (f[a] - (eq_even + eq_odd)) + (F_even + F_odd);
+    f[b] = f[b] - omega * (f[b] - (eq_even - eq_odd)) + (F_even - F_odd);
+  }
+}
+
+struct NodeCoord {
+  int x, y, z;
+  long long row, n;
+  bool valid;
+};
+
+__device__ __forceinline__ NodeCoord node_coord(const Geo& g, int cpr) {
+  NodeCoord c;
+  const int chunk = blockIdx.x % cpr;
+  c.row = blockIdx.x / cpr;
+  c.x = chunk * kLbmBlock + threadIdx.x;
+  c.y = (int)(c.row % g.ny);
+  c.z = (int)(c.row / g.ny);
+  c.valid = c.x < g.nx;
+  c.n = (long long)c.x + (long long)g.nx * c.row;
+  return c;
+}
+
+// ------------------------------------------------------------------ kernels
+
+// One full time step on every node: read f (AA parity), add the IB force on
+// flagged nodes (and clear it), collide, stream in place.  Clears the mask words.
+template <class L, int PARITY>
+__global__ void __launch_bounds__(kLbmBlock) lbm_step_kernel(LbmArgs A, int cpr) {
+  const NodeCoord c = node_coord(A.g, cpr);
+  const int wi = c.x >> 5;
+  uint32_t word = 0u;
+  if (wi < A.g.wpr) word = A.mask[c.row * A.g.wpr + wi];
+  const bool flagged = c.valid && ((word >> (c.x & 31)) & 1u);
+  if (c.valid) {
+    float fa[L::Q];
+    load_pdfs<L, PARITY>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
+    float F[3] = {A.body[0], A.body[1], A.body[2]};
+    if (flagged) {
+#pragma unroll
+      for (int k = 0; k < L::dim; ++k) {
+        float* p = A.fib + k * A.g.N + c.n;
+        F[k] += *p;
+        *p = 0.0f;
+      }
+    }
+    collide<L>(fa, F, A.omega, A.kforce);
+    store_post<L, PARITY>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
+  }
+  __syncwarp();
+  if ((c.x & 31) == 0 && wi < A.g.wpr && word) A.mask[c.row * A.g.wpr + wi] = 0u;
+}
+
+// u* = sum_a e_a f_a (Eq. 5) on flagged nodes only.
+template <class L, int PARITY>
+__global__ void __launch_bounds__(kLbmBlock) lbm_moments_kernel(LbmArgs A, int cpr) {
+  const NodeCoord c = node_coord(A.g, cpr);
+  const int wi = c.x >> 5;
+  if (wi >= A.g.wpr) return;
+  const uint32_t word = A.mask[c.row * A.g.wpr + wi];
+  if (!c.valid || !((word >> (c.x & 31)) & 1u)) return;
+  float fa[L::Q], us[3], s1;
+  load_pdfs<L, PARITY>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
+  moments<L>(fa, us, s1);
+#pragma unroll
+  for (int k = 0; k < L::dim; ++k) A.ustar[k * A.g.N + c.n] = us[k];
+}
+
+// p (Eq. 6 with u = u*) and u* (Eq. 5) on every node, as doubles.
+template <class L, int PARITY>
+__global__ void __launch_bounds__(kLbmBlock) lbm_fields_kernel(LbmArgs A, int cpr, double* p,
+                                                              double* u) {
+  const NodeCoord c = node_coord(A.g, cpr);
+  if (!c.valid) return;
+  float fa[L::Q], us[3], s1;
+  load_pdfs<L, PARITY>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
+  moments<L>(fa, us, s1);
+  const float uu = us[0] * us[0] + us[1] * us[1] + us[2] * us[2];
+  if (p) p[c.n] = (double)pressure<L>(s1, uu);
+  if (u) {
+#pragma unroll
+    for (int k = 0; k < L::dim; ++k) u[k * A.g.N + c.n] = (double)us[k];
+  }
+}
+
+// canonical [Q][N] copy of the current PDFs
+template <class L, int PARITY>
+__global__ void __launch_bounds__(kLbmBlock) lbm_get_kernel(LbmArgs A, int cpr, float* out) {
+  const NodeCoord c = node_coord(A.g, cpr);
+  if (!c.valid) return;
+  float fa[L::Q];
+  load_pdfs<L, PARITY>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
+#pragma unroll
+  for (int a = 0; a < L::Q; ++a) out[a * A.g.N + c.n] = fa[a];
+}
+
+// write canonical [Q][N] PDFs into the layout of the current parity
+template <class L, int PARITY>
+__global__ void __launch_bounds__(kLbmBlock) lbm_put_kernel(LbmArgs A, int cpr,
+                                                           const float* in) {
+  const NodeCoord c = node_coord(A.g, cpr);
+  if (!c.valid) return;
+  float fa[L::Q];
+#pragma unroll
+  for (int a = 0; a < L::Q; ++a) fa[a] = in[a * A.g.N + c.n];
+  put_pdfs<L, PARITY>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
+}
+
+// equilibrium of Eq. 4 for given p [N] and u [D][N] (doubles), current parity layout
+template <class L, int PARITY>
+__global__ void __launch_bounds__(kLbmBlock) lbm_equilibrium_kernel(LbmArgs A, int cpr,
+                                                                   const double* p,
+                                                                   const double* u) {
+  const NodeCoord c = node_coord(A.g, cpr);
+  if (!c.valid) return;
+  float uv[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int k = 0; k < L::dim; ++k) uv[k] = (float)u[k * A.g.N + c.n];
+  const float pp = (float)p[c.n];
+  const float uu = uv[0] * uv[0] + uv[1] * uv[1] + uv[2] * uv[2];
+  float fa[L::Q];
+  fa[0] = 3.0f * (L::w(0) - 1.0f) * pp - 1.5f * L::w(0) * uu;
+#pragma unroll
+  for (int a = 1; a < L::Q; ++a) {
+    const float eu = L::e(a, 0) * uv[0] + L::e(a, 1) * uv[1] + L::e(a, 2) * uv[2];
+    fa[a] = L::w(a) * (3.0f * pp + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
+  }
+  put_pdfs<L, PARITY>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
+}
+
+// ------------------------------------------------------------------ launchers
+static dim3 lbm_grid(const Geo& g, int& cpr) {
+  cpr = (g.nx + kLbmBlock - 1) / kLbmBlock;
+  return dim3((unsigned)((long long)cpr * g.rows));
+}
+
+#define IBMLBM_DISPATCH(D, PARITY, KERNEL, ...)                                     \
+  do {                                                                              \
+    if ((D) == 2) {                                                                 \
+      if ((PARITY) == 0) KERNEL<Lat<2>, 0><<<grid, kLbmBlock, 0, s>>>(__VA_ARGS__); \
+      else KERNEL<Lat<2>, 1><<<grid, kLbmBlock, 0, s>>>(__VA_ARGS__);               \
+    } else {                                                                        \
+      if ((PARITY) == 0) KERNEL<Lat<3>, 0><<<grid, kLbmBlock, 0, s>>>(__VA_ARGS__); \
+      else KERNEL<Lat<3>, 1><<<grid, kLbmBlock, 0, s>>>(__VA_ARGS__);               \
+    }                                                                               \
+  } while (0)
+
+cudaError_t launch_lbm_step(const LbmArgs& A, int D, int parity, cudaStream_t s) {
+  int cpr;
+  const dim3 grid = lbm_grid(A.g, cpr);
+  IBMLBM_DISPATCH(D, parity, lbm_step_kernel, A, cpr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lbm_moments(const LbmArgs& A, int D, int parity, cudaStream_t s) {
+  int cpr;
+  const dim3 grid = lbm_grid(A.g, cpr);
+  IBMLBM_DISPATCH(D, parity, lbm_moments_kernel, A, cpr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lbm_fields(const LbmArgs& A, int D, int parity, double* p, double* u,
+                              cudaStream_t s) {
+  int cpr;
+  const dim3 grid = lbm_grid(A.g, cpr);
+  IBMLBM_DISPATCH(D, parity, lbm_fields_kernel, A, cpr, p, u);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lbm_get(const LbmArgs& A, int D, int parity, float* out, cudaStream_t s) {
+  int cpr;
+  const dim3 grid = lbm_grid(A.g, cpr);
+  IBMLBM_DISPATCH(D, parity, lbm_get_kernel, A, cpr, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lbm_put(const LbmArgs& A, int D, int parity, const float* in,
+                           cudaStream_t s) {
+  int cpr;
+  const dim3 grid = lbm_grid(A.g, cpr);
+  IBMLBM_DISPATCH(D, parity, lbm_put_kernel, A, cpr, in);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lbm_equilibrium(const LbmArgs& A, int D, int parity, const double* p,
+                                   const double* u, cudaStream_t s) {
+  int cpr;
+  const dim3 grid = lbm_grid(A.g, cpr);
+  IBMLBM_DISPATCH(D, parity, lbm_equilibrium_kernel, A, cpr, p, u);
+  return cudaGetLastError();
+}
+
+}  // namespace ibmlbm

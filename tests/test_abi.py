@@ -1,0 +1,76 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every function
+declared in include/ibmlbm.h; configuration checks and workspace sizing (host
+code only, no GPU call)."""
+import ctypes as C
+import re
+
+import pytest
+
+from paper_2002_08855_gb300 import binding, build, inputs
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.lib()
+
+
+def declared_functions():
+    text = open(binding.HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ibm_lbm_\w+)\s*\(", text)))
+
+
+def test_every_declared_function_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    # the binding knows every declared function and nothing else
+    assert sorted(binding.SIGNATURES) == names
+
+
+def test_config_struct_matches_header(lib):
+    text = open(binding.HEADER).read()
+    body = text[text.index("typedef struct ibm_lbm_config"):text.index("} ibm_lbm_config;")]
+    fields = re.findall(r"\b(?:uint32_t|int32_t|double)\s+([^;]+);", body)
+    names = []
+    for f in fields:
+        for part in f.split(","):
+            names.append(re.sub(r"\[.*\]", "", part).strip())
+    assert names == [n for n, _ in binding.Config._fields_]
+
+
+def test_workspace_size_of_the_2048x4096_cavity(lib):
+    w = inputs.cavity_2d_large(0.1)
+    n = binding.workspace_size(w)
+    pdfs = 9 * 2048 * 4096 * 4
+    fields = 2 * 2 * 2048 * 4096 * 4  # u* and f_IB
+    assert pdfs + fields < n < (pdfs + fields) * 1.1
+
+
+@pytest.mark.parametrize("field,value,code", [
+    ("dim", 4, "INVALID_ARG"), ("tau", 0.5, "INVALID_ARG"), ("nx", 0, "INVALID_ARG"),
+    ("delta_kind", 3, "UNSUPPORTED"), ("n_lag", 0, "INVALID_ARG"), ("drs", 0.0, "INVALID_ARG"),
+])
+def test_invalid_configurations_are_rejected(lib, field, value, code):
+    w = inputs.cavity_2d_small().as_dict()
+    w[field] = value
+    with pytest.raises(binding.IbmLbmError) as e:
+        binding.workspace_size(w)
+    assert e.value.name == code
+    assert lib.ibm_lbm_last_error().decode()
+
+
+def test_struct_size_mismatch_rejected(lib):
+    cfg = binding.make_config(inputs.cavity_2d_small())
+    cfg.struct_size = 8
+    n = C.c_size_t(0)
+    assert lib.ibm_lbm_workspace_size(C.byref(cfg), C.byref(n)) == -1
+
+
+def test_pair_scratch_size_host_only(lib):
+    n = C.c_size_t(0)
+    nodes = (C.c_int32 * 3)(2048, 4096, 1)
+    assert lib.ibm_lbm_pair_search_scratch_size(2, nodes, 10.0, 2.0, 42723, 0, C.byref(n)) == 0
+    assert n.value > 42723 * 32 * 4
