@@ -55,14 +55,15 @@ struct Derived {
   int kmax;
   int nc[3];
   double H[3], L[3];
-  int box;
-  double radius, mark_radius, dV, Mp, meff, Ip, Kt, Kr, c_ij, thr2;
+  int box, rcell;
+  double radius, dV, Mp, meff, Ip, Kt, Kr, c_ij, thr2;
+  float mark_radius;
 };
 
 struct Layout {
   size_t f, ustar, fib, mask;
   size_t X, U, Om, Fh, Th, Fhp, Thp, acc, alp, Pint, Lint, Pprev, Lprev, Fc;
-  size_t ref, Xb0, Xb1, Ub0, Ub1, Fb, dFb, ubs;
+  size_t ref_fix, ref_f, Xcf, Xb0, Xb1, Ub0, Ub1, Fb, dFb, ubs;
   size_t cell_count, cell_start, sorted, nbr, nbr_count, gt, pairs, status;
   size_t total;
 };
@@ -131,8 +132,11 @@ Derived derive(const ibm_lbm_config* c) {
   d.L[2] = d.g.nz;
   const double Dp = c->diameter;
   d.radius = 0.5 * Dp;
-  d.mark_radius = d.radius + 2.0 * std::sqrt((double)d.D) + 1e-9;
-  d.box = (int)std::ceil(Dp) + 6;
+  // superset of every support node (within 2 sqrt(D) of a surface point) and of the
+  // interior; the 0.05 margin absorbs single-precision rounding of the marking test
+  d.mark_radius = (float)(d.radius + 2.0 * std::sqrt((double)d.D) + 0.05);
+  d.rcell = (int)std::ceil(d.radius);
+  d.box = 2 * d.rcell + 6;
   cell_grid(d.D, d.L, d.g.per, Dp + c->zeta, d.nc, d.H);
   // Eq. 13 point volume: 2D ds * drs with ds = pi D / N_L; 3D (pi D^2 / N_L) * drs
   if (c->n_lag > 0)
@@ -174,9 +178,11 @@ Layout carve(const ibm_lbm_config* c, const Derived& d) {
   l.Pprev = cv.take(sizeof(double) * np * D);
   l.Lprev = cv.take(sizeof(double) * np * 3);
   l.Fc = cv.take(sizeof(double) * np * D);
-  l.ref = cv.take(sizeof(double) * (size_t)c->n_lag * D);
-  l.Xb0 = cv.take(sizeof(double) * npts * D);
-  l.Xb1 = cv.take(sizeof(double) * npts * D);
+  l.ref_fix = cv.take(sizeof(long long) * (size_t)c->n_lag * D);
+  l.ref_f = cv.take(sizeof(float) * (size_t)c->n_lag * D);
+  l.Xcf = cv.take(sizeof(long long) * np * D);
+  l.Xb0 = cv.take(sizeof(long long) * npts * D);
+  l.Xb1 = cv.take(sizeof(long long) * npts * D);
   l.Ub0 = cv.take(sizeof(float) * npts * D);
   l.Ub1 = cv.take(sizeof(float) * npts * D);
   l.Fb = cv.take(sizeof(float) * npts * D);
@@ -255,16 +261,19 @@ struct ibm_lbm_handle {
     a.nl = cfg.n_lag;
     a.npts = d.npts;
     a.radius = d.radius;
+    a.radius_f = (float)d.radius;
+    a.rcell = d.rcell;
     a.dV = (float)d.dV;
     a.box = d.box;
     a.ustar = at<float>(l.ustar);
     a.fib = at<float>(l.fib);
-    a.Xb = at<double>(parity ? l.Xb1 : l.Xb0);
+    a.Xb = at<long long>(parity ? l.Xb1 : l.Xb0);
     a.Ub = at<float>(parity ? l.Ub1 : l.Ub0);
     a.Fb = at<float>(l.Fb);
     a.dFb = at<float>(l.dFb);
     a.ubs = at<float>(l.ubs);
     a.Xc = at<double>(l.X);
+    a.Xcf = at<long long>(l.Xcf);
     a.Pint = at<double>(l.Pint);
     a.Lint = at<double>(l.Lint);
     a.status = at<uint32_t>(l.status);
@@ -286,7 +295,9 @@ struct ibm_lbm_handle {
     a.Kr = d.Kr;
     for (int k = 0; k < 3; ++k) a.grav[k] = cfg.gravity[k];
     a.fixed = cfg.fixed_particles;
-    a.ref = at<double>(l.ref);
+    a.ref_fix = at<long long>(l.ref_fix);
+    a.ref_f = at<float>(l.ref_f);
+    a.Xcf = at<long long>(l.Xcf);
     a.Fb = at<float>(l.Fb);
     a.X = at<double>(l.X);
     a.U = at<double>(l.U);
@@ -302,7 +313,7 @@ struct ibm_lbm_handle {
     a.Pprev = at<double>(l.Pprev);
     a.Lprev = at<double>(l.Lprev);
     a.Fc = at<double>(l.Fc);
-    a.Xb_out = at<double>(out_parity ? l.Xb1 : l.Xb0);
+    a.Xb_out = at<long long>(out_parity ? l.Xb1 : l.Xb0);
     a.Ub_out = at<float>(out_parity ? l.Ub1 : l.Ub0);
     a.mask = at<uint32_t>(l.mask);
     a.status = at<uint32_t>(l.status);
@@ -488,8 +499,17 @@ int ibm_lbm_init(const ibm_lbm_config* cfg, void* d_workspace, size_t bytes, voi
                              sizeof(double) * (size_t)cfg->n_particles * d.D,
                              cudaMemcpyHostToDevice, h->s));
     const std::vector<double> ref = reference_points(d.D, cfg->n_lag, d.radius);
-    INIT_TRY(cudaMemcpyAsync(h->at<double>(l.ref), ref.data(), sizeof(double) * ref.size(),
+    std::vector<long long> ref_fix(ref.size());
+    std::vector<float> ref_f(ref.size());
+    for (size_t k = 0; k < ref.size(); ++k) {
+      ref_fix[k] = std::llrint(ref[k] * kFixScale);
+      ref_f[k] = (float)ref[k];
+    }
+    INIT_TRY(cudaMemcpyAsync(h->at<long long>(l.ref_fix), ref_fix.data(),
+                             sizeof(long long) * ref_fix.size(), cudaMemcpyHostToDevice, h->s));
+    INIT_TRY(cudaMemcpyAsync(h->at<float>(l.ref_f), ref_f.data(), sizeof(float) * ref_f.size(),
                              cudaMemcpyHostToDevice, h->s));
+    INIT_TRY(cudaStreamSynchronize(h->s));  // host vectors go out of scope
     INIT_TRY(prepare_ibm_spread(d.D, ibm_spread_smem(d.D, cfg->n_lag, d.box)));
     if (regenerate_points(h) != IBMLBM_OK) return bail(IBMLBM_ERR_CUDA);
   }
@@ -643,9 +663,10 @@ int ibm_lbm_get_lagrangian(ibm_lbm_handle* h, double* X_b, float* U_b, float* F_
   if (npts == 0) return IBMLBM_OK;
   // points used by the last step (before its update regenerated them)
   const int last = h->step > 0 ? (int)((h->step - 1) & 1) : 0;
+  std::vector<long long> xb_fix(X_b ? npts * D : 0);
   if (X_b)
-    CUDA_TRY(cudaMemcpyAsync(X_b, h->at<double>(last ? h->l.Xb1 : h->l.Xb0),
-                             sizeof(double) * npts * D, cudaMemcpyDeviceToHost, h->s));
+    CUDA_TRY(cudaMemcpyAsync(xb_fix.data(), h->at<long long>(last ? h->l.Xb1 : h->l.Xb0),
+                             sizeof(long long) * npts * D, cudaMemcpyDeviceToHost, h->s));
   if (U_b)
     CUDA_TRY(cudaMemcpyAsync(U_b, h->at<float>(last ? h->l.Ub1 : h->l.Ub0),
                              sizeof(float) * npts * D, cudaMemcpyDeviceToHost, h->s));
@@ -656,6 +677,7 @@ int ibm_lbm_get_lagrangian(ibm_lbm_handle* h, double* X_b, float* U_b, float* F_
     CUDA_TRY(cudaMemcpyAsync(u_b_star, h->at<float>(h->l.ubs), sizeof(float) * npts * D,
                              cudaMemcpyDeviceToHost, h->s));
   CUDA_TRY(cudaStreamSynchronize(h->s));
+  for (size_t k = 0; k < xb_fix.size(); ++k) X_b[k] = (double)xb_fix[k] / kFixScale;
   return IBMLBM_OK;
 }
 

@@ -11,7 +11,9 @@
 //   mask   [rows][wpr] u32  one bit per node: nodes within R + 2 sqrt(D) of a
 //                           particle centre (support of every Lagrangian point
 //                           and the particle interior)
-//   particle state in double, Lagrangian point data [npts][D].
+//   particle state in double, Lagrangian point data [npts][D]; point positions as
+//   32.32 fixed-point int64 (integer part = node anchor, low word = fraction), so
+//   per-point work needs no double-precision arithmetic.
 #pragma once
 
 #include <cstdint>
@@ -90,6 +92,38 @@ __device__ __forceinline__ bool step_axis(int c, int s, int n, int periodic, int
   return true;
 }
 
+// ------------------------------------------------------------ fixed point
+// Positions as int64 with 32 fractional bits: exact integer addition of offsets,
+// floor(X) = arithmetic shift, fraction exact to 2^-32 before the float conversion.
+constexpr double kFixScale = 4294967296.0;  // 2^32
+
+__host__ __device__ __forceinline__ int fix_anchor(long long v) { return (int)(v >> 32); }
+__host__ __device__ __forceinline__ float fix_frac(long long v) {
+  return (float)(unsigned)(v & 0xffffffffLL) * (1.0f / 4294967296.0f);
+}
+
+// compensated single-precision accumulator (Knuth's TwoSum on every addition)
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ void ff_add(FF& s, float x) {
+  const float t = s.hi + x;
+  const float bp = t - s.hi;
+  s.lo += (s.hi - (t - bp)) + (x - bp);
+  s.hi = t;
+}
+__device__ __forceinline__ FF ff_warp_sum(FF s) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h = __shfl_xor_sync(0xffffffffu, s.hi, o);
+    const float l = __shfl_xor_sync(0xffffffffu, s.lo, o);
+    ff_add(s, h);
+    s.lo += l;
+  }
+  return s;
+}
+__device__ __forceinline__ double ff_value(FF s) { return (double)s.hi + (double)s.lo; }
+
 // ------------------------------------------------------------ kernel arguments
 struct LbmArgs {
   Geo g;
@@ -108,16 +142,19 @@ struct IbmArgs {
   int np, nl;
   long long npts;
   double radius;     // D_p / 2
+  float radius_f;    // D_p / 2 as float
+  int rcell;         // ceil(D_p / 2)
   float dV;          // point volume (Eq. 13 reading)
   int box;           // side of the spreading box (nodes)
   const float* ustar;
   float* fib;
-  const double* Xb;  // [npts][D]
+  const long long* Xb;  // [npts][D] fixed point
   const float* Ub;   // [npts][D]
   float* Fb;         // [npts][D] sum of MDF increments
   float* dFb;        // [npts][D] increment of the current iteration
   float* ubs;        // [npts][D] D_I u*
   const double* Xc;  // [np][D]
+  const long long* Xcf;  // [np][D] fixed point centres
   double* Pint;      // [np][D]
   double* Lint;      // [np][3]
   uint32_t* status;
@@ -127,12 +164,14 @@ struct PartArgs {
   Geo g;
   int D;
   int np, nl;
-  double radius, mark_radius;
+  double radius;
+  float mark_radius;   // radius of the marked ball (float, already padded)
   double dV;
   double Mp, meff, Ip, Kt, Kr;
   double grav[3];
   int fixed;
-  const double* ref;   // [nl][D] offsets of the points from the centre
+  const long long* ref_fix;  // [nl][D] offsets of the points, fixed point
+  const float* ref_f;        // [nl][D] offsets of the points, float
   const float* Fb;     // [npts][D]
   double* X;           // [np][D]
   double* U;           // [np][D]
@@ -148,7 +187,8 @@ struct PartArgs {
   double* Pprev;       // [np][D]
   double* Lprev;       // [np][3]
   const double* Fc;    // [np][D]
-  double* Xb_out;      // [npts][D] points for the next step
+  long long* Xcf;       // [np][D] fixed-point centres (written)
+  long long* Xb_out;   // [npts][D] fixed-point points for the next step
   float* Ub_out;       // [npts][D]
   uint32_t* mask;
   uint32_t* status;

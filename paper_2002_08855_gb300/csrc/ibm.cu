@@ -31,14 +31,16 @@ struct AxisSup {
   bool ok[4];
 };
 
-// support nodes floor(X)-1 .. floor(X)+2 along one axis; nodes beyond a wall are
-// dropped, periodic axes wrap
-__device__ __forceinline__ void axis_support(double X, int n, int per, AxisSup& s) {
-  const int i0 = (int)floor(X) - 1;
+// support nodes floor(X)-1 .. floor(X)+2 along one axis of a fixed-point coordinate;
+// the offsets from X are (t - 1) - frac(X).  Nodes beyond a wall are dropped,
+// periodic axes wrap.
+__device__ __forceinline__ void axis_support(long long Xfix, int n, int per, AxisSup& s) {
+  const int i0 = fix_anchor(Xfix) - 1;
+  const float fr = fix_frac(Xfix);
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     int i = i0 + t;
-    s.w[t] = delta4((float)((double)i - X));
+    s.w[t] = delta4((float)(t - 1) - fr);
     bool ok = true;
     if (i < 0 || i >= n) {
       if (per)
@@ -109,21 +111,21 @@ __global__ void __launch_bounds__(256) ibm_spread_kernel(IbmArgs A) {
   extern __shared__ float smem[];
   const int S = A.box;
   const int cells = (D == 3) ? S * S * S : S * S;
-  float* box = smem;                                    // [D][cells]
-  float* wts = box + D * cells;                         // [nl][D][4]
+  float* box = smem;                                       // [D][cells]
+  float* wts = box + D * cells;                            // [nl][D][4]
   int* base = reinterpret_cast<int*>(wts + A.nl * D * 4);  // [nl][D]
   const int i = blockIdx.x;
   int org[3] = {0, 0, 0};
-  for (int k = 0; k < D; ++k) org[k] = (int)floor(A.Xc[(long long)i * D + k] - A.radius) - 2;
+  for (int k = 0; k < D; ++k) org[k] = fix_anchor(A.Xcf[(long long)i * D + k]) - A.rcell - 2;
 
   for (int t = threadIdx.x; t < D * cells; t += blockDim.x) box[t] = 0.0f;
   for (int t = threadIdx.x; t < A.nl * D; t += blockDim.x) {
     const long long b = (long long)i * A.nl + t / D;
-    const double X = A.Xb[b * D + (t % D)];
-    const int i0 = (int)floor(X) - 1;
-    base[t] = i0;
+    const long long X = A.Xb[b * D + (t % D)];
+    const float fr = fix_frac(X);
+    base[t] = fix_anchor(X) - 1;
 #pragma unroll
-    for (int s = 0; s < 4; ++s) wts[t * 4 + s] = delta4((float)((double)(i0 + s) - X));
+    for (int s = 0; s < 4; ++s) wts[t * 4 + s] = delta4((float)(s - 1) - fr);
   }
   __syncthreads();
 
@@ -172,37 +174,46 @@ __global__ void __launch_bounds__(256) ibm_spread_kernel(IbmArgs A) {
   }
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // Momentum and angular momentum about X_c of the fluid at the nodes strictly inside
-// each particle, with the corrected velocity u* + f_IB/2 after the MDF iterations;
-// the inside test |x - X_c|^2 < R^2 is evaluated without fused multiply-add.
+// each particle, with the corrected velocity u* + f_IB/2 after the MDF iterations.
+// The inside test |x - X_c|^2 < R^2 runs in single precision and falls back to the
+// double-precision test (without fused multiply-add) in a thin band around R^2, so
+// the set of interior nodes is the one the double-precision test gives.
 template <int D>
 __global__ void __launch_bounds__(256) interior_momentum_kernel(IbmArgs A) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= A.np) return;
-  double X[3] = {0.0, 0.0, 0.0};
-  int lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
+  int an[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
+  float fr[3] = {0.0f, 0.0f, 0.0f};
   const int n[3] = {A.g.nx, A.g.ny, A.g.nz};
   for (int k = 0; k < D; ++k) {
-    X[k] = A.Xc[(long long)i * D + k];
-    lo[k] = (int)floor(X[k] - A.radius);
-    ext[k] = (int)ceil(X[k] + A.radius) - lo[k] + 1;
+    const long long v = A.Xcf[(long long)i * D + k];
+    an[k] = fix_anchor(v);
+    fr[k] = fix_frac(v);
+    lo[k] = an[k] - A.rcell;
+    ext[k] = 2 * A.rcell + 2;
   }
-  const double R2 = __dmul_rn(A.radius, A.radius);
-  double P[3] = {0.0, 0.0, 0.0}, L[3] = {0.0, 0.0, 0.0};
+  const float R2f = A.radius_f * A.radius_f;
+  const float band = 1e-4f * R2f + 1e-5f;
+  FF P[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, L[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   const int total = ext[0] * ext[1] * ext[2];
   for (int t = lane; t < total; t += 32) {
     int gc[3] = {lo[0] + t % ext[0], lo[1] + (t / ext[0]) % ext[1], lo[2] + t / (ext[0] * ext[1])};
-    double r[3] = {0.0, 0.0, 0.0};
+    float r[3] = {0.0f, 0.0f, 0.0f};
+    for (int k = 0; k < D; ++k) r[k] = (float)(gc[k] - an[k]) - fr[k];
+    const float d2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    bool inside = d2 < R2f;
+    if (fabsf(d2 - R2f) < band) {
+      double rd[3] = {0.0, 0.0, 0.0};
+      for (int k = 0; k < D; ++k) rd[k] = (double)gc[k] - A.Xc[(long long)i * D + k];
+      const double d2d = __dadd_rn(__dadd_rn(__dmul_rn(rd[0], rd[0]), __dmul_rn(rd[1], rd[1])),
+                                   __dmul_rn(rd[2], rd[2]));
+      inside = d2d < __dmul_rn(A.radius, A.radius);
+    }
+    if (!inside) continue;
     bool ok = true;
     for (int k = 0; k < D; ++k) {
-      r[k] = (double)gc[k] - X[k];
       if (gc[k] < 0 || gc[k] >= n[k]) {
         if (A.g.per[k])
           gc[k] = ((gc[k] % n[k]) + n[k]) % n[k];
@@ -210,33 +221,36 @@ __global__ void __launch_bounds__(256) interior_momentum_kernel(IbmArgs A) {
           ok = false;
       }
     }
-    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(r[0], r[0]), __dmul_rn(r[1], r[1])), __dmul_rn(r[2], r[2]));
-    if (!ok || !(d2 < R2)) continue;
+    if (!ok) continue;
     const long long nn = (long long)gc[0] + (long long)A.g.nx * ((long long)gc[1] + (long long)A.g.ny * gc[2]);
-    double u[3] = {0.0, 0.0, 0.0};
-    for (int c = 0; c < D; ++c) u[c] = (double)(A.ustar[c * A.g.N + nn] + 0.5f * A.fib[c * A.g.N + nn]);
-    for (int c = 0; c < 3; ++c) P[c] += u[c];
-    L[0] += r[1] * u[2] - r[2] * u[1];
-    L[1] += r[2] * u[0] - r[0] * u[2];
-    L[2] += r[0] * u[1] - r[1] * u[0];
+    float u[3] = {0.0f, 0.0f, 0.0f};
+    for (int c = 0; c < D; ++c) u[c] = A.ustar[c * A.g.N + nn] + 0.5f * A.fib[c * A.g.N + nn];
+    for (int c = 0; c < D; ++c) ff_add(P[c], u[c]);
+    if (D == 3) {
+      ff_add(L[0], r[1] * u[2] - r[2] * u[1]);
+      ff_add(L[1], r[2] * u[0] - r[0] * u[2]);
+    }
+    ff_add(L[2], r[0] * u[1] - r[1] * u[0]);
   }
   for (int c = 0; c < 3; ++c) {
-    P[c] = warp_sum(P[c]);
-    L[c] = warp_sum(L[c]);
+    P[c] = ff_warp_sum(P[c]);
+    L[c] = ff_warp_sum(L[c]);
   }
   if (lane == 0) {
-    for (int c = 0; c < D; ++c) A.Pint[(long long)i * D + c] = P[c];
-    for (int c = 0; c < 3; ++c) A.Lint[(long long)i * 3 + c] = L[c];
+    for (int c = 0; c < D; ++c) A.Pint[(long long)i * D + c] = ff_value(P[c]);
+    for (int c = 0; c < 3; ++c) A.Lint[(long long)i * 3 + c] = (D == 2 && c < 2) ? 0.0 : ff_value(L[c]);
   }
 }
 
-// Newton-Euler update of one particle per warp (double precision), regeneration of its
-// Lagrangian points for the next step and marking of the nodes within mark_radius of
-// the new centre.  mode 0 only regenerates and marks (initial state).
-//   F_h = -sum_b F_b dV, T_h = -sum_b r_b x F_b dV                 (Eq. 14-15)
+// Newton-Euler update of one particle per warp, regeneration of its Lagrangian points
+// for the next step and marking of the nodes within mark_radius of the new centre.
+// mode 0 only regenerates and marks (initial state, new particle state).
+//   F_h = -dV sum_b F_b, T_h = -dV sum_b r_b x F_b     (Eq. 14-15; compensated sums)
 //   (M_p + K) a^n - K a^{n-1} = (F_h^n + F_h^{n-1})/2 + F_c + (P_int^n - P_int^{n-1})
 //                              + (M_p - rho_f V_p) g
 //   U^{n+1} = U^n + a^n, X^{n+1} = X^n + (U^n + U^{n+1})/2; rotation alike with I_p, K_r.
+// Double precision only for the per-particle integration by lane 0; points are
+// regenerated with 32.32 fixed-point additions and single-precision velocities.
 template <int D>
 __global__ void __launch_bounds__(256) particle_update_kernel(PartArgs A, int mode,
                                                               int have_prev) {
@@ -244,25 +258,39 @@ __global__ void __launch_bounds__(256) particle_update_kernel(PartArgs A, int mo
   const int lane = threadIdx.x & 31;
   if (i >= A.np) return;
   const long long pi = i;
+  double fh[3] = {0.0, 0.0, 0.0}, th[3] = {0.0, 0.0, 0.0};
   if (mode == 1) {
-    double fh[3] = {0.0, 0.0, 0.0}, th[3] = {0.0, 0.0, 0.0};
+    FF sF[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, sT[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     for (int k = lane; k < A.nl; k += 32) {
       const long long b = pi * A.nl + k;
-      double r[3] = {0.0, 0.0, 0.0}, F[3] = {0.0, 0.0, 0.0};
+      float r[3] = {0.0f, 0.0f, 0.0f}, F[3] = {0.0f, 0.0f, 0.0f};
       for (int c = 0; c < D; ++c) {
-        r[c] = A.ref[k * D + c];
-        F[c] = (double)A.Fb[b * D + c];
-        fh[c] -= F[c] * A.dV;
+        r[c] = A.ref_f[k * D + c];
+        F[c] = A.Fb[b * D + c];
+        ff_add(sF[c], F[c]);
       }
-      th[0] -= (r[1] * F[2] - r[2] * F[1]) * A.dV;
-      th[1] -= (r[2] * F[0] - r[0] * F[2]) * A.dV;
-      th[2] -= (r[0] * F[1] - r[1] * F[0]) * A.dV;
+      if (D == 3) {
+        ff_add(sT[0], r[1] * F[2] - r[2] * F[1]);
+        ff_add(sT[1], r[2] * F[0] - r[0] * F[2]);
+      }
+      ff_add(sT[2], r[0] * F[1] - r[1] * F[0]);
     }
     for (int c = 0; c < 3; ++c) {
-      fh[c] = warp_sum(fh[c]);
-      th[c] = warp_sum(th[c]);
+      sF[c] = ff_warp_sum(sF[c]);
+      sT[c] = ff_warp_sum(sT[c]);
     }
     if (lane == 0) {
+      for (int c = 0; c < 3; ++c) {
+        fh[c] = -A.dV * ff_value(sF[c]);
+        th[c] = -A.dV * ff_value(sT[c]);
+      }
+    }
+  }
+  // lane 0: integrate (mode 1) and publish the centre in fixed point
+  long long xf[3] = {0, 0, 0};
+  float uf[3] = {0.0f, 0.0f, 0.0f}, of[3] = {0.0f, 0.0f, 0.0f};
+  if (lane == 0) {
+    if (mode == 1) {
       bool bad = false;
       for (int c = 0; c < D; ++c) {
         const long long o = pi * D + c;
@@ -293,15 +321,15 @@ __global__ void __launch_bounds__(256) particle_update_kernel(PartArgs A, int mo
           A.Om[o] += al;
         }
       }
-      const int n[3] = {A.g.nx, A.g.ny, A.g.nz};
+      const int nn[3] = {A.g.nx, A.g.ny, A.g.nz};
       for (int c = 0; c < D; ++c) {
         double& x = A.X[pi * D + c];
         if (A.g.per[c]) {
-          if (x >= n[c] - 0.5)
-            x -= n[c];
+          if (x >= nn[c] - 0.5)
+            x -= nn[c];
           else if (x < -0.5)
-            x += n[c];
-        } else if (!(x >= -0.5 && x < n[c] - 0.5)) {
+            x += nn[c];
+        } else if (!(x >= -0.5 && x < nn[c] - 0.5)) {
           atomicOr(A.status, ST_OUT_OF_DOMAIN);
         }
         if (!isfinite(x) || !isfinite(A.U[pi * D + c])) bad = true;
@@ -310,36 +338,48 @@ __global__ void __launch_bounds__(256) particle_update_kernel(PartArgs A, int mo
         if (!isfinite(A.Om[pi * 3 + c])) bad = true;
       if (bad) atomicOr(A.status, ST_NONFINITE);
     }
-    __syncwarp();
+    for (int c = 0; c < D; ++c) {
+      const double x = A.X[pi * D + c];
+      xf[c] = isfinite(x) ? __double2ll_rn(x * kFixScale) : 0;
+      A.Xcf[pi * D + c] = xf[c];
+      uf[c] = (float)A.U[pi * D + c];
+    }
+    for (int c = 0; c < 3; ++c) of[c] = (D == 2 && c < 2) ? 0.0f : (float)A.Om[pi * 3 + c];
   }
-  double X[3] = {0.0, 0.0, 0.0}, U[3] = {0.0, 0.0, 0.0}, Om[3] = {0.0, 0.0, 0.0};
-  for (int c = 0; c < D; ++c) {
-    X[c] = A.X[pi * D + c];
-    U[c] = A.U[pi * D + c];
+  for (int c = 0; c < 3; ++c) {
+    xf[c] = __shfl_sync(0xffffffffu, xf[c], 0);
+    uf[c] = __shfl_sync(0xffffffffu, uf[c], 0);
+    of[c] = __shfl_sync(0xffffffffu, of[c], 0);
   }
-  for (int c = 0; c < 3; ++c) Om[c] = A.Om[pi * 3 + c];
-  if (D == 2) Om[0] = Om[1] = 0.0;
+  // regenerate the points: X_b = X_c + r_b (fixed point), U_b = U_c + Omega x r_b
   for (int k = lane; k < A.nl; k += 32) {
     const long long b = pi * A.nl + k;
-    double r[3] = {0.0, 0.0, 0.0};
-    for (int c = 0; c < D; ++c) r[c] = A.ref[k * D + c];
-    const double w[3] = {Om[1] * r[2] - Om[2] * r[1], Om[2] * r[0] - Om[0] * r[2],
-                         Om[0] * r[1] - Om[1] * r[0]};
+    float r[3] = {0.0f, 0.0f, 0.0f};
+    for (int c = 0; c < D; ++c) r[c] = A.ref_f[k * D + c];
+    const float w[3] = {of[1] * r[2] - of[2] * r[1], of[2] * r[0] - of[0] * r[2],
+                        of[0] * r[1] - of[1] * r[0]};
     for (int c = 0; c < D; ++c) {
-      A.Xb_out[b * D + c] = X[c] + r[c];
-      A.Ub_out[b * D + c] = (float)(U[c] + w[c]);
+      A.Xb_out[b * D + c] = xf[c] + A.ref_fix[k * D + c];
+      A.Ub_out[b * D + c] = uf[c] + w[c];
     }
   }
-  // mark the nodes of the ball |x - X_c| <= mark_radius, row by row
-  const double Rm = A.mark_radius, Rm2 = Rm * Rm;
-  const int ylo = (int)ceil(X[1] - Rm), yhi = (int)floor(X[1] + Rm);
-  const int zlo = (D == 3) ? (int)ceil(X[2] - Rm) : 0, zhi = (D == 3) ? (int)floor(X[2] + Rm) : 0;
-  const int ey = yhi - ylo + 1, ez = zhi - zlo + 1;
+  // mark the nodes of the ball |x - X_c| <= mark_radius, row by row (single precision
+  // relative to the centre's anchor node; the radius carries a safety margin)
+  int an[3] = {0, 0, 0};
+  float fr[3] = {0.0f, 0.0f, 0.0f};
+  for (int c = 0; c < D; ++c) {
+    an[c] = fix_anchor(xf[c]);
+    fr[c] = fix_frac(xf[c]);
+  }
+  const float Rm = A.mark_radius, Rm2 = Rm * Rm;
+  const int rr = (int)ceilf(Rm) + 1;
+  const int ey = 2 * rr + 1, ez = (D == 3) ? 2 * rr + 1 : 1;
   for (int t = lane; t < ey * ez; t += 32) {
-    int gy = ylo + t % ey, gz = zlo + t / ey;
-    const double dy = gy - X[1], dz = (D == 3) ? gz - X[2] : 0.0;
-    const double rem = Rm2 - dy * dy - dz * dz;
-    if (rem < 0.0) continue;
+    const int oy = t % ey - rr, oz = (D == 3) ? t / ey - rr : 0;
+    const float dy = (float)oy - fr[1], dz = (D == 3) ? (float)oz - fr[2] : 0.0f;
+    const float rem = Rm2 - dy * dy - dz * dz;
+    if (rem < 0.0f) continue;
+    int gy = an[1] + oy, gz = (D == 3) ? an[2] + oz : 0;
     if (gy < 0 || gy >= A.g.ny) {
       if (!A.g.per[1]) continue;
       gy = ((gy % A.g.ny) + A.g.ny) % A.g.ny;
@@ -348,8 +388,8 @@ __global__ void __launch_bounds__(256) particle_update_kernel(PartArgs A, int mo
       if (!A.g.per[2]) continue;
       gz = ((gz % A.g.nz) + A.g.nz) % A.g.nz;
     }
-    const double h = sqrt(rem);
-    int x0 = (int)ceil(X[0] - h), x1 = (int)floor(X[0] + h);
+    const float h = sqrtf(rem);
+    int x0 = an[0] + (int)ceilf(fr[0] - h), x1 = an[0] + (int)floorf(fr[0] + h);
     uint32_t* row = A.mask + ((long long)gy + (long long)A.g.ny * gz) * A.g.wpr;
     if (A.g.per[0] && (x0 < 0 || x1 >= A.g.nx)) {
       for (int x = x0; x <= x1; ++x) {

@@ -184,15 +184,19 @@ struct NodeCoord {
   bool valid;
 };
 
+// 32-bit index arithmetic (rows < 2^31); only the flat node index is 64-bit
 __device__ __forceinline__ NodeCoord node_coord(const Geo& g, int cpr) {
   NodeCoord c;
-  const int chunk = blockIdx.x % cpr;
-  c.row = blockIdx.x / cpr;
-  c.x = chunk * kLbmBlock + threadIdx.x;
-  c.y = (int)(c.row % g.ny);
-  c.z = (int)(c.row / g.ny);
+  const unsigned b = blockIdx.x, ucpr = (unsigned)cpr, uny = (unsigned)g.ny;
+  const unsigned row = b / ucpr;
+  const unsigned chunk = b - row * ucpr;
+  const unsigned z = row / uny;
+  c.row = row;
+  c.x = (int)(chunk * kLbmBlock + threadIdx.x);
+  c.y = (int)(row - z * uny);
+  c.z = (int)z;
   c.valid = c.x < g.nx;
-  c.n = (long long)c.x + (long long)g.nx * c.row;
+  c.n = (long long)c.x + (long long)g.nx * (long long)row;
   return c;
 }
 

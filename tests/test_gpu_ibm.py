@@ -50,7 +50,7 @@ def test_one_step_lagrangian_forces(dim, shape, per, xc, D, nl):
     sim.step(1)
     ref.step(1)
     lg, lo = sim.get_lagrangian(), ref.get_lagrangian()
-    assert np.abs(lg["X_b"] - lo["X_b"]).max() < 1e-12
+    assert np.abs(lg["X_b"] - lo["X_b"]).max() < 1e-9  # 32.32 fixed point on the GPU
     assert rel_l2(lg["U_b"], lo["U_b"]) < 1e-6
     assert rel_l2(lg["u_b_star"], lo["u_b_star"]) < 1e-5
     assert rel_l2(lg["F_b"], lo["F_b"]) < 1e-5
