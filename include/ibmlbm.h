@@ -191,6 +191,29 @@ int ibm_lbm_pair_search(int32_t dim, const int32_t* n_nodes, const int32_t* peri
                         int32_t max_neighbors, void* d_scratch, size_t scratch_bytes,
                         int32_t* d_pairs, int64_t cap, int64_t* h_count, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Pair search that allocates nothing (no counterpart in the paper; it is an
+ * interface for callers, not part of the method).  Same arguments and results as
+ * ibm_lbm_pair_search, but the cell and neighbour lists live in a fixed 16 MiB
+ * device array inside this library instead of caller-provided scratch, and the call
+ * makes no cudaMalloc, cudaFree or other allocating call.  It is meant for callers
+ * that cannot provide or allocate device scratch: code without access to a CUDA
+ * allocator, code running while another thread captures a graph in global mode,
+ * code that must not pay the implicit synchronisation of cudaMalloc/cudaFree.
+ *   - A problem whose scratch (cells, per-particle lists) exceeds 16 MiB returns
+ *     IBMLBM_ERR_CAPACITY and writes nothing; use ibm_lbm_pair_search for it.
+ *   - Every GPU that loads the array keeps the 16 MiB until the process exits.
+ *   - All calls on a device share the array and it keeps the last call's contents
+ *     (counters and the status word are cleared on the stream at each call); calls
+ *     that overlap on the GPU race on it.  Order them on one stream.
+ *   - The first call on a device (with that device current) looks up the array's
+ *     device address and caches it; make that first call before any stream capture.
+ * Synchronises the stream before returning. */
+int ibm_lbm_pair_search_static(int32_t dim, const int32_t* n_nodes, const int32_t* periodic,
+                               double diameter, double zeta, int32_t n, const double* d_X,
+                               int32_t max_neighbors, int32_t* d_pairs, int64_t cap,
+                               int64_t* h_count, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -103,6 +103,9 @@ SIGNATURES = {
     "ibm_lbm_pair_search": (C.c_int, [C.c_int32, _ip, _ip, C.c_double, C.c_double, C.c_int32,
                                       _vp, C.c_int32, _vp, C.c_size_t, _vp, C.c_int64, _i64p,
                                       _vp]),
+    "ibm_lbm_pair_search_static": (C.c_int, [C.c_int32, _ip, _ip, C.c_double, C.c_double,
+                                             C.c_int32, _vp, C.c_int32, _vp, C.c_int64, _i64p,
+                                             _vp]),
 }
 
 
@@ -311,4 +314,31 @@ def pair_search(dim: int, n_nodes, periodic, diameter: float, zeta: float, X,
             cap = int(cnt.value)
             continue
         _check(rc, "pair_search")
+        return pairs[: cnt.value].cpu().numpy()
+
+
+def pair_search_static(dim: int, n_nodes, periodic, diameter: float, zeta: float, X,
+                       max_neighbors: int = 0, stream=None, cap=None) -> np.ndarray:
+    """Pair search through the entry point that allocates nothing on the library side
+    (its lists live in a fixed 16 MiB device array); same result as pair_search."""
+    import torch
+
+    X = torch.as_tensor(np.asarray(X, dtype=np.float64), device="cuda").reshape(-1, dim).contiguous()
+    n = X.shape[0]
+    nn = np.ascontiguousarray((list(n_nodes) + [1, 1, 1])[:3], dtype=np.int32)
+    per = np.ascontiguousarray((list(periodic) + [0, 0, 0])[:3], dtype=np.int32)
+    s = stream if stream is not None else torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    cap = max(16, n * 8) if cap is None else cap
+    while True:
+        pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device="cuda")
+        cnt = C.c_int64(0)
+        rc = lib().ibm_lbm_pair_search_static(dim, _ptr(nn, C.c_int32), _ptr(per, C.c_int32),
+                                              diameter, zeta, n, C.c_void_p(X.data_ptr()),
+                                              max_neighbors, C.c_void_p(pairs.data_ptr()), cap,
+                                              C.byref(cnt), C.c_void_p(s.cuda_stream))
+        if rc == -7 and cnt.value > cap:
+            cap = int(cnt.value)
+            continue
+        _check(rc, "pair_search_static")
         return pairs[: cnt.value].cpu().numpy()

@@ -769,6 +769,13 @@ void ibm_lbm_destroy(ibm_lbm_handle* h) {
 
 const char* ibm_lbm_last_error(void) { return g_err.c_str(); }
 
+}  // extern "C"
+
+// lets other translation units report through ibm_lbm_last_error()
+void ibmlbm::set_last_error(const std::string& msg) { g_err = msg; }
+
+extern "C" {
+
 // ------------------------------------------------------ standalone pair search
 namespace {
 struct PairScratch {

@@ -1,6 +1,8 @@
 // Host-side launchers of the IB-LBM kernels (internal to libibmlbm.so).
 #pragma once
 
+#include <string>
+
 #include "common.cuh"
 
 namespace ibmlbm {
@@ -27,5 +29,8 @@ cudaError_t launch_pair_cells(const PairArgs& A, cudaStream_t s);   // 3 kernels
 cudaError_t launch_pair_contacts(const PairArgs& A, cudaStream_t s);
 cudaError_t launch_pair_compact(const PairArgs& A, int* pairs, long long cap, cudaStream_t s);
 cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t s);
+
+// sets the calling thread's text for ibm_lbm_last_error()
+void set_last_error(const std::string& msg);
 
 }  // namespace ibmlbm
