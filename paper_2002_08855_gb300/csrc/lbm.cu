@@ -52,8 +52,16 @@ __device__ __forceinline__ bool neighbour(const Geo& g, int a, int s, int x, int
   return true;
 }
 
-// pre-collision PDFs f_a(x) of the current time under the layout of the given parity
-template <class L, int PARITY>
+// offset of the neighbour x - s*e_a for a node whose whole neighbourhood is inside
+template <class L>
+__device__ __forceinline__ long long inner_offset(const Geo& g, int a, int s) {
+  return -(long long)s * ((long long)L::e(a, 0) + (long long)g.nx * L::e(a, 1) +
+                          (long long)g.nx * g.ny * L::e(a, 2));
+}
+
+// pre-collision PDFs f_a(x) of the current time under the layout of the given parity;
+// INNER: the node is at least one node away from every domain face
+template <class L, int PARITY, bool INNER = false>
 __device__ __forceinline__ void load_pdfs(const Geo& g, const float* __restrict__ f, int x,
                                           int y, int z, long long n, float (&fa)[L::Q]) {
   const long long N = g.N;
@@ -61,6 +69,8 @@ __device__ __forceinline__ void load_pdfs(const Geo& g, const float* __restrict_
   for (int a = 0; a < L::Q; ++a) {
     if (PARITY == 0 || a == 0) {
       fa[a] = f[a * N + n];
+    } else if (INNER) {
+      fa[a] = f[opp<L>(a) * N + n + inner_offset<L>(g, a, 1)];
     } else {
       long long src;
       if (neighbour<L>(g, a, 1, x, y, z, n, src))
@@ -91,7 +101,7 @@ __device__ __forceinline__ void put_pdfs(const Geo& g, float* __restrict__ f, in
 }
 
 // post-collision store of the given parity (after which the opposite parity holds)
-template <class L, int PARITY>
+template <class L, int PARITY, bool INNER = false>
 __device__ __forceinline__ void store_post(const Geo& g, float* __restrict__ f, int x, int y,
                                            int z, long long n, const float (&fa)[L::Q]) {
   const long long N = g.N;
@@ -101,6 +111,8 @@ __device__ __forceinline__ void store_post(const Geo& g, float* __restrict__ f, 
       f[n] = fa[0];
     } else if (PARITY == 0) {
       f[opp<L>(a) * N + n] = fa[a];
+    } else if (INNER) {
+      f[a * N + n + inner_offset<L>(g, a, -1)] = fa[a];
     } else {
       long long dst;
       if (neighbour<L>(g, a, -1, x, y, z, n, dst))
@@ -202,41 +214,60 @@ __device__ __forceinline__ NodeCoord node_coord(const Geo& g, int cpr) {
 
 // ------------------------------------------------------------------ kernels
 
-// One full time step on every node: read f (AA parity), add the IB force on
-// flagged nodes (and clear it), collide, stream in place.  Clears the mask words.
+// whole block (one row segment) at least one node away from every domain face
+__device__ __forceinline__ bool block_inner(const Geo& g, int x0, int y, int z, int dim) {
+  return x0 >= 1 && x0 + kLbmBlock <= g.nx - 1 && y >= 1 && y <= g.ny - 2 &&
+         (dim == 2 || (z >= 1 && z <= g.nz - 2));
+}
+
+template <class L, int PARITY, bool INNER>
+__device__ __forceinline__ void step_node(const LbmArgs& A, const NodeCoord& c) {
+  float* __restrict__ f = A.f;
+  float* __restrict__ fib = A.fib;
+  const long long N = A.g.N;
+  float fa[L::Q];
+  float fv[3] = {0.0f, 0.0f, 0.0f};
+  // the IB force is read for every node together with the PDFs (one memory latency);
+  // it is zero wherever no Lagrangian point spread into the node
+  load_pdfs<L, PARITY, INNER>(A.g, f, c.x, c.y, c.z, c.n, fa);
+#pragma unroll
+  for (int k = 0; k < L::dim; ++k) fv[k] = fib[k * N + c.n];
+  float F[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) F[k] = A.body[k] + fv[k];
+  collide<L>(fa, F, A.omega, A.kforce);
+  store_post<L, PARITY, INNER>(A.g, f, c.x, c.y, c.z, c.n, fa);
+#pragma unroll
+  for (int k = 0; k < L::dim; ++k)
+    if (fv[k] != 0.0f) fib[k * N + c.n] = 0.0f;
+}
+
+// One full time step on every node: read f (AA parity) and the IB force, collide,
+// stream in place, clear the IB force.
 template <class L, int PARITY>
 __global__ void __launch_bounds__(kLbmBlock) lbm_step_kernel(LbmArgs A, int cpr) {
   const NodeCoord c = node_coord(A.g, cpr);
-  const int wi = c.x >> 5;
-  uint32_t word = 0u;
-  if (wi < A.g.wpr) word = A.mask[c.row * A.g.wpr + wi];
-  const bool flagged = c.valid && ((word >> (c.x & 31)) & 1u);
-  if (c.valid) {
-    float fa[L::Q];
-    load_pdfs<L, PARITY>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
-    float F[3] = {A.body[0], A.body[1], A.body[2]};
-    if (flagged) {
-#pragma unroll
-      for (int k = 0; k < L::dim; ++k) {
-        float* p = A.fib + k * A.g.N + c.n;
-        F[k] += *p;
-        *p = 0.0f;
-      }
-    }
-    collide<L>(fa, F, A.omega, A.kforce);
-    store_post<L, PARITY>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
+  if (PARITY == 1 && block_inner(A.g, c.x - (int)threadIdx.x, c.y, c.z, L::dim)) {
+    step_node<L, PARITY, true>(A, c);
+    return;
   }
-  __syncwarp();
-  if ((c.x & 31) == 0 && wi < A.g.wpr && word) A.mask[c.row * A.g.wpr + wi] = 0u;
+  if (!c.valid) return;
+  step_node<L, PARITY, false>(A, c);
 }
 
 // u* = sum_a e_a f_a (Eq. 5) on flagged nodes only.
+// The mask is consumed here: each warp clears its word after reading it, and the
+// particle update marks the nodes of the next step.
 template <class L, int PARITY>
 __global__ void __launch_bounds__(kLbmBlock) lbm_moments_kernel(LbmArgs A, int cpr) {
   const NodeCoord c = node_coord(A.g, cpr);
   const int wi = c.x >> 5;
-  if (wi >= A.g.wpr) return;
-  const uint32_t word = A.mask[c.row * A.g.wpr + wi];
+  if (wi >= A.g.wpr) return;  // whole warp: a warp covers exactly one mask word
+  uint32_t* wp = A.mask + c.row * A.g.wpr + wi;
+  const uint32_t word = *wp;
+  if (!word) return;  // whole warp
+  __syncwarp();
+  if ((c.x & 31) == 0) *wp = 0u;
   if (!c.valid || !((word >> (c.x & 31)) & 1u)) return;
   float fa[L::Q], us[3], s1;
   load_pdfs<L, PARITY>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
