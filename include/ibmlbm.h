@@ -153,11 +153,11 @@ int ibm_lbm_get_launch_count(ibm_lbm_handle* h, int64_t* n);
  * ms[IBMLBM_PART_COUNT], in the order of enum ibm_lbm_part; the parts follow the
  * per-part timing of Sec. 6.2 (Fig. 10, Fig. 16). */
 enum ibm_lbm_part {
-  IBMLBM_PART_MACRO = 0,      /* lbm_moments on the flagged nodes                */
-  IBMLBM_PART_IBM = 1,        /* interpolation, spreading, interior momentum     */
-  IBMLBM_PART_COLLIDE = 2,    /* fused collision + streaming + bounce-back       */
-  IBMLBM_PART_PAIRS = 3,      /* cell lists, pair search and contact force       */
-  IBMLBM_PART_PARTICLES = 4,  /* Newton-Euler update, point regeneration, marks  */
+  IBMLBM_PART_MACRO = 0,      /* lbm_moments on the flagged nodes                  */
+  IBMLBM_PART_IBM = 1,        /* interpolation, spreading, F_h/T_h, interior sums  */
+  IBMLBM_PART_COLLIDE = 2,    /* fused collision + streaming + bounce-back         */
+  IBMLBM_PART_PAIRS = 3,      /* cell buckets, contact force, Newton-Euler update  */
+  IBMLBM_PART_PARTICLES = 4,  /* regeneration of the points, node marks            */
   IBMLBM_PART_COUNT = 5
 };
 int ibm_lbm_time_parts(ibm_lbm_handle* h, int32_t n_steps, double* ms);

@@ -2,8 +2,9 @@
 // workspace layout, the per-step kernel sequence and its CUDA-graph replay.
 //
 // One step (Sec. 3 step list, Sec. 6.2 part list; explicit particle coupling):
-//   lbm_moments -> [ibm_interp -> ibm_spread] x M -> interior_momentum -> lbm_step
-//   -> pair cells (count, scan, fill) -> pair contacts -> particle_update
+//   lbm_moments -> [ibm_interp -> ibm_spread] x M -> ibm_forces (F_h, T_h, interior
+//   momentum) -> lbm_step -> pair cells (buckets) -> pair contacts + particle update
+//   -> regen (points and node marks of the next step)
 // All of it is enqueued on the caller's stream; after the first step each step
 // parity is captured once as a CUDA graph and replayed.
 #include <cmath>
@@ -62,9 +63,9 @@ struct Derived {
 
 struct Layout {
   size_t f, ustar, fib, mask;
-  size_t X, U, Om, Fh, Th, Fhp, Thp, acc, alp, Pint, Lint, Pprev, Lprev, Fc;
-  size_t ref_fix, ref_f, Xcf, Xb0, Xb1, Ub0, Ub1, Fb, dFb, ubs;
-  size_t cell_count, cell_start, sorted, nbr, nbr_count, gt, pairs, status;
+  size_t X0, X1, U, Om, Fh, Th, FhN, ThN, acc, alp, Pint, Lint, Pprev, Lprev, Fc;
+  size_t Uf, Omf, ref_fix, ref_f, Xcf, Xb0, Xb1, Ub0, Ub1, Fb, dFb, ubs, ubox;
+  size_t cell_count, cell_ids, nbr, nbr_count, gt, pairs, status;
   size_t total;
 };
 
@@ -164,13 +165,16 @@ Layout carve(const ibm_lbm_config* c, const Derived& d) {
   l.ustar = cv.take(sizeof(float) * D * N);
   l.fib = cv.take(sizeof(float) * D * N);
   l.mask = cv.take(sizeof(uint32_t) * (size_t)d.g.rows * d.g.wpr);
-  l.X = cv.take(sizeof(double) * np * D);
+  l.X0 = cv.take(sizeof(double) * np * D);
+  l.X1 = cv.take(sizeof(double) * np * D);
   l.U = cv.take(sizeof(double) * np * D);
   l.Om = cv.take(sizeof(double) * np * 3);
   l.Fh = cv.take(sizeof(double) * np * D);
   l.Th = cv.take(sizeof(double) * np * 3);
-  l.Fhp = cv.take(sizeof(double) * np * D);
-  l.Thp = cv.take(sizeof(double) * np * 3);
+  l.FhN = cv.take(sizeof(double) * np * D);
+  l.ThN = cv.take(sizeof(double) * np * 3);
+  l.Uf = cv.take(sizeof(float) * np * D);
+  l.Omf = cv.take(sizeof(float) * np * 3);
   l.acc = cv.take(sizeof(double) * np * D);
   l.alp = cv.take(sizeof(double) * np * 3);
   l.Pint = cv.take(sizeof(double) * np * D);
@@ -188,10 +192,11 @@ Layout carve(const ibm_lbm_config* c, const Derived& d) {
   l.Fb = cv.take(sizeof(float) * npts * D);
   l.dFb = cv.take(sizeof(float) * npts * D);
   l.ubs = cv.take(sizeof(float) * npts * D);
+  // 2D: u* of each particle's node box (box x (box + 1) per component)
+  l.ubox = cv.take(D == 2 ? sizeof(float) * np * 2 * (size_t)d.box * (d.box + 1) : 0);
   const size_t ncells = (size_t)d.nc[0] * d.nc[1] * d.nc[2];
   l.cell_count = cv.take(sizeof(int) * ncells);
-  l.cell_start = cv.take(sizeof(int) * (ncells + 1));
-  l.sorted = cv.take(sizeof(int) * np);
+  l.cell_ids = cv.take(sizeof(int) * ncells * cell_capacity(c->n_particles, (long long)ncells));
   l.nbr = cv.take(sizeof(int) * np * d.kmax);
   l.nbr_count = cv.take(sizeof(int) * np);
   l.gt = cv.take(sizeof(int) * 2 * (np + 1));
@@ -253,6 +258,8 @@ struct ibm_lbm_handle {
     for (int k = 0; k < 3; ++k) a.body[k] = (k < d.D) ? (float)cfg.body_force[k] : 0.0f;
     return a;
   }
+  double* X(int parity) const { return at<double>(parity ? l.X1 : l.X0); }
+
   IbmArgs ibm(int parity) const {
     IbmArgs a{};
     a.g = d.g;
@@ -267,59 +274,47 @@ struct ibm_lbm_handle {
     a.box = d.box;
     a.ustar = at<float>(l.ustar);
     a.fib = at<float>(l.fib);
+    a.f = at<float>(l.f);
+    a.parity = parity;
+    a.ubox = at<float>(l.ubox);
     a.Xb = at<long long>(parity ? l.Xb1 : l.Xb0);
     a.Ub = at<float>(parity ? l.Ub1 : l.Ub0);
     a.Fb = at<float>(l.Fb);
     a.dFb = at<float>(l.dFb);
     a.ubs = at<float>(l.ubs);
-    a.Xc = at<double>(l.X);
+    a.Xc = X(parity);
     a.Xcf = at<long long>(l.Xcf);
+    a.ref_f = at<float>(l.ref_f);
     a.Pint = at<double>(l.Pint);
     a.Lint = at<double>(l.Lint);
+    a.FhN = at<double>(l.FhN);
+    a.ThN = at<double>(l.ThN);
     a.status = at<uint32_t>(l.status);
     return a;
   }
-  PartArgs part(int out_parity) const {
-    PartArgs a{};
+  // regeneration into the point buffer of the given parity, from the centres of
+  // the same parity (init) or from the fixed-point centres the update wrote
+  RegenArgs regen(int parity) const {
+    RegenArgs a{};
     a.g = d.g;
     a.D = d.D;
     a.np = cfg.n_particles;
     a.nl = cfg.n_lag;
-    a.radius = d.radius;
     a.mark_radius = d.mark_radius;
-    a.dV = d.dV;
-    a.Mp = d.Mp;
-    a.meff = d.meff;
-    a.Ip = d.Ip;
-    a.Kt = d.Kt;
-    a.Kr = d.Kr;
-    for (int k = 0; k < 3; ++k) a.grav[k] = cfg.gravity[k];
-    a.fixed = cfg.fixed_particles;
     a.ref_fix = at<long long>(l.ref_fix);
     a.ref_f = at<float>(l.ref_f);
-    a.Xcf = at<long long>(l.Xcf);
-    a.Fb = at<float>(l.Fb);
-    a.X = at<double>(l.X);
+    a.X = X(parity);
     a.U = at<double>(l.U);
     a.Om = at<double>(l.Om);
-    a.Fh = at<double>(l.Fh);
-    a.Th = at<double>(l.Th);
-    a.Fhp = at<double>(l.Fhp);
-    a.Thp = at<double>(l.Thp);
-    a.acc = at<double>(l.acc);
-    a.alp = at<double>(l.alp);
-    a.Pint = at<double>(l.Pint);
-    a.Lint = at<double>(l.Lint);
-    a.Pprev = at<double>(l.Pprev);
-    a.Lprev = at<double>(l.Lprev);
-    a.Fc = at<double>(l.Fc);
-    a.Xb_out = at<long long>(out_parity ? l.Xb1 : l.Xb0);
-    a.Ub_out = at<float>(out_parity ? l.Ub1 : l.Ub0);
+    a.Xcf = at<long long>(l.Xcf);
+    a.Uf = at<float>(l.Uf);
+    a.Omf = at<float>(l.Omf);
+    a.Xb_out = at<long long>(parity ? l.Xb1 : l.Xb0);
+    a.Ub_out = at<float>(parity ? l.Ub1 : l.Ub0);
     a.mask = at<uint32_t>(l.mask);
-    a.status = at<uint32_t>(l.status);
     return a;
   }
-  PairArgs pairs() const {
+  PairArgs pairs(int parity, int have_prev) const {
     PairArgs a{};
     a.g = d.g;
     a.D = d.D;
@@ -336,15 +331,41 @@ struct ibm_lbm_handle {
     a.eps_pp = cfg.eps_pp;
     a.E_pp = cfg.E_pp;
     a.kmax = d.kmax;
-    a.X = at<double>(l.X);
+    a.X = X(parity);
     a.cell_count = at<int>(l.cell_count);
-    a.cell_start = at<int>(l.cell_start);
-    a.sorted = at<int>(l.sorted);
+    a.cell_ids = at<int>(l.cell_ids);
+    a.cell_cap = cell_capacity(cfg.n_particles, (long long)d.nc[0] * d.nc[1] * d.nc[2]);
     a.nbr = at<int>(l.nbr);
     a.nbr_count = at<int>(l.nbr_count);
     a.Fc = at<double>(l.Fc);
     a.gt_count = at<int>(l.gt);
     a.status = at<uint32_t>(l.status);
+    a.integrate = 1;
+    a.have_prev = have_prev;
+    PartState& p = a.ps;
+    p.Xnew = X(1 - parity);
+    p.U = at<double>(l.U);
+    p.Om = at<double>(l.Om);
+    p.Fh = at<double>(l.Fh);
+    p.Th = at<double>(l.Th);
+    p.acc = at<double>(l.acc);
+    p.alp = at<double>(l.alp);
+    p.Pprev = at<double>(l.Pprev);
+    p.Lprev = at<double>(l.Lprev);
+    p.FhN = at<double>(l.FhN);
+    p.ThN = at<double>(l.ThN);
+    p.Pint = at<double>(l.Pint);
+    p.Lint = at<double>(l.Lint);
+    p.Xcf = at<long long>(l.Xcf);
+    p.Uf = at<float>(l.Uf);
+    p.Omf = at<float>(l.Omf);
+    p.Mp = d.Mp;
+    p.meff = d.meff;
+    p.Ip = d.Ip;
+    p.Kt = d.Kt;
+    p.Kr = d.Kr;
+    for (int k = 0; k < 3; ++k) p.grav[k] = cfg.gravity[k];
+    p.fixed = cfg.fixed_particles;
     return a;
   }
 };
@@ -360,18 +381,22 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
   const LbmArgs la = h->lbm();
   const IbmArgs ia = h->ibm(parity);
   if (ev) CUDA_TRY(cudaEventRecord(ev[0], s));
-  if (particles) {
+  if (particles && h->d.D == 3) {  // 2D computes u* per particle box in the first interpolation
     CUDA_TRY(launch_lbm_moments(la, h->d.D, parity, s));
     ++k;
   }
   if (ev) CUDA_TRY(cudaEventRecord(ev[1], s));
   if (particles) {
+    if (h->d.D == 2 && h->cfg.mdf_iters == 0) {  // the interior momentum still needs box u*
+      CUDA_TRY(launch_ibm_interp(ia, 0, s));
+      ++k;
+    }
     for (int m = 1; m <= h->cfg.mdf_iters; ++m) {
       CUDA_TRY(launch_ibm_interp(ia, m, s));
       CUDA_TRY(launch_ibm_spread(ia, s));
       k += 2;
     }
-    CUDA_TRY(launch_interior_momentum(ia, s));
+    CUDA_TRY(launch_ibm_forces(ia, s));
     ++k;
   }
   if (ev) CUDA_TRY(cudaEventRecord(ev[2], s));
@@ -379,14 +404,14 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
   ++k;
   if (ev) CUDA_TRY(cudaEventRecord(ev[3], s));
   if (particles) {
-    const PairArgs pa = h->pairs();
+    const PairArgs pa = h->pairs(parity, have_prev);
     CUDA_TRY(launch_pair_cells(pa, s));
     CUDA_TRY(launch_pair_contacts(pa, s));
-    k += 4;
+    k += 3;
   }
   if (ev) CUDA_TRY(cudaEventRecord(ev[4], s));
   if (particles) {
-    CUDA_TRY(launch_particle_update(h->part(1 - parity), 1, have_prev, s));
+    CUDA_TRY(launch_regen(h->regen(1 - parity), 0, s));
     ++k;
   }
   if (ev) CUDA_TRY(cudaEventRecord(ev[5], s));
@@ -421,9 +446,10 @@ int capture_graph(ibm_lbm_handle* h, int parity) {
   return IBMLBM_OK;
 }
 
+// points and node marks of the current state (after init or a new particle state)
 int regenerate_points(ibm_lbm_handle* h) {
   if (h->cfg.n_particles == 0) return IBMLBM_OK;
-  CUDA_TRY(launch_particle_update(h->part((int)(h->step & 1)), 0, 0, h->s));
+  CUDA_TRY(launch_regen(h->regen((int)(h->step & 1)), 1, h->s));
   h->launches += 1;
   return IBMLBM_OK;
 }
@@ -468,7 +494,7 @@ int ibm_lbm_init(const ibm_lbm_config* cfg, void* d_workspace, size_t bytes, voi
         return fail(IBMLBM_ERR_INVALID_ARG, "particle centre outside the domain");
     }
   if (cfg->n_particles > 0) {
-    const size_t smem = ibm_spread_smem(d.D, cfg->n_lag, d.box);
+    const size_t smem = spread_smem(d.D, cfg->n_lag, d.box);
     if (smem > 227 * 1024)
       return fail(IBMLBM_ERR_UNSUPPORTED, "particle too large for the spreading box");
   }
@@ -495,7 +521,7 @@ int ibm_lbm_init(const ibm_lbm_config* cfg, void* d_workspace, size_t bytes, voi
   } while (0)
   INIT_TRY(cudaMemsetAsync(h->ws, 0, l.total, h->s));
   if (cfg->n_particles > 0) {
-    INIT_TRY(cudaMemcpyAsync(h->at<double>(l.X), h_centres,
+    INIT_TRY(cudaMemcpyAsync(h->at<double>(l.X0), h_centres,
                              sizeof(double) * (size_t)cfg->n_particles * d.D,
                              cudaMemcpyHostToDevice, h->s));
     const std::vector<double> ref = reference_points(d.D, cfg->n_lag, d.radius);
@@ -510,7 +536,7 @@ int ibm_lbm_init(const ibm_lbm_config* cfg, void* d_workspace, size_t bytes, voi
     INIT_TRY(cudaMemcpyAsync(h->at<float>(l.ref_f), ref_f.data(), sizeof(float) * ref_f.size(),
                              cudaMemcpyHostToDevice, h->s));
     INIT_TRY(cudaStreamSynchronize(h->s));  // host vectors go out of scope
-    INIT_TRY(prepare_ibm_spread(d.D, ibm_spread_smem(d.D, cfg->n_lag, d.box)));
+    INIT_TRY(prepare_ibm_spread(d.D, spread_smem(d.D, cfg->n_lag, d.box)));
     if (regenerate_points(h) != IBMLBM_OK) return bail(IBMLBM_ERR_CUDA);
   }
   INIT_TRY(cudaStreamSynchronize(h->s));
@@ -609,7 +635,7 @@ int ibm_lbm_set_particles(ibm_lbm_handle* h, const double* X, const double* U,
         if (!std::isfinite(x) || x < -0.5 || x >= h->d.L[k] - 0.5)
           return fail(IBMLBM_ERR_INVALID_ARG, "particle centre outside the domain");
       }
-    CUDA_TRY(cudaMemcpyAsync(h->at<double>(h->l.X), X, sizeof(double) * np * D,
+    CUDA_TRY(cudaMemcpyAsync(h->X((int)(h->step & 1)), X, sizeof(double) * np * D,
                              cudaMemcpyHostToDevice, h->s));
   }
   if (U)
@@ -636,7 +662,7 @@ int ibm_lbm_get_particles(ibm_lbm_handle* h, double* X, double* U, double* Omega
   const int np = h->cfg.n_particles, D = h->d.D;
   if (np == 0) return IBMLBM_OK;
   const size_t vb = sizeof(double) * np * D;
-  if (X) CUDA_TRY(cudaMemcpyAsync(X, h->at<double>(h->l.X), vb, cudaMemcpyDeviceToHost, h->s));
+  if (X) CUDA_TRY(cudaMemcpyAsync(X, h->X((int)(h->step & 1)), vb, cudaMemcpyDeviceToHost, h->s));
   if (U) CUDA_TRY(cudaMemcpyAsync(U, h->at<double>(h->l.U), vb, cudaMemcpyDeviceToHost, h->s));
   if (F_h) CUDA_TRY(cudaMemcpyAsync(F_h, h->at<double>(h->l.Fh), vb, cudaMemcpyDeviceToHost, h->s));
   if (F_c) CUDA_TRY(cudaMemcpyAsync(F_c, h->at<double>(h->l.Fc), vb, cudaMemcpyDeviceToHost, h->s));
@@ -708,7 +734,7 @@ int ibm_lbm_get_pairs(ibm_lbm_handle* h, int32_t* pairs, int64_t cap, int64_t* n
   const int np = h->cfg.n_particles;
   *n = 0;
   if (np == 0) return IBMLBM_OK;
-  const PairArgs pa = h->pairs();
+  const PairArgs pa = h->pairs(0, 1);
   const long long dev_cap = (long long)np * h->d.kmax / 2;
   CUDA_TRY(launch_pair_compact(pa, h->at<int>(h->l.pairs), dev_cap, h->s));
   h->launches += 2;
@@ -779,7 +805,7 @@ extern "C" {
 // ------------------------------------------------------ standalone pair search
 namespace {
 struct PairScratch {
-  size_t cell_count, cell_start, sorted, nbr, nbr_count, gt, status, total;
+  size_t cell_count, cell_ids, nbr, nbr_count, gt, status, total;
 };
 
 PairScratch pair_scratch(int D, int n, int kmax, const int* nc) {
@@ -788,8 +814,7 @@ PairScratch pair_scratch(int D, int n, int kmax, const int* nc) {
   const size_t ncells = (size_t)nc[0] * nc[1] * nc[2];
   (void)D;
   p.cell_count = cv.take(sizeof(int) * ncells);
-  p.cell_start = cv.take(sizeof(int) * (ncells + 1));
-  p.sorted = cv.take(sizeof(int) * (size_t)n);
+  p.cell_ids = cv.take(sizeof(int) * ncells * cell_capacity(n, (long long)ncells));
   p.nbr = cv.take(sizeof(int) * (size_t)n * kmax);
   p.nbr_count = cv.take(sizeof(int) * (size_t)n);
   p.gt = cv.take(sizeof(int) * 2 * ((size_t)n + 1));
@@ -867,14 +892,13 @@ int ibm_lbm_pair_search(int32_t dim, const int32_t* n_nodes, const int32_t* peri
   a.kmax = kmax;
   a.X = d_X;
   a.cell_count = reinterpret_cast<int*>(sc + ps.cell_count);
-  a.cell_start = reinterpret_cast<int*>(sc + ps.cell_start);
-  a.sorted = reinterpret_cast<int*>(sc + ps.sorted);
+  a.cell_ids = reinterpret_cast<int*>(sc + ps.cell_ids);
+  a.cell_cap = cell_capacity(n, (long long)nc[0] * nc[1] * nc[2]);
   a.nbr = reinterpret_cast<int*>(sc + ps.nbr);
   a.nbr_count = reinterpret_cast<int*>(sc + ps.nbr_count);
   a.gt_count = reinterpret_cast<int*>(sc + ps.gt);
   a.status = reinterpret_cast<uint32_t*>(sc + ps.status);
   a.Fc = nullptr;
-  CUDA_TRY(cudaMemsetAsync(a.cell_count, 0, sizeof(int) * (size_t)nc[0] * nc[1] * nc[2], s));
   CUDA_TRY(cudaMemsetAsync(a.status, 0, sizeof(uint32_t), s));
   CUDA_TRY(launch_pair_cells(a, s));
   CUDA_TRY(launch_pair_contacts(a, s));

@@ -146,53 +146,77 @@ struct IbmArgs {
   int rcell;         // ceil(D_p / 2)
   float dV;          // point volume (Eq. 13 reading)
   int box;           // side of the spreading box (nodes)
-  const float* ustar;
+  const float* ustar;    // 3D: u* on flagged nodes (lbm_moments)
   float* fib;
+  const float* f;        // 2D: the PDFs, for u* of each particle's box
+  int parity;            // 2D: AA parity of the PDFs
+  float* ubox;           // 2D: [np][2][box][box + 1] u* of each particle's box
   const long long* Xb;  // [npts][D] fixed point
   const float* Ub;   // [npts][D]
   float* Fb;         // [npts][D] sum of MDF increments
   float* dFb;        // [npts][D] increment of the current iteration
   float* ubs;        // [npts][D] D_I u*
-  const double* Xc;  // [np][D]
+  const double* Xc;  // [np][D] centres of the current step
   const long long* Xcf;  // [np][D] fixed point centres
-  double* Pint;      // [np][D]
-  double* Lint;      // [np][3]
+  const float* ref_f;    // [nl][D] offsets of the points from the centre
+  double* Pint;      // [np][D] interior momentum
+  double* Lint;      // [np][3] interior angular momentum
+  double* FhN;       // [np][D] -dV sum_b F_b of this step
+  double* ThN;       // [np][3] -dV sum_b r_b x F_b of this step
   uint32_t* status;
 };
 
-struct PartArgs {
+// Regeneration of the Lagrangian points and marking of the nodes near each particle.
+struct RegenArgs {
   Geo g;
   int D;
   int np, nl;
-  double radius;
   float mark_radius;   // radius of the marked ball (float, already padded)
-  double dV;
+  const long long* ref_fix;  // [nl][D] offsets of the points, fixed point
+  const float* ref_f;        // [nl][D] offsets of the points, float
+  const double* X;     // [np][D] (used to refresh the fixed-point centres when init != 0)
+  const double* U;     // [np][D]
+  const double* Om;    // [np][3]
+  long long* Xcf;      // [np][D] fixed-point centres
+  float* Uf;           // [np][D] single-precision velocity
+  float* Omf;          // [np][3] single-precision angular velocity
+  long long* Xb_out;   // [npts][D] fixed-point points
+  float* Ub_out;       // [npts][D]
+  uint32_t* mask;
+};
+
+// Per-particle double-precision state advanced by the contact kernel (Eq. 14-15).
+struct PartState {
+  double* Xnew;        // [np][D] centres after the step (the other buffer)
+  double* U;           // [np][D]
+  double* Om;          // [np][3]
+  double* Fh;          // [np][D] F_h of the last step (reported)
+  double* Th;          // [np][3]
+  double* acc;         // [np][D] previous linear acceleration
+  double* alp;         // [np][3] previous angular acceleration
+  double* Pprev;       // [np][D] interior momentum of the previous step
+  double* Lprev;       // [np][3]
+  const double* FhN;   // [np][D] this step's F_h
+  const double* ThN;   // [np][3]
+  const double* Pint;  // [np][D] this step's interior momentum
+  const double* Lint;  // [np][3]
+  long long* Xcf;      // [np][D] fixed-point centres for the regeneration
+  float* Uf;           // [np][D]
+  float* Omf;          // [np][3]
   double Mp, meff, Ip, Kt, Kr;
   double grav[3];
   int fixed;
-  const long long* ref_fix;  // [nl][D] offsets of the points, fixed point
-  const float* ref_f;        // [nl][D] offsets of the points, float
-  const float* Fb;     // [npts][D]
-  double* X;           // [np][D]
-  double* U;           // [np][D]
-  double* Om;          // [np][3]
-  double* Fh;          // [np][D]
-  double* Th;          // [np][3]
-  double* Fhp;         // [np][D] previous step
-  double* Thp;         // [np][3]
-  double* acc;         // [np][D] previous linear acceleration
-  double* alp;         // [np][3] previous angular acceleration
-  const double* Pint;  // [np][D] interior momentum of this step
-  const double* Lint;  // [np][3]
-  double* Pprev;       // [np][D]
-  double* Lprev;       // [np][3]
-  const double* Fc;    // [np][D]
-  long long* Xcf;       // [np][D] fixed-point centres (written)
-  long long* Xb_out;   // [npts][D] fixed-point points for the next step
-  float* Ub_out;       // [npts][D]
-  uint32_t* mask;
-  uint32_t* status;
 };
+
+// Capacity of one search-cell bucket: eight times the mean occupancy plus eight
+// (at least 16); a bucket that overflows is reported as CAPACITY.
+inline int cell_capacity(long long n, long long ncells) {
+  long long mean = (n + ncells - 1) / (ncells > 0 ? ncells : 1);
+  long long cap = 8 * mean + 8;
+  if (cap < 16) cap = 16;
+  if (cap > n && n >= 16) cap = n;
+  return (int)cap;
+}
 
 struct PairArgs {
   Geo g;
@@ -205,14 +229,17 @@ struct PairArgs {
   double c_ij, eps_pp, E_pp;
   int kmax;
   const double* X;      // [n][D]
-  int* cell_count;      // [ncells]
-  int* cell_start;      // [ncells + 1]
-  int* sorted;          // [n]
+  int* cell_count;      // [ncells], zero before the insertion
+  int* cell_ids;        // [ncells][cell_cap]
+  int cell_cap;         // bucket capacity (cell_capacity)
   int* nbr;             // [n][kmax]
   int* nbr_count;       // [n]
-  double* Fc;           // [n][D] (may be null: pair list only)
-  int* gt_count;        // [n + 1] partners j > i, then their offsets
+  double* Fc;           // [n][D] (null: pair list only)
+  int* gt_count;        // [2 (n + 1)] partners j > i, then their offsets
   uint32_t* status;
+  int integrate;        // 1: advance the particles (PartState) after the contact force
+  int have_prev;        // a previous step exists (history terms of the update)
+  PartState ps;
 };
 
 }  // namespace ibmlbm

@@ -14,6 +14,7 @@
 
 #include "common.cuh"
 #include "launch.h"
+#include "pdf_access.cuh"
 
 namespace ibmlbm {
 
@@ -174,13 +175,172 @@ __global__ void __launch_bounds__(256) ibm_spread_kernel(IbmArgs A) {
   }
 }
 
-// Momentum and angular momentum about X_c of the fluid at the nodes strictly inside
-// each particle, with the corrected velocity u* + f_IB/2 after the MDF iterations.
-// The inside test |x - X_c|^2 < R^2 runs in single precision and falls back to the
-// double-precision test (without fused multiply-add) in a thin band around R^2, so
-// the set of interior nodes is the one the double-precision test gives.
+// 2D kernels with one warp per particle and the particle's node box in shared memory
+// (kIbmWarps particles per block, box rows padded by one float against bank
+// conflicts, no block-wide barrier).
+constexpr int kIbmWarps = 8;
+
+size_t ibm_box2_smem(int box) { return sizeof(float) * 2 * (size_t)box * (box + 1) * kIbmWarps; }
+
+// Interpolation (Eq. 47), iteration m.  In the first iteration (or m = 0: box only,
+// when no forcing iteration runs) the warp computes u* (Eq. 5) of every
+// node of the particle's box from the PDFs (coalesced row loads, AA-parity layout) and
+// keeps it in the particle's box buffer; later iterations stage that buffer plus
+// f_IB/2.  Lane k then interpolates point k from shared memory.  Box nodes beyond a
+// wall hold zero, which drops them from the sum.
+template <int PARITY>
+__global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A, int m) {
+  extern __shared__ float smem_i[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int i = blockIdx.x * kIbmWarps + wib;
+  if (i >= A.np) return;  // whole warp
+  const int S = A.box, P = S + 1, cells = S * P;
+  float* box = smem_i + (size_t)wib * 2 * cells;
+  float* ub = A.ubox + (size_t)i * 2 * cells;
+  const int ox = fix_anchor(A.Xcf[(long long)i * 2 + 0]) - A.rcell - 2;
+  const int oy = fix_anchor(A.Xcf[(long long)i * 2 + 1]) - A.rcell - 2;
+  const long long N = A.g.N;
+  for (int t = lane; t < S * S; t += 32) {
+    const int r = t / S, c = t - r * S;
+    int gx = ox + c, gy = oy + r;
+    bool ok = true;
+    if (gx < 0 || gx >= A.g.nx) {
+      if (A.g.per[0]) gx = ((gx % A.g.nx) + A.g.nx) % A.g.nx; else ok = false;
+    }
+    if (gy < 0 || gy >= A.g.ny) {
+      if (A.g.per[1]) gy = ((gy % A.g.ny) + A.g.ny) % A.g.ny; else ok = false;
+    }
+    float v0 = 0.0f, v1 = 0.0f;
+    const long long n = (long long)gx + (long long)A.g.nx * gy;
+    if (m <= 1) {
+      if (ok) {
+        float fa[9], us[3], s1;
+        load_pdfs<Lat<2>, PARITY>(A.g, A.f, gx, gy, 0, n, fa);
+        moments<Lat<2>>(fa, us, s1);
+        v0 = us[0];
+        v1 = us[1];
+      }
+      ub[r * P + c] = v0;
+      ub[cells + r * P + c] = v1;
+    } else {
+      v0 = ub[r * P + c];
+      v1 = ub[cells + r * P + c];
+      if (ok) {
+        v0 += 0.5f * A.fib[n];
+        v1 += 0.5f * A.fib[N + n];
+      }
+    }
+    box[r * P + c] = v0;
+    box[cells + r * P + c] = v1;
+  }
+  if (m == 0) return;  // box u* only (no multi-direct forcing iteration this step)
+  __syncwarp();
+  for (int k = lane; k < A.nl; k += 32) {
+    const long long b = (long long)i * A.nl + k;
+    const long long Xx = A.Xb[b * 2], Xy = A.Xb[b * 2 + 1];
+    const int lx0 = fix_anchor(Xx) - 1 - ox, ly0 = fix_anchor(Xy) - 1 - oy;
+    const float rx = fix_frac(Xx), ry = fix_frac(Xy);
+    float acc0 = 0.0f, acc1 = 0.0f;
+    if (lx0 < 0 || ly0 < 0 || lx0 + 3 >= S || ly0 + 3 >= S) {
+      atomicOr(A.status, ST_CAPACITY);
+    } else {
+#pragma unroll
+      for (int sy = 0; sy < 4; ++sy) {
+        const float wy = delta4((float)(sy - 1) - ry);
+        const float* r0 = box + (ly0 + sy) * P + lx0;
+        float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+        for (int sx = 0; sx < 4; ++sx) {
+          const float wx = delta4((float)(sx - 1) - rx);
+          a0 += wx * r0[sx];
+          a1 += wx * r0[cells + sx];
+        }
+        acc0 += wy * a0;
+        acc1 += wy * a1;
+      }
+    }
+    const float d0 = 2.0f * (A.Ub[b * 2] - acc0), d1 = 2.0f * (A.Ub[b * 2 + 1] - acc1);
+    A.dFb[b * 2] = d0;
+    A.dFb[b * 2 + 1] = d1;
+    if (m == 1) {
+      A.Fb[b * 2] = d0;
+      A.Fb[b * 2 + 1] = d1;
+      A.ubs[b * 2] = acc0;
+      A.ubs[b * 2 + 1] = acc1;
+    } else {
+      A.Fb[b * 2] += d0;
+      A.Fb[b * 2 + 1] += d1;
+    }
+  }
+}
+
+// Spreading (Eq. 48): each lane spreads its points into the box with shared-memory
+// atomics; then the warp adds the non-zero box cells to f_IB with one global atomic
+// per cell and component.
+__global__ void __launch_bounds__(kIbmWarps * 32) ibm_spread2_kernel(IbmArgs A) {
+  extern __shared__ float smem2[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int i = blockIdx.x * kIbmWarps + wib;
+  if (i >= A.np) return;  // whole warp
+  const int S = A.box, P = S + 1, cells = S * P;
+  float* box = smem2 + (size_t)wib * 2 * cells;
+  for (int t = lane; t < 2 * cells; t += 32) box[t] = 0.0f;
+  const int ox = fix_anchor(A.Xcf[(long long)i * 2 + 0]) - A.rcell - 2;
+  const int oy = fix_anchor(A.Xcf[(long long)i * 2 + 1]) - A.rcell - 2;
+  __syncwarp();
+  for (int k = lane; k < A.nl; k += 32) {
+    const long long b = (long long)i * A.nl + k;
+    const long long Xx = A.Xb[b * 2], Xy = A.Xb[b * 2 + 1];
+    const float fx = A.dFb[b * 2] * A.dV, fy = A.dFb[b * 2 + 1] * A.dV;
+    const int bx = fix_anchor(Xx) - 1, by = fix_anchor(Xy) - 1;
+    const float rx = fix_frac(Xx), ry = fix_frac(Xy);
+    if (bx - ox < 0 || by - oy < 0 || bx - ox + 3 >= S || by - oy + 3 >= S) {
+      atomicOr(A.status, ST_CAPACITY);
+      continue;
+    }
+    float wx[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) wx[t] = delta4((float)(t - 1) - rx);
+#pragma unroll
+    for (int sy = 0; sy < 4; ++sy) {
+      const int gy = by + sy;
+      if (!A.g.per[1] && (gy < 0 || gy >= A.g.ny)) continue;
+      const float wy = delta4((float)(sy - 1) - ry);
+      float* r0 = box + (gy - oy) * P + (bx - ox);
+#pragma unroll
+      for (int sx = 0; sx < 4; ++sx) {
+        const int gx = bx + sx;
+        if (!A.g.per[0] && (gx < 0 || gx >= A.g.nx)) continue;
+        const float w = wx[sx] * wy;
+        atomicAdd(r0 + sx, fx * w);
+        atomicAdd(r0 + cells + sx, fy * w);
+      }
+    }
+  }
+  __syncwarp();
+  for (int t = lane; t < S * S; t += 32) {
+    const int r = t / S, c = t - r * S;
+    const float v0 = box[r * P + c], v1 = box[cells + r * P + c];
+    if (v0 == 0.0f && v1 == 0.0f) continue;
+    int gx = ox + c, gy = oy + r;
+    if (gx < 0 || gx >= A.g.nx) gx = ((gx % A.g.nx) + A.g.nx) % A.g.nx;  // only periodic
+    if (gy < 0 || gy >= A.g.ny) gy = ((gy % A.g.ny) + A.g.ny) % A.g.ny;  // axes reach here
+    const long long n = (long long)gx + (long long)A.g.nx * gy;
+    if (v0 != 0.0f) atomicAdd(&A.fib[n], v0);
+    if (v1 != 0.0f) atomicAdd(&A.fib[A.g.N + n], v1);
+  }
+}
+
+// Per particle (one warp), after the last MDF iteration:
+//   F_h = -dV sum_b F_b, T_h = -dV sum_b r_b x F_b            (Eq. 14-15, via BTDF)
+//   momentum and angular momentum about X_c of the fluid at the nodes strictly inside,
+//   with the corrected velocity u* + f_IB/2 (the F_f, T_f closure of Eq. 14-15).
+// Sums are compensated single precision.  The inside test |x - X_c|^2 < R^2 runs in
+// single precision and falls back to the double-precision test (without fused
+// multiply-add) in a thin band around R^2, so the set of interior nodes is the one
+// the double-precision test gives.
 template <int D>
-__global__ void __launch_bounds__(256) interior_momentum_kernel(IbmArgs A) {
+__global__ void __launch_bounds__(256) ibm_forces_kernel(IbmArgs A) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= A.np) return;
@@ -224,7 +384,16 @@ __global__ void __launch_bounds__(256) interior_momentum_kernel(IbmArgs A) {
     if (!ok) continue;
     const long long nn = (long long)gc[0] + (long long)A.g.nx * ((long long)gc[1] + (long long)A.g.ny * gc[2]);
     float u[3] = {0.0f, 0.0f, 0.0f};
-    for (int c = 0; c < D; ++c) u[c] = A.ustar[c * A.g.N + nn] + 0.5f * A.fib[c * A.g.N + nn];
+    if (D == 2) {  // u* from the particle's box buffer (box coordinates, unwrapped)
+      const int S = A.box, P = S + 1, cells = S * P;
+      const int lc = (lo[0] + t % ext[0]) - (an[0] - A.rcell - 2);
+      const int lr = (lo[1] + (t / ext[0]) % ext[1]) - (an[1] - A.rcell - 2);
+      const float* ub = A.ubox + (size_t)i * 2 * cells + lr * P + lc;
+      u[0] = ub[0] + 0.5f * A.fib[nn];
+      u[1] = ub[cells] + 0.5f * A.fib[A.g.N + nn];
+    } else {
+      for (int c = 0; c < D; ++c) u[c] = A.ustar[c * A.g.N + nn] + 0.5f * A.fib[c * A.g.N + nn];
+    }
     for (int c = 0; c < D; ++c) ff_add(P[c], u[c]);
     if (D == 3) {
       ff_add(L[0], r[1] * u[2] - r[2] * u[1]);
@@ -232,126 +401,71 @@ __global__ void __launch_bounds__(256) interior_momentum_kernel(IbmArgs A) {
     }
     ff_add(L[2], r[0] * u[1] - r[1] * u[0]);
   }
-  for (int c = 0; c < 3; ++c) {
+  FF sF[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, sT[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  for (int k = lane; k < A.nl; k += 32) {
+    const long long b = (long long)i * A.nl + k;
+    float r[3] = {0.0f, 0.0f, 0.0f}, F[3] = {0.0f, 0.0f, 0.0f};
+    for (int c = 0; c < D; ++c) {
+      r[c] = A.ref_f[k * D + c];
+      F[c] = A.Fb[b * D + c];
+      ff_add(sF[c], F[c]);
+    }
+    if (D == 3) {
+      ff_add(sT[0], r[1] * F[2] - r[2] * F[1]);
+      ff_add(sT[1], r[2] * F[0] - r[0] * F[2]);
+    }
+    ff_add(sT[2], r[0] * F[1] - r[1] * F[0]);
+  }
+  // only the components that exist in this dimension (2D: x, y and the z rotation)
+  for (int c = 0; c < D; ++c) {
     P[c] = ff_warp_sum(P[c]);
+    sF[c] = ff_warp_sum(sF[c]);
+  }
+  for (int c = (D == 2 ? 2 : 0); c < 3; ++c) {
     L[c] = ff_warp_sum(L[c]);
+    sT[c] = ff_warp_sum(sT[c]);
   }
   if (lane == 0) {
-    for (int c = 0; c < D; ++c) A.Pint[(long long)i * D + c] = ff_value(P[c]);
-    for (int c = 0; c < 3; ++c) A.Lint[(long long)i * 3 + c] = (D == 2 && c < 2) ? 0.0 : ff_value(L[c]);
+    const double dV = (double)A.dV;
+    for (int c = 0; c < D; ++c) {
+      A.Pint[(long long)i * D + c] = ff_value(P[c]);
+      A.FhN[(long long)i * D + c] = -dV * ff_value(sF[c]);
+    }
+    for (int c = 0; c < 3; ++c) {
+      const bool used = !(D == 2 && c < 2);
+      A.Lint[(long long)i * 3 + c] = used ? ff_value(L[c]) : 0.0;
+      A.ThN[(long long)i * 3 + c] = used ? -dV * ff_value(sT[c]) : 0.0;
+    }
   }
 }
 
-// Newton-Euler update of one particle per warp, regeneration of its Lagrangian points
-// for the next step and marking of the nodes within mark_radius of the new centre.
-// mode 0 only regenerates and marks (initial state, new particle state).
-//   F_h = -dV sum_b F_b, T_h = -dV sum_b r_b x F_b     (Eq. 14-15; compensated sums)
-//   (M_p + K) a^n - K a^{n-1} = (F_h^n + F_h^{n-1})/2 + F_c + (P_int^n - P_int^{n-1})
-//                              + (M_p - rho_f V_p) g
-//   U^{n+1} = U^n + a^n, X^{n+1} = X^n + (U^n + U^{n+1})/2; rotation alike with I_p, K_r.
-// Double precision only for the per-particle integration by lane 0; points are
-// regenerated with 32.32 fixed-point additions and single-precision velocities.
+// One warp per particle: regenerate its Lagrangian points for the next step,
+//   X_b = X_c + r_b (32.32 fixed point), U_b = U_c + Omega x r_b (single precision),
+// and mark the nodes within mark_radius of the centre for the next lbm_moments.
+// init != 0 first refreshes the fixed-point centre and the single-precision
+// velocities from the double-precision state (initial state, new particle state).
 template <int D>
-__global__ void __launch_bounds__(256) particle_update_kernel(PartArgs A, int mode,
-                                                              int have_prev) {
+__global__ void __launch_bounds__(256) regen_kernel(RegenArgs A, int init) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= A.np) return;
   const long long pi = i;
-  double fh[3] = {0.0, 0.0, 0.0}, th[3] = {0.0, 0.0, 0.0};
-  if (mode == 1) {
-    FF sF[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, sT[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    for (int k = lane; k < A.nl; k += 32) {
-      const long long b = pi * A.nl + k;
-      float r[3] = {0.0f, 0.0f, 0.0f}, F[3] = {0.0f, 0.0f, 0.0f};
-      for (int c = 0; c < D; ++c) {
-        r[c] = A.ref_f[k * D + c];
-        F[c] = A.Fb[b * D + c];
-        ff_add(sF[c], F[c]);
-      }
-      if (D == 3) {
-        ff_add(sT[0], r[1] * F[2] - r[2] * F[1]);
-        ff_add(sT[1], r[2] * F[0] - r[0] * F[2]);
-      }
-      ff_add(sT[2], r[0] * F[1] - r[1] * F[0]);
-    }
-    for (int c = 0; c < 3; ++c) {
-      sF[c] = ff_warp_sum(sF[c]);
-      sT[c] = ff_warp_sum(sT[c]);
-    }
-    if (lane == 0) {
-      for (int c = 0; c < 3; ++c) {
-        fh[c] = -A.dV * ff_value(sF[c]);
-        th[c] = -A.dV * ff_value(sT[c]);
-      }
-    }
-  }
-  // lane 0: integrate (mode 1) and publish the centre in fixed point
-  long long xf[3] = {0, 0, 0};
-  float uf[3] = {0.0f, 0.0f, 0.0f}, of[3] = {0.0f, 0.0f, 0.0f};
-  if (lane == 0) {
-    if (mode == 1) {
-      bool bad = false;
-      for (int c = 0; c < D; ++c) {
-        const long long o = pi * D + c;
-        const double Fm = 0.5 * (fh[c] + A.Fhp[o]);
-        const double dP = have_prev ? A.Pint[o] - A.Pprev[o] : 0.0;
-        A.Fh[o] = fh[c];
-        A.Fhp[o] = fh[c];
-        A.Pprev[o] = A.Pint[o];
-        if (!A.fixed) {
-          const double F = Fm + A.Fc[o] + dP + A.meff * A.grav[c];
-          const double a = (F + A.Kt * A.acc[o]) / (A.Mp + A.Kt);
-          const double u0 = A.U[o], u1 = u0 + a;
-          A.acc[o] = a;
-          A.U[o] = u1;
-          A.X[o] += 0.5 * (u0 + u1);
-        }
-      }
-      for (int c = (D == 2 ? 2 : 0); c < 3; ++c) {
-        const long long o = pi * 3 + c;
-        const double Tm = 0.5 * (th[c] + A.Thp[o]);
-        const double dL = have_prev ? A.Lint[o] - A.Lprev[o] : 0.0;
-        A.Th[o] = th[c];
-        A.Thp[o] = th[c];
-        A.Lprev[o] = A.Lint[o];
-        if (!A.fixed) {
-          const double al = (Tm + dL + A.Kr * A.alp[o]) / (A.Ip + A.Kr);
-          A.alp[o] = al;
-          A.Om[o] += al;
-        }
-      }
-      const int nn[3] = {A.g.nx, A.g.ny, A.g.nz};
-      for (int c = 0; c < D; ++c) {
-        double& x = A.X[pi * D + c];
-        if (A.g.per[c]) {
-          if (x >= nn[c] - 0.5)
-            x -= nn[c];
-          else if (x < -0.5)
-            x += nn[c];
-        } else if (!(x >= -0.5 && x < nn[c] - 0.5)) {
-          atomicOr(A.status, ST_OUT_OF_DOMAIN);
-        }
-        if (!isfinite(x) || !isfinite(A.U[pi * D + c])) bad = true;
-      }
-      for (int c = 0; c < 3; ++c)
-        if (!isfinite(A.Om[pi * 3 + c])) bad = true;
-      if (bad) atomicOr(A.status, ST_NONFINITE);
-    }
+  if (init && lane == 0) {
     for (int c = 0; c < D; ++c) {
       const double x = A.X[pi * D + c];
-      xf[c] = isfinite(x) ? __double2ll_rn(x * kFixScale) : 0;
-      A.Xcf[pi * D + c] = xf[c];
-      uf[c] = (float)A.U[pi * D + c];
+      A.Xcf[pi * D + c] = isfinite(x) ? __double2ll_rn(x * kFixScale) : 0;
+      A.Uf[pi * D + c] = (float)A.U[pi * D + c];
     }
-    for (int c = 0; c < 3; ++c) of[c] = (D == 2 && c < 2) ? 0.0f : (float)A.Om[pi * 3 + c];
+    for (int c = 0; c < 3; ++c) A.Omf[pi * 3 + c] = (D == 2 && c < 2) ? 0.0f : (float)A.Om[pi * 3 + c];
   }
-  for (int c = 0; c < 3; ++c) {
-    xf[c] = __shfl_sync(0xffffffffu, xf[c], 0);
-    uf[c] = __shfl_sync(0xffffffffu, uf[c], 0);
-    of[c] = __shfl_sync(0xffffffffu, of[c], 0);
+  __syncwarp();
+  long long xf[3] = {0, 0, 0};
+  float uf[3] = {0.0f, 0.0f, 0.0f}, of[3] = {0.0f, 0.0f, 0.0f};
+  for (int c = 0; c < D; ++c) {
+    xf[c] = A.Xcf[pi * D + c];
+    uf[c] = A.Uf[pi * D + c];
   }
-  // regenerate the points: X_b = X_c + r_b (fixed point), U_b = U_c + Omega x r_b
+  for (int c = 0; c < 3; ++c) of[c] = A.Omf[pi * 3 + c];
   for (int k = lane; k < A.nl; k += 32) {
     const long long b = pi * A.nl + k;
     float r[3] = {0.0f, 0.0f, 0.0f};
@@ -363,8 +477,10 @@ __global__ void __launch_bounds__(256) particle_update_kernel(PartArgs A, int mo
       A.Ub_out[b * D + c] = uf[c] + w[c];
     }
   }
-  // mark the nodes of the ball |x - X_c| <= mark_radius, row by row (single precision
-  // relative to the centre's anchor node; the radius carries a safety margin)
+  // 3D: mark the nodes of the ball |x - X_c| <= mark_radius, row by row (single
+  // precision relative to the centre's anchor node; the radius carries a safety
+  // margin).  2D computes u* per particle box and needs no marks.
+  if (D == 2) return;
   int an[3] = {0, 0, 0};
   float fr[3] = {0.0f, 0.0f, 0.0f};
   for (int c = 0; c < D; ++c) {
@@ -414,56 +530,75 @@ __global__ void __launch_bounds__(256) particle_update_kernel(PartArgs A, int mo
 // ------------------------------------------------------------------ launchers
 cudaError_t launch_ibm_interp(const IbmArgs& A, int m, cudaStream_t s) {
   if (A.npts == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)((A.npts + 255) / 256);
-  if (A.D == 2)
-    ibm_interp_kernel<2><<<grid, 256, 0, s>>>(A, m);
-  else
+  if (A.D == 2) {
+    const unsigned grid = (unsigned)((A.np + kIbmWarps - 1) / kIbmWarps);
+    if (A.parity == 0)
+      ibm_interp2_kernel<0><<<grid, kIbmWarps * 32, ibm_box2_smem(A.box), s>>>(A, m);
+    else
+      ibm_interp2_kernel<1><<<grid, kIbmWarps * 32, ibm_box2_smem(A.box), s>>>(A, m);
+  } else {
+    const unsigned grid = (unsigned)((A.npts + 255) / 256);
     ibm_interp_kernel<3><<<grid, 256, 0, s>>>(A, m);
+  }
   return cudaGetLastError();
 }
 
 // The attribute is per kernel and process-wide, so it only ever grows: a later, smaller
 // run must not lower the limit an earlier, larger run still launches with.
+// shared memory of the spreading kernel used for this dimension (the 2D
+// interpolation kernel uses the same amount)
+size_t spread_smem(int D, int nl, int box) {
+  return D == 2 ? ibm_box2_smem(box) : ibm_spread_smem(D, nl, box);
+}
+
 cudaError_t prepare_ibm_spread(int D, size_t smem) {
   static std::mutex mu;
   static size_t granted[2] = {0, 0};
   std::lock_guard<std::mutex> lock(mu);
   size_t& g = granted[D == 2 ? 0 : 1];
   if (smem <= g) return cudaSuccess;
-  const cudaError_t e =
-      (D == 2) ? cudaFuncSetAttribute(ibm_spread_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-               : cudaFuncSetAttribute(ibm_spread_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e;
+  if (D == 2) {
+    e = cudaFuncSetAttribute(ibm_spread2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ibm_interp2_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ibm_interp2_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  } else {
+    e = cudaFuncSetAttribute(ibm_spread_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
   if (e == cudaSuccess) g = smem;
   return e;
 }
 
 cudaError_t launch_ibm_spread(const IbmArgs& A, cudaStream_t s) {
   if (A.np == 0) return cudaSuccess;
-  const size_t smem = ibm_spread_smem(A.D, A.nl, A.box);
-  if (A.D == 2)
-    ibm_spread_kernel<2><<<A.np, 256, smem, s>>>(A);
-  else
-    ibm_spread_kernel<3><<<A.np, 256, smem, s>>>(A);
+  if (A.D == 2) {
+    const unsigned grid = (unsigned)((A.np + kIbmWarps - 1) / kIbmWarps);
+    ibm_spread2_kernel<<<grid, kIbmWarps * 32, ibm_box2_smem(A.box), s>>>(A);
+  } else {
+    ibm_spread_kernel<3><<<A.np, 256, ibm_spread_smem(3, A.nl, A.box), s>>>(A);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_interior_momentum(const IbmArgs& A, cudaStream_t s) {
+cudaError_t launch_ibm_forces(const IbmArgs& A, cudaStream_t s) {
   if (A.np == 0) return cudaSuccess;
   const unsigned grid = (unsigned)(((long long)A.np * 32 + 255) / 256);
   if (A.D == 2)
-    interior_momentum_kernel<2><<<grid, 256, 0, s>>>(A);
+    ibm_forces_kernel<2><<<grid, 256, 0, s>>>(A);
   else
-    interior_momentum_kernel<3><<<grid, 256, 0, s>>>(A);
+    ibm_forces_kernel<3><<<grid, 256, 0, s>>>(A);
   return cudaGetLastError();
 }
 
-cudaError_t launch_particle_update(const PartArgs& A, int mode, int have_prev, cudaStream_t s) {
+cudaError_t launch_regen(const RegenArgs& A, int init, cudaStream_t s) {
   if (A.np == 0) return cudaSuccess;
   const unsigned grid = (unsigned)(((long long)A.np * 32 + 255) / 256);
   if (A.D == 2)
-    particle_update_kernel<2><<<grid, 256, 0, s>>>(A, mode, have_prev);
+    regen_kernel<2><<<grid, 256, 0, s>>>(A, init);
   else
-    particle_update_kernel<3><<<grid, 256, 0, s>>>(A, mode, have_prev);
+    regen_kernel<3><<<grid, 256, 0, s>>>(A, init);
   return cudaGetLastError();
 }
 

@@ -20,12 +20,13 @@ cudaError_t launch_lbm_equilibrium(const LbmArgs& A, int D, int parity, const do
 cudaError_t launch_ibm_interp(const IbmArgs& A, int m, cudaStream_t s);
 cudaError_t launch_ibm_spread(const IbmArgs& A, cudaStream_t s);
 size_t ibm_spread_smem(int D, int nl, int box);
+size_t spread_smem(int D, int nl, int box);  // of the kernel launch_ibm_spread uses
 cudaError_t prepare_ibm_spread(int D, size_t smem);  // once, before any capture
-cudaError_t launch_interior_momentum(const IbmArgs& A, cudaStream_t s);
-cudaError_t launch_particle_update(const PartArgs& A, int mode, int have_prev, cudaStream_t s);
+cudaError_t launch_ibm_forces(const IbmArgs& A, cudaStream_t s);
+cudaError_t launch_regen(const RegenArgs& A, int init, cudaStream_t s);
 
-// pair search: cell lists by counting sort, neighbour lists and contact forces
-cudaError_t launch_pair_cells(const PairArgs& A, cudaStream_t s);   // 3 kernels
+// pair search: cell buckets, neighbour lists, contact forces (and the particle update)
+cudaError_t launch_pair_cells(const PairArgs& A, cudaStream_t s);   // memset + 1 kernel
 cudaError_t launch_pair_contacts(const PairArgs& A, cudaStream_t s);
 cudaError_t launch_pair_compact(const PairArgs& A, int* pairs, long long cap, cudaStream_t s);
 cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t s);

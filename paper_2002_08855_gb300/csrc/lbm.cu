@@ -12,74 +12,11 @@
 // copy of the PDFs suffices (the role the swap algorithm of Sec. 3.3 plays on a CPU).
 #include "common.cuh"
 #include "launch.h"
+#include "pdf_access.cuh"
 
 namespace ibmlbm {
 
 constexpr int kLbmBlock = 128;
-
-// index of the neighbour x - s*e_a (s = +1 for the pull source, -1 for the push
-// target); false if it lies beyond a wall
-template <class L>
-__device__ __forceinline__ bool neighbour(const Geo& g, int a, int s, int x, int y, int z,
-                                          long long n, long long& idx) {
-  idx = n;
-  const int ex = s * L::e(a, 0), ey = s * L::e(a, 1), ez = s * L::e(a, 2);
-  if (ex) {
-    const int t = x - ex;
-    if (t < 0 || t >= g.nx) {
-      if (!g.per[0]) return false;
-      idx += (t < 0) ? g.nx : -g.nx;
-    }
-    idx -= ex;
-  }
-  if (ey) {
-    const int t = y - ey;
-    if (t < 0 || t >= g.ny) {
-      if (!g.per[1]) return false;
-      idx += (long long)((t < 0) ? g.ny : -g.ny) * g.nx;
-    }
-    idx -= (long long)ey * g.nx;
-  }
-  if (L::dim == 3 && ez) {
-    const int t = z - ez;
-    const long long plane = (long long)g.nx * g.ny;
-    if (t < 0 || t >= g.nz) {
-      if (!g.per[2]) return false;
-      idx += ((t < 0) ? g.nz : -g.nz) * plane;
-    }
-    idx -= ez * plane;
-  }
-  return true;
-}
-
-// offset of the neighbour x - s*e_a for a node whose whole neighbourhood is inside
-template <class L>
-__device__ __forceinline__ long long inner_offset(const Geo& g, int a, int s) {
-  return -(long long)s * ((long long)L::e(a, 0) + (long long)g.nx * L::e(a, 1) +
-                          (long long)g.nx * g.ny * L::e(a, 2));
-}
-
-// pre-collision PDFs f_a(x) of the current time under the layout of the given parity;
-// INNER: the node is at least one node away from every domain face
-template <class L, int PARITY, bool INNER = false>
-__device__ __forceinline__ void load_pdfs(const Geo& g, const float* __restrict__ f, int x,
-                                          int y, int z, long long n, float (&fa)[L::Q]) {
-  const long long N = g.N;
-#pragma unroll
-  for (int a = 0; a < L::Q; ++a) {
-    if (PARITY == 0 || a == 0) {
-      fa[a] = f[a * N + n];
-    } else if (INNER) {
-      fa[a] = f[opp<L>(a) * N + n + inner_offset<L>(g, a, 1)];
-    } else {
-      long long src;
-      if (neighbour<L>(g, a, 1, x, y, z, n, src))
-        fa[a] = f[opp<L>(a) * N + src];
-      else
-        fa[a] = f[a * N + n];
-    }
-  }
-}
 
 // inverse of load_pdfs: slot of f_a(x) under the layout of the given parity
 template <class L, int PARITY>
@@ -119,22 +56,6 @@ __device__ __forceinline__ void store_post(const Geo& g, float* __restrict__ f, 
         f[a * N + dst] = fa[a];
       else
         f[opp<L>(a) * N + n] = fa[a];
-    }
-  }
-}
-
-// Eq. 5 (u* = sum e f) and the sum of the moving populations used by Eq. 6
-template <class L>
-__device__ __forceinline__ void moments(const float (&f)[L::Q], float (&us)[3], float& s1) {
-  us[0] = us[1] = us[2] = 0.0f;
-  s1 = 0.0f;
-#pragma unroll
-  for (int a = 1; a < L::Q; ++a) {
-    s1 += f[a];
-#pragma unroll
-    for (int k = 0; k < L::dim; ++k) {
-      if (L::e(a, k) == 1) us[k] += f[a];
-      if (L::e(a, k) == -1) us[k] -= f[a];
     }
   }
 }
@@ -243,10 +164,12 @@ __device__ __forceinline__ void step_node(const LbmArgs& A, const NodeCoord& c) 
 }
 
 // One full time step on every node: read f (AA parity) and the IB force, collide,
-// stream in place, clear the IB force.
+// stream in place, clear the IB force.  Also clears the node mask (one store per 32
+// nodes) for the particle update to mark the next step's nodes.
 template <class L, int PARITY>
 __global__ void __launch_bounds__(kLbmBlock) lbm_step_kernel(LbmArgs A, int cpr) {
   const NodeCoord c = node_coord(A.g, cpr);
+  if ((c.x & 31) == 0 && c.valid) A.mask[c.row * A.g.wpr + (c.x >> 5)] = 0u;
   if (PARITY == 1 && block_inner(A.g, c.x - (int)threadIdx.x, c.y, c.z, L::dim)) {
     step_node<L, PARITY, true>(A, c);
     return;
@@ -256,24 +179,28 @@ __global__ void __launch_bounds__(kLbmBlock) lbm_step_kernel(LbmArgs A, int cpr)
 }
 
 // u* = sum_a e_a f_a (Eq. 5) on flagged nodes only.
-// The mask is consumed here: each warp clears its word after reading it, and the
-// particle update marks the nodes of the next step.
+// u* = sum_a e_a f_a (Eq. 5) on the flagged nodes only: one thread per node in large
+// blocks; threads of unflagged nodes leave after reading their mask word.  The mask
+// is cleared by lbm_step later in the step.
+constexpr int kMomBlock = 512;
+
 template <class L, int PARITY>
-__global__ void __launch_bounds__(kLbmBlock) lbm_moments_kernel(LbmArgs A, int cpr) {
-  const NodeCoord c = node_coord(A.g, cpr);
-  const int wi = c.x >> 5;
-  if (wi >= A.g.wpr) return;  // whole warp: a warp covers exactly one mask word
-  uint32_t* wp = A.mask + c.row * A.g.wpr + wi;
-  const uint32_t word = *wp;
-  if (!word) return;  // whole warp
-  __syncwarp();
-  if ((c.x & 31) == 0) *wp = 0u;
-  if (!c.valid || !((word >> (c.x & 31)) & 1u)) return;
+__global__ void __launch_bounds__(kMomBlock) lbm_moments_kernel(LbmArgs A) {
+  const long long n = blockIdx.x * (long long)kMomBlock + threadIdx.x;
+  if (n >= A.g.N) return;
+  const unsigned nx = (unsigned)A.g.nx;
+  const unsigned row = (unsigned)(n / nx);
+  const int x = (int)(n - (long long)row * nx);
+  const uint32_t word = A.mask[(long long)row * A.g.wpr + (x >> 5)];
+  if (!((word >> (x & 31)) & 1u)) return;
+  const unsigned uny = (unsigned)A.g.ny;
+  const unsigned z = row / uny;
+  const int y = (int)(row - z * uny);
   float fa[L::Q], us[3], s1;
-  load_pdfs<L, PARITY>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
+  load_pdfs<L, PARITY>(A.g, A.f, x, y, (int)z, n, fa);
   moments<L>(fa, us, s1);
 #pragma unroll
-  for (int k = 0; k < L::dim; ++k) A.ustar[k * A.g.N + c.n] = us[k];
+  for (int k = 0; k < L::dim; ++k) A.ustar[k * A.g.N + n] = us[k];
 }
 
 // p (Eq. 6 with u = u*) and u* (Eq. 5) on every node, as doubles.
@@ -363,9 +290,14 @@ cudaError_t launch_lbm_step(const LbmArgs& A, int D, int parity, cudaStream_t s)
 }
 
 cudaError_t launch_lbm_moments(const LbmArgs& A, int D, int parity, cudaStream_t s) {
-  int cpr;
-  const dim3 grid = lbm_grid(A.g, cpr);
-  IBMLBM_DISPATCH(D, parity, lbm_moments_kernel, A, cpr);
+  const dim3 grid((unsigned)((A.g.N + kMomBlock - 1) / kMomBlock));
+  if (D == 2) {
+    if (parity == 0) lbm_moments_kernel<Lat<2>, 0><<<grid, kMomBlock, 0, s>>>(A);
+    else lbm_moments_kernel<Lat<2>, 1><<<grid, kMomBlock, 0, s>>>(A);
+  } else {
+    if (parity == 0) lbm_moments_kernel<Lat<3>, 0><<<grid, kMomBlock, 0, s>>>(A);
+    else lbm_moments_kernel<Lat<3>, 1><<<grid, kMomBlock, 0, s>>>(A);
+  }
   return cudaGetLastError();
 }
 

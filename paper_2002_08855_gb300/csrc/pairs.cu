@@ -1,15 +1,18 @@
-// Cell-list pair search and short-range repulsive force (Sec. 5, Eq. 16).
+// Cell-list pair search, short-range repulsive force (Sec. 5, Eq. 16) and the
+// double-precision particle update (Eq. 14-15).
 //
 // Cells of side H_k = L_k / nc_k >= D_p + zeta (a periodic axis with fewer than three
 // cells becomes one cell), so every pair closer than D_p + zeta lies in the 3^D
-// neighbourhood of a cell.  Cell lists come from a counting sort: count per cell
-// (atomics), exclusive scan, scatter (atomics again, which leaves the counts at zero
-// for the next step).  Each particle then scans its neighbourhood, keeps partners j
-// with |X_i - X_j|^2 < (D_p + zeta)^2 -- squared distance summed in axis order in
-// double precision without fused multiply-add, nearest image on periodic axes --
-// sorts them by index and sums the Eq. 16 force in that order, so the result does
-// not depend on the order of the cell lists.  The canonical pair list (i < j, sorted)
-// is compacted from these per-particle lists on request.
+// neighbourhood of a cell.  Each cell is a bucket of at most cell_cap particle ids
+// filled with one atomic slot per particle (overflow is reported, never dropped
+// silently).  A warp per particle then scans its neighbourhood, keeps partners j with
+// |X_i - X_j|^2 < (D_p + zeta)^2 -- squared distance summed in axis order in double
+// precision without fused multiply-add, nearest image on periodic axes -- sorts them
+// by index and sums the Eq. 16 force in that order, so the result does not depend on
+// the order inside the buckets.  The canonical pair list (i < j, sorted) is compacted
+// from these per-particle lists on request.  In a time step one thread per particle
+// then sums the contact force and advances the particle in double precision, writing
+// the new centre to the other centre buffer, so neighbours still read old centres.
 #include <cmath>
 
 #include "common.cuh"
@@ -35,19 +38,15 @@ __device__ __forceinline__ int cell_of(const PairArgs& A, int i) {
 }
 
 template <int D>
-__global__ void pair_count_kernel(PairArgs A) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.n) return;
-  atomicAdd(&A.cell_count[cell_of<D>(A, i)], 1);
-}
-
-template <int D>
-__global__ void pair_fill_kernel(PairArgs A) {
+__global__ void pair_insert_kernel(PairArgs A) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
   const int c = cell_of<D>(A, i);
-  const int slot = A.cell_start[c] + atomicSub(&A.cell_count[c], 1) - 1;
-  A.sorted[slot] = i;
+  const int slot = atomicAdd(&A.cell_count[c], 1);
+  if (slot < A.cell_cap)
+    A.cell_ids[(long long)c * A.cell_cap + slot] = i;
+  else
+    atomicOr(A.status, ST_CAPACITY);
 }
 
 // X_i - X_j with the nearest image on periodic axes
@@ -84,75 +83,176 @@ __device__ __forceinline__ double eq16_magnitude(const PairArgs& A, double d) {
   return mag;
 }
 
+// Newton-Euler update of particle i (Eq. 14-15 with the interior-momentum closure):
+//   (M_p + K) a^n - K a^{n-1} = (F_h^n + F_h^{n-1})/2 + F_c + (P_int^n - P_int^{n-1})
+//                              + (M_p - rho_f V_p) g
+//   U^{n+1} = U^n + a^n, X^{n+1} = X^n + (U^n + U^{n+1})/2; rotation alike with I_p, K_r.
+// The K terms telescope, so momentum is conserved; they keep the explicit coupling
+// stable when the IB shell outweighs the particle.
 template <int D>
-__global__ void pair_contact_kernel(PairArgs A) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.n) return;
+__device__ void advance_particle(const PairArgs& A, int i, const double* X, const double* Fc) {
+  const PartState& P = A.ps;
+  const long long pi = i;
+  bool bad = false;
+  for (int c = 0; c < D; ++c) {
+    const long long o = pi * D + c;
+    const double fh = P.FhN[o];
+    const double Fm = 0.5 * (fh + P.Fh[o]);
+    const double dP = A.have_prev ? P.Pint[o] - P.Pprev[o] : 0.0;
+    P.Fh[o] = fh;
+    P.Pprev[o] = P.Pint[o];
+    double x = X[c];
+    if (!P.fixed) {
+      const double F = Fm + Fc[c] + dP + P.meff * P.grav[c];
+      const double a = (F + P.Kt * P.acc[o]) / (P.Mp + P.Kt);
+      const double u0 = P.U[o], u1 = u0 + a;
+      P.acc[o] = a;
+      P.U[o] = u1;
+      x += 0.5 * (u0 + u1);
+    }
+    const double n = A.L[c];
+    if (A.g.per[c]) {
+      if (x >= n - 0.5)
+        x -= n;
+      else if (x < -0.5)
+        x += n;
+    } else if (!(x >= -0.5 && x < n - 0.5)) {
+      atomicOr(A.status, ST_OUT_OF_DOMAIN);
+    }
+    if (!isfinite(x) || !isfinite(P.U[o])) bad = true;
+    P.Xnew[o] = x;
+    P.Xcf[o] = isfinite(x) ? __double2ll_rn(x * kFixScale) : 0;
+    P.Uf[o] = (float)P.U[o];
+  }
+  for (int c = (D == 2 ? 2 : 0); c < 3; ++c) {
+    const long long o = pi * 3 + c;
+    const double th = P.ThN[o];
+    const double Tm = 0.5 * (th + P.Th[o]);
+    const double dL = A.have_prev ? P.Lint[o] - P.Lprev[o] : 0.0;
+    P.Th[o] = th;
+    P.Lprev[o] = P.Lint[o];
+    if (!P.fixed) {
+      const double al = (Tm + dL + P.Kr * P.alp[o]) / (P.Ip + P.Kr);
+      P.alp[o] = al;
+      P.Om[o] += al;
+    }
+    if (!isfinite(P.Om[o])) bad = true;
+    P.Omf[o] = (float)P.Om[o];
+  }
+  if (D == 2) P.Omf[pi * 3] = P.Omf[pi * 3 + 1] = 0.0f;
+  if (bad) atomicOr(A.status, ST_NONFINITE);
+}
+
+// Neighbour search, one warp per particle.  Lane c < 3^D reads the count of
+// neighbouring cell c; a warp scan turns the counts into offsets, and lane l then
+// tests occupied slots l, l+32, ... of the concatenated buckets.  Accepted partners
+// are appended in lane order and sorted by index.  Writes the sorted list, its length
+// and the number of partners j > i.
+template <int D>
+__global__ void __launch_bounds__(256) pair_search_kernel(PairArgs A) {
+  __shared__ int s_list[8][kMaxNeighbors];
+  __shared__ int s_cell[8][32];
+  __shared__ int s_off[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  if (i >= A.n) return;  // whole warp
+  int* list = s_list[w];
+  int* sc = s_cell[w];
+  int* so = s_off[w];
   double Xi[3] = {0.0, 0.0, 0.0};
   int cc[3] = {0, 0, 0};
   for (int k = 0; k < D; ++k) {
     Xi[k] = A.X[(long long)i * D + k];
     cc[k] = cell_coord(Xi[k], A.H[k], A.nc[k]);
   }
-  int list[kMaxNeighbors];
-  int cnt = 0;
-  for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz)
-    for (int oy = -1; oy <= 1; ++oy)
-      for (int ox = -1; ox <= 1; ++ox) {
-        const int off[3] = {ox, oy, oz};
-        int cell = 0, stride = 1;
-        bool ok = true;
-        for (int k = 0; k < D; ++k) {
-          int c = cc[k] + off[k];
-          if (A.nc[k] == 1) {
-            if (off[k] != 0) ok = false;
-            c = 0;
-          } else if (c < 0 || c >= A.nc[k]) {
-            if (A.g.per[k])
-              c = (c + A.nc[k]) % A.nc[k];
-            else
-              ok = false;
-          }
-          cell += stride * c;
-          stride *= A.nc[k];
-        }
-        if (!ok) continue;
-        for (int s = A.cell_start[cell]; s < A.cell_start[cell + 1]; ++s) {
-          const int j = A.sorted[s];
-          if (j == i) continue;
-          double Xj[3] = {0.0, 0.0, 0.0}, dx[3];
-          for (int k = 0; k < D; ++k) Xj[k] = A.X[(long long)j * D + k];
-          separation<D>(A, Xi, Xj, dx);
-          if (dist2_nofma(dx) < A.thr2) {
-            if (cnt < A.kmax) list[cnt] = j;
-            ++cnt;
-          }
-        }
+  constexpr int NCELL = (D == 3) ? 27 : 9;
+  int cnt_c = 0, cell = 0;
+  if (lane < NCELL) {
+    const int off[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+    int stride = 1;
+    bool ok = true;
+    for (int k = 0; k < D; ++k) {
+      int c = cc[k] + off[k];
+      if (A.nc[k] == 1) {
+        if (off[k] != 0) ok = false;
+        c = 0;
+      } else if (c < 0 || c >= A.nc[k]) {
+        if (A.g.per[k])
+          c = (c + A.nc[k]) % A.nc[k];
+        else
+          ok = false;
       }
-  if (cnt > A.kmax) {
-    atomicOr(A.status, ST_CAPACITY);
-    cnt = A.kmax;
-  }
-  for (int a = 1; a < cnt; ++a) {  // insertion sort by partner index
-    const int v = list[a];
-    int b = a - 1;
-    while (b >= 0 && list[b] > v) {
-      list[b + 1] = list[b];
-      --b;
+      cell += stride * c;
+      stride *= A.nc[k];
     }
-    list[b + 1] = v;
+    if (ok) cnt_c = min(A.cell_count[cell], A.cell_cap);
   }
-  int gt = 0;
-  for (int a = 0; a < cnt; ++a) {
-    A.nbr[(long long)i * A.kmax + a] = list[a];
-    gt += list[a] > i;
+  int incl = cnt_c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
   }
-  A.nbr_count[i] = cnt;
-  A.gt_count[i] = gt;
-  if (!A.Fc) return;
+  sc[lane] = cell;
+  so[lane + 1] = incl;
+  if (lane == 0) so[0] = 0;
+  __syncwarp();
+  const int total = so[32];
+  int cnt = 0;
+  for (int base = 0; base < total; base += 32) {
+    const int q = base + lane;
+    bool hit = false;
+    int j = -1;
+    if (q < total) {
+      int c = 0;
+      while (so[c + 1] <= q) ++c;
+      j = A.cell_ids[(long long)sc[c] * A.cell_cap + (q - so[c])];
+      if (j != i) {
+        double Xj[3] = {0.0, 0.0, 0.0}, dx[3];
+        for (int k = 0; k < D; ++k) Xj[k] = A.X[(long long)j * D + k];
+        separation<D>(A, Xi, Xj, dx);
+        hit = dist2_nofma(dx) < A.thr2;
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+    if (hit && pos < A.kmax) list[pos] = j;
+    cnt += __popc(m);
+  }
+  __syncwarp();
+  const int n_ok = min(cnt, A.kmax);
+  if (lane == 0) {
+    if (cnt > A.kmax) atomicOr(A.status, ST_CAPACITY);
+    int gt = 0;
+    for (int a = 1; a < n_ok; ++a) {  // insertion sort by partner index
+      const int v = list[a];
+      int b = a - 1;
+      while (b >= 0 && list[b] > v) {
+        list[b + 1] = list[b];
+        --b;
+      }
+      list[b + 1] = v;
+    }
+    for (int a = 0; a < n_ok; ++a) gt += list[a] > i;
+    A.nbr_count[i] = n_ok;
+    A.gt_count[i] = gt;
+  }
+  __syncwarp();
+  for (int a = lane; a < n_ok; a += 32) A.nbr[(long long)i * A.kmax + a] = list[a];
+}
+
+// Eq. 16 contact force on particle i from its sorted partner list (summed in index
+// order) and from one mirror image per wall, then (in a time step) the particle update.
+template <int D>
+__global__ void __launch_bounds__(128) pair_force_kernel(PairArgs A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  double Xi[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < D; ++k) Xi[k] = A.X[(long long)i * D + k];
+  const int cnt = A.nbr_count[i];
   double F[3] = {0.0, 0.0, 0.0};
   for (int a = 0; a < cnt; ++a) {
-    const int j = list[a];
+    const int j = A.nbr[(long long)i * A.kmax + a];
     double Xj[3] = {0.0, 0.0, 0.0}, dx[3];
     for (int k = 0; k < D; ++k) Xj[k] = A.X[(long long)j * D + k];
     separation<D>(A, Xi, Xj, dx);
@@ -173,6 +273,7 @@ __global__ void pair_contact_kernel(PairArgs A) {
     }
   }
   for (int k = 0; k < D; ++k) A.Fc[(long long)i * D + k] = F[k];
+  if (A.integrate) advance_particle<D>(A, i, Xi, F);
 }
 
 // exclusive scan of n ints into out[0..n] (out[n] = total); one block of 1024 threads
@@ -245,30 +346,33 @@ cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t s) {
 
 cudaError_t launch_pair_cells(const PairArgs& A, cudaStream_t s) {
   if (A.n == 0) return cudaSuccess;
+  const size_t ncells = (size_t)A.nc[0] * A.nc[1] * A.nc[2];
+  cudaError_t e = cudaMemsetAsync(A.cell_count, 0, sizeof(int) * ncells, s);
+  if (e != cudaSuccess) return e;
   const unsigned g = blocks_for(A.n, 256);
-  const int ncells = A.nc[0] * A.nc[1] * A.nc[2];
   if (A.D == 2)
-    pair_count_kernel<2><<<g, 256, 0, s>>>(A);
+    pair_insert_kernel<2><<<g, 256, 0, s>>>(A);
   else
-    pair_count_kernel<3><<<g, 256, 0, s>>>(A);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  e = launch_scan(A.cell_count, A.cell_start, ncells, s);
-  if (e != cudaSuccess) return e;
-  if (A.D == 2)
-    pair_fill_kernel<2><<<g, 256, 0, s>>>(A);
-  else
-    pair_fill_kernel<3><<<g, 256, 0, s>>>(A);
+    pair_insert_kernel<3><<<g, 256, 0, s>>>(A);
   return cudaGetLastError();
 }
 
+// neighbour lists (warp per particle), then, when A.Fc is set, contact forces and the
+// particle update (thread per particle)
 cudaError_t launch_pair_contacts(const PairArgs& A, cudaStream_t s) {
   if (A.n == 0) return cudaSuccess;
+  const unsigned gw = blocks_for((long long)A.n * 32, 256);
+  if (A.D == 2)
+    pair_search_kernel<2><<<gw, 256, 0, s>>>(A);
+  else
+    pair_search_kernel<3><<<gw, 256, 0, s>>>(A);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !A.Fc) return e;
   const unsigned g = blocks_for(A.n, 128);
   if (A.D == 2)
-    pair_contact_kernel<2><<<g, 128, 0, s>>>(A);
+    pair_force_kernel<2><<<g, 128, 0, s>>>(A);
   else
-    pair_contact_kernel<3><<<g, 128, 0, s>>>(A);
+    pair_force_kernel<3><<<g, 128, 0, s>>>(A);
   return cudaGetLastError();
 }
 

@@ -103,8 +103,8 @@ extern "C" int ibm_lbm_pair_search_static(int32_t dim, const int32_t* n_nodes, c
   const size_t ncells = (size_t)a.nc[0] * a.nc[1] * a.nc[2];
   size_t off = 0;
   const size_t o_count = take(off, sizeof(int) * ncells);
-  const size_t o_start = take(off, sizeof(int) * (ncells + 1));
-  const size_t o_sorted = take(off, sizeof(int) * (size_t)n);
+  const int cell_cap = cell_capacity(n, (long long)ncells);
+  const size_t o_ids = take(off, sizeof(int) * ncells * cell_cap);
   const size_t o_nbr = take(off, sizeof(int) * (size_t)n * kmax);
   const size_t o_ncnt = take(off, sizeof(int) * (size_t)n);
   const size_t o_gt = take(off, sizeof(int) * 2 * ((size_t)n + 1));
@@ -129,8 +129,8 @@ extern "C" int ibm_lbm_pair_search_static(int32_t dim, const int32_t* n_nodes, c
   a.kmax = kmax;
   a.X = d_X;
   a.cell_count = reinterpret_cast<int*>(sc + o_count);
-  a.cell_start = reinterpret_cast<int*>(sc + o_start);
-  a.sorted = reinterpret_cast<int*>(sc + o_sorted);
+  a.cell_ids = reinterpret_cast<int*>(sc + o_ids);
+  a.cell_cap = cell_capacity(n, (long long)ncells);
   a.nbr = reinterpret_cast<int*>(sc + o_nbr);
   a.nbr_count = reinterpret_cast<int*>(sc + o_ncnt);
   a.gt_count = reinterpret_cast<int*>(sc + o_gt);
@@ -142,9 +142,8 @@ extern "C" int ibm_lbm_pair_search_static(int32_t dim, const int32_t* n_nodes, c
     if (e_ != cudaSuccess)                                                                    \
       return static_fail(IBMLBM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
   } while (0)
-  // the counters and the status word must start at zero; everything else is written
-  // before it is read
-  STATIC_TRY(cudaMemsetAsync(a.cell_count, 0, sizeof(int) * ncells, s));
+  // the status word must start at zero (the cell counters are cleared by
+  // launch_pair_cells); everything else is written before it is read
   STATIC_TRY(cudaMemsetAsync(a.status, 0, sizeof(uint32_t), s));
   STATIC_TRY(launch_pair_cells(a, s));
   STATIC_TRY(launch_pair_contacts(a, s));

@@ -1,0 +1,94 @@
+// Reading the PDFs of a node under the AA-pattern layout (device helpers shared by
+// the lattice kernels and the immersed-boundary kernels).
+//
+// AA pattern, one PDF array a[Q][N]:
+//   parity 0 (before an even step): f_a(x) is stored at a[a][x];
+//   parity 1 (before an odd step): f_a(x) is stored at a[opp(a)][x - e_a], or at
+//     a[a][x] when x - e_a lies beyond a wall (halfway bounce-back).
+#pragma once
+
+#include "common.cuh"
+
+namespace ibmlbm {
+
+// index of the neighbour x - s*e_a (s = +1 for the pull source, -1 for the push
+// target); false if it lies beyond a wall
+template <class L>
+__device__ __forceinline__ bool neighbour(const Geo& g, int a, int s, int x, int y, int z,
+                                          long long n, long long& idx) {
+  idx = n;
+  const int ex = s * L::e(a, 0), ey = s * L::e(a, 1), ez = s * L::e(a, 2);
+  if (ex) {
+    const int t = x - ex;
+    if (t < 0 || t >= g.nx) {
+      if (!g.per[0]) return false;
+      idx += (t < 0) ? g.nx : -g.nx;
+    }
+    idx -= ex;
+  }
+  if (ey) {
+    const int t = y - ey;
+    if (t < 0 || t >= g.ny) {
+      if (!g.per[1]) return false;
+      idx += (long long)((t < 0) ? g.ny : -g.ny) * g.nx;
+    }
+    idx -= (long long)ey * g.nx;
+  }
+  if (L::dim == 3 && ez) {
+    const int t = z - ez;
+    const long long plane = (long long)g.nx * g.ny;
+    if (t < 0 || t >= g.nz) {
+      if (!g.per[2]) return false;
+      idx += ((t < 0) ? g.nz : -g.nz) * plane;
+    }
+    idx -= ez * plane;
+  }
+  return true;
+}
+
+// offset of the neighbour x - s*e_a for a node whose whole neighbourhood is inside
+template <class L>
+__device__ __forceinline__ long long inner_offset(const Geo& g, int a, int s) {
+  return -(long long)s * ((long long)L::e(a, 0) + (long long)g.nx * L::e(a, 1) +
+                          (long long)g.nx * g.ny * L::e(a, 2));
+}
+
+// pre-collision PDFs f_a(x) of the current time under the layout of the given parity;
+// INNER: the node is at least one node away from every domain face
+template <class L, int PARITY, bool INNER = false>
+__device__ __forceinline__ void load_pdfs(const Geo& g, const float* __restrict__ f, int x,
+                                          int y, int z, long long n, float (&fa)[L::Q]) {
+  const long long N = g.N;
+#pragma unroll
+  for (int a = 0; a < L::Q; ++a) {
+    if (PARITY == 0 || a == 0) {
+      fa[a] = f[a * N + n];
+    } else if (INNER) {
+      fa[a] = f[opp<L>(a) * N + n + inner_offset<L>(g, a, 1)];
+    } else {
+      long long src;
+      if (neighbour<L>(g, a, 1, x, y, z, n, src))
+        fa[a] = f[opp<L>(a) * N + src];
+      else
+        fa[a] = f[a * N + n];
+    }
+  }
+}
+
+// Eq. 5 (u* = sum e f) and the sum of the moving populations used by Eq. 6
+template <class L>
+__device__ __forceinline__ void moments(const float (&f)[L::Q], float (&us)[3], float& s1) {
+  us[0] = us[1] = us[2] = 0.0f;
+  s1 = 0.0f;
+#pragma unroll
+  for (int a = 1; a < L::Q; ++a) {
+    s1 += f[a];
+#pragma unroll
+    for (int k = 0; k < L::dim; ++k) {
+      if (L::e(a, k) == 1) us[k] += f[a];
+      if (L::e(a, k) == -1) us[k] -= f[a];
+    }
+  }
+}
+
+}  // namespace ibmlbm
