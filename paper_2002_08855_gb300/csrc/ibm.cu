@@ -188,15 +188,26 @@ size_t ibm_box2_smem(int box) { return sizeof(float) * 2 * (size_t)box * (box + 
 // keeps it in the particle's box buffer; later iterations stage that buffer plus
 // f_IB/2.  Lane k then interpolates point k from shared memory.  Box nodes beyond a
 // wall hold zero, which drops them from the sum.
-template <int PARITY>
+template <int SC, int PARITY>
 __global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A, int m) {
   extern __shared__ float smem_i[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int i = blockIdx.x * kIbmWarps + wib;
   if (i >= A.np) return;  // whole warp
-  const int S = A.box, P = S + 1, cells = S * P;
+  const int S = SC ? SC : A.box, P = S + 1, cells = S * P;
   float* box = smem_i + (size_t)wib * 2 * cells;
   float* ub = A.ubox + (size_t)i * 2 * cells;
+  // the first point of this lane is loaded before the box, so both latencies overlap
+  const bool has0 = m > 0 && lane < A.nl;
+  const long long b0 = (long long)i * A.nl + lane;
+  long long X0x = 0, X0y = 0;
+  float U0x = 0.0f, U0y = 0.0f;
+  if (has0) {
+    X0x = A.Xb[b0 * 2];
+    X0y = A.Xb[b0 * 2 + 1];
+    U0x = A.Ub[b0 * 2];
+    U0y = A.Ub[b0 * 2 + 1];
+  }
   const int ox = fix_anchor(A.Xcf[(long long)i * 2 + 0]) - A.rcell - 2;
   const int oy = fix_anchor(A.Xcf[(long long)i * 2 + 1]) - A.rcell - 2;
   const long long N = A.g.N;
@@ -237,13 +248,18 @@ __global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A, 
   __syncwarp();
   for (int k = lane; k < A.nl; k += 32) {
     const long long b = (long long)i * A.nl + k;
-    const long long Xx = A.Xb[b * 2], Xy = A.Xb[b * 2 + 1];
+    const bool first = k == lane;
+    const long long Xx = first ? X0x : A.Xb[b * 2], Xy = first ? X0y : A.Xb[b * 2 + 1];
+    const float Ux = first ? U0x : A.Ub[b * 2], Uy = first ? U0y : A.Ub[b * 2 + 1];
     const int lx0 = fix_anchor(Xx) - 1 - ox, ly0 = fix_anchor(Xy) - 1 - oy;
     const float rx = fix_frac(Xx), ry = fix_frac(Xy);
     float acc0 = 0.0f, acc1 = 0.0f;
     if (lx0 < 0 || ly0 < 0 || lx0 + 3 >= S || ly0 + 3 >= S) {
       atomicOr(A.status, ST_CAPACITY);
     } else {
+      float wx[4];
+#pragma unroll
+      for (int sx = 0; sx < 4; ++sx) wx[sx] = delta4((float)(sx - 1) - rx);
 #pragma unroll
       for (int sy = 0; sy < 4; ++sy) {
         const float wy = delta4((float)(sy - 1) - ry);
@@ -251,15 +267,14 @@ __global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A, 
         float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
         for (int sx = 0; sx < 4; ++sx) {
-          const float wx = delta4((float)(sx - 1) - rx);
-          a0 += wx * r0[sx];
-          a1 += wx * r0[cells + sx];
+          a0 += wx[sx] * r0[sx];
+          a1 += wx[sx] * r0[cells + sx];
         }
         acc0 += wy * a0;
         acc1 += wy * a1;
       }
     }
-    const float d0 = 2.0f * (A.Ub[b * 2] - acc0), d1 = 2.0f * (A.Ub[b * 2 + 1] - acc1);
+    const float d0 = 2.0f * (Ux - acc0), d1 = 2.0f * (Uy - acc1);
     A.dFb[b * 2] = d0;
     A.dFb[b * 2 + 1] = d1;
     if (m == 1) {
@@ -277,21 +292,34 @@ __global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A, 
 // Spreading (Eq. 48): each lane spreads its points into the box with shared-memory
 // atomics; then the warp adds the non-zero box cells to f_IB with one global atomic
 // per cell and component.
+template <int SC>
 __global__ void __launch_bounds__(kIbmWarps * 32) ibm_spread2_kernel(IbmArgs A) {
   extern __shared__ float smem2[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int i = blockIdx.x * kIbmWarps + wib;
   if (i >= A.np) return;  // whole warp
-  const int S = A.box, P = S + 1, cells = S * P;
+  const int S = SC ? SC : A.box, P = S + 1, cells = S * P;
   float* box = smem2 + (size_t)wib * 2 * cells;
+  const bool has0 = lane < A.nl;
+  const long long b0 = (long long)i * A.nl + lane;
+  long long X0x = 0, X0y = 0;
+  float F0x = 0.0f, F0y = 0.0f;
+  if (has0) {
+    X0x = A.Xb[b0 * 2];
+    X0y = A.Xb[b0 * 2 + 1];
+    F0x = A.dFb[b0 * 2];
+    F0y = A.dFb[b0 * 2 + 1];
+  }
   for (int t = lane; t < 2 * cells; t += 32) box[t] = 0.0f;
   const int ox = fix_anchor(A.Xcf[(long long)i * 2 + 0]) - A.rcell - 2;
   const int oy = fix_anchor(A.Xcf[(long long)i * 2 + 1]) - A.rcell - 2;
   __syncwarp();
   for (int k = lane; k < A.nl; k += 32) {
     const long long b = (long long)i * A.nl + k;
-    const long long Xx = A.Xb[b * 2], Xy = A.Xb[b * 2 + 1];
-    const float fx = A.dFb[b * 2] * A.dV, fy = A.dFb[b * 2 + 1] * A.dV;
+    const bool first = k == lane;
+    const long long Xx = first ? X0x : A.Xb[b * 2], Xy = first ? X0y : A.Xb[b * 2 + 1];
+    const float fx = (first ? F0x : A.dFb[b * 2]) * A.dV;
+    const float fy = (first ? F0y : A.dFb[b * 2 + 1]) * A.dV;
     const int bx = fix_anchor(Xx) - 1, by = fix_anchor(Xy) - 1;
     const float rx = fix_frac(Xx), ry = fix_frac(Xy);
     if (bx - ox < 0 || by - oy < 0 || bx - ox + 3 >= S || by - oy + 3 >= S) {
@@ -532,10 +560,16 @@ cudaError_t launch_ibm_interp(const IbmArgs& A, int m, cudaStream_t s) {
   if (A.npts == 0) return cudaSuccess;
   if (A.D == 2) {
     const unsigned grid = (unsigned)((A.np + kIbmWarps - 1) / kIbmWarps);
-    if (A.parity == 0)
-      ibm_interp2_kernel<0><<<grid, kIbmWarps * 32, ibm_box2_smem(A.box), s>>>(A, m);
-    else
-      ibm_interp2_kernel<1><<<grid, kIbmWarps * 32, ibm_box2_smem(A.box), s>>>(A, m);
+    const size_t sm = ibm_box2_smem(A.box);
+#define IBMLBM_INTERP2(SC)                                                          \
+  do {                                                                               \
+    if (A.parity == 0) ibm_interp2_kernel<SC, 0><<<grid, kIbmWarps * 32, sm, s>>>(A, m); \
+    else ibm_interp2_kernel<SC, 1><<<grid, kIbmWarps * 32, sm, s>>>(A, m);            \
+  } while (0)
+    if (A.box == 16) IBMLBM_INTERP2(16);
+    else if (A.box == 22) IBMLBM_INTERP2(22);
+    else IBMLBM_INTERP2(0);
+#undef IBMLBM_INTERP2
   } else {
     const unsigned grid = (unsigned)((A.npts + 255) / 256);
     ibm_interp_kernel<3><<<grid, 256, 0, s>>>(A, m);
@@ -559,11 +593,16 @@ cudaError_t prepare_ibm_spread(int D, size_t smem) {
   if (smem <= g) return cudaSuccess;
   cudaError_t e;
   if (D == 2) {
-    e = cudaFuncSetAttribute(ibm_spread2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ibm_interp2_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ibm_interp2_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const void* fns[] = {
+        (const void*)ibm_spread2_kernel<16>, (const void*)ibm_spread2_kernel<22>,
+        (const void*)ibm_spread2_kernel<0>,  (const void*)ibm_interp2_kernel<16, 0>,
+        (const void*)ibm_interp2_kernel<16, 1>, (const void*)ibm_interp2_kernel<22, 0>,
+        (const void*)ibm_interp2_kernel<22, 1>, (const void*)ibm_interp2_kernel<0, 0>,
+        (const void*)ibm_interp2_kernel<0, 1>};
+    e = cudaSuccess;
+    for (const void* fn : fns)
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   } else {
     e = cudaFuncSetAttribute(ibm_spread_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
@@ -575,7 +614,13 @@ cudaError_t launch_ibm_spread(const IbmArgs& A, cudaStream_t s) {
   if (A.np == 0) return cudaSuccess;
   if (A.D == 2) {
     const unsigned grid = (unsigned)((A.np + kIbmWarps - 1) / kIbmWarps);
-    ibm_spread2_kernel<<<grid, kIbmWarps * 32, ibm_box2_smem(A.box), s>>>(A);
+    const size_t sm = ibm_box2_smem(A.box);
+    if (A.box == 16)
+      ibm_spread2_kernel<16><<<grid, kIbmWarps * 32, sm, s>>>(A);
+    else if (A.box == 22)
+      ibm_spread2_kernel<22><<<grid, kIbmWarps * 32, sm, s>>>(A);
+    else
+      ibm_spread2_kernel<0><<<grid, kIbmWarps * 32, sm, s>>>(A);
   } else {
     ibm_spread_kernel<3><<<A.np, 256, ibm_spread_smem(3, A.nl, A.box), s>>>(A);
   }
