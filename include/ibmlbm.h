@@ -81,7 +81,9 @@ int ibm_lbm_workspace_size(const ibm_lbm_config* cfg, size_t* bytes);
 
 /* Create a run.  d_workspace: device memory of at least ibm_lbm_workspace_size
  * bytes, borrowed (not owned) until ibm_lbm_destroy.  stream: every kernel and
- * copy of the run is ordered on it.  h_centres: host [n_particles][dim] particle
+ * copy of the run is ordered on it (within a step the particle update runs on a
+ * second stream the run owns, forked from and joined back into this one, so work
+ * enqueued on it after a step sees the whole step).  h_centres: host [n_particles][dim] particle
  * centres (may be NULL when n_particles = 0).  The fluid starts at rest with
  * p = 0 (every PDF zero, the deviation gauge of the incompressible model) and the
  * particles with U = Omega = 0.  Copies the centres to the device and waits for

@@ -162,9 +162,9 @@ Layout carve(const ibm_lbm_config* c, const Derived& d) {
   const size_t N = (size_t)d.g.N, np = (size_t)c->n_particles, D = d.D;
   const size_t npts = (size_t)d.npts;
   l.f = cv.take(sizeof(float) * d.Q * N);
-  l.ustar = cv.take(sizeof(float) * D * N);
+  l.ustar = cv.take(D == 3 ? sizeof(float) * D * N : 0);  // 2D keeps u* per particle box (ubox)
   l.fib = cv.take(sizeof(float) * D * N);
-  l.mask = cv.take(sizeof(uint32_t) * (size_t)d.g.rows * d.g.wpr);
+  l.mask = cv.take(D == 3 ? sizeof(uint32_t) * (size_t)d.g.rows * d.g.wpr : 0);  // 3D only
   l.X0 = cv.take(sizeof(double) * np * D);
   l.X1 = cv.take(sizeof(double) * np * D);
   l.U = cv.take(sizeof(double) * np * D);
@@ -192,8 +192,8 @@ Layout carve(const ibm_lbm_config* c, const Derived& d) {
   l.Fb = cv.take(sizeof(float) * npts * D);
   l.dFb = cv.take(sizeof(float) * npts * D);
   l.ubs = cv.take(sizeof(float) * npts * D);
-  // 2D: u* of each particle's node box (box x (box + 1) per component)
-  l.ubox = cv.take(D == 2 ? sizeof(float) * np * 2 * (size_t)d.box * (d.box + 1) : 0);
+  // 2D: u* of each particle's node box (box rows of box_pitch(box) float2 cells)
+  l.ubox = cv.take(D == 2 ? sizeof(float) * np * 2 * (size_t)d.box * box_pitch(d.box) : 0);
   const size_t ncells = (size_t)d.nc[0] * d.nc[1] * d.nc[2];
   l.cell_count = cv.take(sizeof(int) * ncells);
   l.cell_ids = cv.take(sizeof(int) * ncells * cell_capacity(c->n_particles, (long long)ncells));
@@ -235,6 +235,10 @@ struct ibm_lbm_handle {
   Layout l;
   char* ws;
   cudaStream_t s;
+  // second stream for the particle work that runs beside lbm_step, and the events
+  // that fork it from and join it back into s
+  cudaStream_t side;
+  cudaEvent_t fork, join;
   long long step;
   int have_prev;
   int64_t launches;
@@ -400,6 +404,33 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
     ++k;
   }
   if (ev) CUDA_TRY(cudaEventRecord(ev[2], s));
+  if (particles && !ev) {
+    // The contact forces, the Newton-Euler update and (2D) the regeneration of the
+    // points read nothing lbm_step writes and write nothing it reads, so they run on
+    // the side stream while lbm_step streams the PDFs.  3D regeneration marks the node
+    // mask that lbm_step clears, so it waits for lbm_step.
+    CUDA_TRY(cudaEventRecord(h->fork, s));
+    CUDA_TRY(cudaStreamWaitEvent(h->side, h->fork, 0));
+    const PairArgs pa = h->pairs(parity, have_prev);
+    CUDA_TRY(launch_pair_cells(pa, h->side));
+    CUDA_TRY(launch_pair_contacts(pa, h->side));
+    k += 3;
+    if (h->d.D == 2) {
+      CUDA_TRY(launch_regen(h->regen(1 - parity), 0, h->side));
+      ++k;
+    }
+    CUDA_TRY(cudaEventRecord(h->join, h->side));
+    CUDA_TRY(launch_lbm_step(la, h->d.D, parity, s));
+    ++k;
+    CUDA_TRY(cudaStreamWaitEvent(s, h->join, 0));
+    if (h->d.D == 3) {
+      CUDA_TRY(launch_regen(h->regen(1 - parity), 0, s));
+      ++k;
+    }
+    *nk = k;
+    return IBMLBM_OK;
+  }
+  // one part after the other (no particles, or timed parts)
   CUDA_TRY(launch_lbm_step(la, h->d.D, parity, s));
   ++k;
   if (ev) CUDA_TRY(cudaEventRecord(ev[3], s));
@@ -509,7 +540,12 @@ int ibm_lbm_init(const ibm_lbm_config* cfg, void* d_workspace, size_t bytes, voi
   h->launches = 0;
   h->graph_ok[0] = h->graph_ok[1] = false;
   h->graph_tried[0] = h->graph_tried[1] = false;
+  h->side = nullptr;
+  h->fork = h->join = nullptr;
   auto bail = [&](int code) {
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->join) cudaEventDestroy(h->join);
     delete h;
     return code;
   };
@@ -520,6 +556,9 @@ int ibm_lbm_init(const ibm_lbm_config* cfg, void* d_workspace, size_t bytes, voi
       return bail(fail(IBMLBM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_))); \
   } while (0)
   INIT_TRY(cudaMemsetAsync(h->ws, 0, l.total, h->s));
+  INIT_TRY(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  INIT_TRY(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
+  INIT_TRY(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
   if (cfg->n_particles > 0) {
     INIT_TRY(cudaMemcpyAsync(h->at<double>(l.X0), h_centres,
                              sizeof(double) * (size_t)cfg->n_particles * d.D,
@@ -790,6 +829,12 @@ void ibm_lbm_destroy(ibm_lbm_handle* h) {
   if (!h) return;
   for (int p = 0; p < 2; ++p)
     if (h->graph_ok[p]) cudaGraphExecDestroy(h->graph[p]);
+  if (h->side) {
+    cudaStreamSynchronize(h->side);
+    cudaStreamDestroy(h->side);
+  }
+  if (h->fork) cudaEventDestroy(h->fork);
+  if (h->join) cudaEventDestroy(h->join);
   delete h;
 }
 

@@ -7,7 +7,8 @@
 // Data layout in HBM (one workspace, carved by the host):
 //   f      [Q][N]  float  PDFs, one copy, AA-pattern in-place streaming
 //   ustar  [D][N]  float  u* = sum_a e_a f_a, written only on flagged nodes
-//   fib    [D][N]  float  IB force density; zero outside the IBM phase
+//   fib    float  IB force density, zero outside the IBM phase: 2D [N][2]
+//                 (interleaved), 3D [3][N]
 //   mask   [rows][wpr] u32  one bit per node: nodes within R + 2 sqrt(D) of a
 //                           particle centre (support of every Lagrangian point
 //                           and the particle interior)
@@ -124,6 +125,14 @@ __device__ __forceinline__ FF ff_warp_sum(FF s) {
 }
 __device__ __forceinline__ double ff_value(FF s) { return (double)s.hi + (double)s.lo; }
 
+// Row pitch (in cells) of a 2D particle box of side S: at least S, and 4 or 12 modulo
+// 16, so the 16 cells of a 4 x 4 support of float2 cells use 16 different bank pairs.
+__host__ __device__ inline int box_pitch(int S) {
+  int p = S;
+  while ((p & 15) != 4 && (p & 15) != 12) ++p;
+  return p;
+}
+
 // ------------------------------------------------------------ kernel arguments
 struct LbmArgs {
   Geo g;
@@ -150,7 +159,7 @@ struct IbmArgs {
   float* fib;
   const float* f;        // 2D: the PDFs, for u* of each particle's box
   int parity;            // 2D: AA parity of the PDFs
-  float* ubox;           // 2D: [np][2][box][box + 1] u* of each particle's box
+  float* ubox;           // 2D: [np][box][box_pitch(box)] float2, u* of each particle's box
   const long long* Xb;  // [npts][D] fixed point
   const float* Ub;   // [npts][D]
   float* Fb;         // [npts][D] sum of MDF increments

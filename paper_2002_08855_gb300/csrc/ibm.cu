@@ -176,27 +176,69 @@ __global__ void __launch_bounds__(256) ibm_spread_kernel(IbmArgs A) {
 }
 
 // 2D kernels with one warp per particle and the particle's node box in shared memory
-// (kIbmWarps particles per block, box rows padded by one float against bank
-// conflicts, no block-wide barrier).
+// (kIbmWarps particles per block, no block-wide barrier).  A box cell holds both
+// components (float2); rows are box_pitch(S) cells apart, so the 4 x 4 support of a
+// point falls on 16 different bank pairs.  In the later interpolations the box
+// reaches shared memory through cp.async, so all of a warp's loads are in flight at
+// once.  f_IB is stored interleaved in 2D ([N][2]).
 constexpr int kIbmWarps = 8;
 
-size_t ibm_box2_smem(int box) { return sizeof(float) * 2 * (size_t)box * (box + 1) * kIbmWarps; }
+__device__ __forceinline__ void cp_async8(float2* dst, const float2* src, bool pred) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(pred ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Interpolation (Eq. 47), iteration m.  In the first iteration (or m = 0: box only,
-// when no forcing iteration runs) the warp computes u* (Eq. 5) of every
-// node of the particle's box from the PDFs (coalesced row loads, AA-parity layout) and
-// keeps it in the particle's box buffer; later iterations stage that buffer plus
-// f_IB/2.  Lane k then interpolates point k from shared memory.  Box nodes beyond a
-// wall hold zero, which drops them from the sum.
-template <int SC, int PARITY>
+// floats of shared memory per warp: the box [S][P] float2, then
+//   interpolation, mode 1: f_IB of the box [S][P] float2;
+//   spreading: the point table, weights [32][17] and (F_x, F_y, first cell) [32] float4.
+constexpr int kTw = 17;  // 16 node weights per point (+1 against bank conflicts)
+__host__ __device__ inline int interp2_warp_floats(int mode, int S) {
+  return 2 * S * box_pitch(S) * (mode == 0 ? 1 : 2);
+}
+__host__ __device__ inline int spread2_warp_floats(int S) { return 2 * S * box_pitch(S) + 32 * kTw + 32 * 4; }
+
+size_t ibm_box2_smem(int box) {
+  const int a = interp2_warp_floats(1, box), c = spread2_warp_floats(box);
+  return sizeof(float) * (size_t)kIbmWarps * (size_t)max(a, c);
+}
+
+// box node (row r, column c) -> grid node; false beyond a wall
+__device__ __forceinline__ bool box_node(const Geo& g, int ox, int oy, int r, int c, int& gx, int& gy) {
+  gx = ox + c;
+  gy = oy + r;
+  bool ok = true;
+  if (gx < 0 || gx >= g.nx) {
+    if (g.per[0]) gx = ((gx % g.nx) + g.nx) % g.nx; else ok = false;
+  }
+  if (gy < 0 || gy >= g.ny) {
+    if (g.per[1]) gy = ((gy % g.ny) + g.ny) % g.ny; else ok = false;
+  }
+  return ok;
+}
+
+// Interpolation (Eq. 47), iteration m.
+//   MODE 0 (m = 1, or m = 0: box only, when no forcing iteration runs): u* (Eq. 5) of
+//     every node of the particle's box from the PDFs (AA-parity addressing), kept in
+//     the particle's box buffer for the later iterations and the interior sums;
+//   MODE 1 (m >= 2): the box buffer plus f_IB/2.
+// Lane k then interpolates point k from shared memory.  Box nodes beyond a wall hold
+// zero, which drops them from the sum.
+template <int SC, int PARITY, int MODE>
 __global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A, int m) {
-  extern __shared__ float smem_i[];
+  extern __shared__ __align__(16) float smem_i[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int i = blockIdx.x * kIbmWarps + wib;
   if (i >= A.np) return;  // whole warp
-  const int S = SC ? SC : A.box, P = S + 1, cells = S * P;
-  float* box = smem_i + (size_t)wib * 2 * cells;
-  float* ub = A.ubox + (size_t)i * 2 * cells;
+  const int S = SC ? SC : A.box, P = box_pitch(S), cells = S * P;
+  float2* box = reinterpret_cast<float2*>(smem_i + (size_t)wib * interp2_warp_floats(MODE, S));
+  float2* aux = box + cells;
+  float2* ub = reinterpret_cast<float2*>(A.ubox) + (size_t)i * cells;
   // the first point of this lane is loaded before the box, so both latencies overlap
   const bool has0 = m > 0 && lane < A.nl;
   const long long b0 = (long long)i * A.nl + lane;
@@ -210,42 +252,34 @@ __global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A, 
   }
   const int ox = fix_anchor(A.Xcf[(long long)i * 2 + 0]) - A.rcell - 2;
   const int oy = fix_anchor(A.Xcf[(long long)i * 2 + 1]) - A.rcell - 2;
-  const long long N = A.g.N;
-  for (int t = lane; t < S * S; t += 32) {
-    const int r = t / S, c = t - r * S;
-    int gx = ox + c, gy = oy + r;
-    bool ok = true;
-    if (gx < 0 || gx >= A.g.nx) {
-      if (A.g.per[0]) gx = ((gx % A.g.nx) + A.g.nx) % A.g.nx; else ok = false;
-    }
-    if (gy < 0 || gy >= A.g.ny) {
-      if (A.g.per[1]) gy = ((gy % A.g.ny) + A.g.ny) % A.g.ny; else ok = false;
-    }
-    float v0 = 0.0f, v1 = 0.0f;
-    const long long n = (long long)gx + (long long)A.g.nx * gy;
-    if (m <= 1) {
-      if (ok) {
+  if (MODE == 0) {
+    for (int t = lane; t < S * S; t += 32) {
+      const int r = t / S, c = t - r * S;
+      int gx, gy;
+      float2 v = make_float2(0.0f, 0.0f);
+      if (box_node(A.g, ox, oy, r, c, gx, gy)) {
         float fa[9], us[3], s1;
-        load_pdfs<Lat<2>, PARITY>(A.g, A.f, gx, gy, 0, n, fa);
+        load_pdfs<Lat<2>, PARITY>(A.g, A.f, gx, gy, 0, (long long)gx + (long long)A.g.nx * gy, fa);
         moments<Lat<2>>(fa, us, s1);
-        v0 = us[0];
-        v1 = us[1];
+        v = make_float2(us[0], us[1]);
       }
-      ub[r * P + c] = v0;
-      ub[cells + r * P + c] = v1;
-    } else {
-      v0 = ub[r * P + c];
-      v1 = ub[cells + r * P + c];
-      if (ok) {
-        v0 += 0.5f * A.fib[n];
-        v1 += 0.5f * A.fib[N + n];
-      }
+      box[r * P + c] = v;
+      ub[r * P + c] = v;
     }
-    box[r * P + c] = v0;
-    box[cells + r * P + c] = v1;
+    __syncwarp();
+    if (m == 0) return;  // box u* only (no multi-direct forcing iteration this step)
+  } else {
+    for (int q = lane; q < cells / 2; q += 32) cp_async16(box + 2 * q, ub + 2 * q);
+    const float2* fib2 = reinterpret_cast<const float2*>(A.fib);
+    for (int t = lane; t < S * S; t += 32) {
+      const int r = t / S, c = t - r * S;
+      int gx, gy;
+      const bool ok = box_node(A.g, ox, oy, r, c, gx, gy);
+      cp_async8(aux + r * P + c, fib2 + (ok ? (long long)gx + (long long)A.g.nx * gy : 0), ok);
+    }
+    cp_async_wait_all();
+    __syncwarp();
   }
-  if (m == 0) return;  // box u* only (no multi-direct forcing iteration this step)
-  __syncwarp();
   for (int k = lane; k < A.nl; k += 32) {
     const long long b = (long long)i * A.nl + k;
     const bool first = k == lane;
@@ -263,12 +297,18 @@ __global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A, 
 #pragma unroll
       for (int sy = 0; sy < 4; ++sy) {
         const float wy = delta4((float)(sy - 1) - ry);
-        const float* r0 = box + (ly0 + sy) * P + lx0;
+        const int o = (ly0 + sy) * P + lx0;
         float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
         for (int sx = 0; sx < 4; ++sx) {
-          a0 += wx[sx] * r0[sx];
-          a1 += wx[sx] * r0[cells + sx];
+          float2 v = box[o + sx];
+          if (MODE == 1) {
+            const float2 h = aux[o + sx];
+            v.x += 0.5f * h.x;
+            v.y += 0.5f * h.y;
+          }
+          a0 += wx[sx] * v.x;
+          a1 += wx[sx] * v.y;
         }
         acc0 += wy * a0;
         acc1 += wy * a1;
@@ -289,75 +329,150 @@ __global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A, 
   }
 }
 
-// Spreading (Eq. 48): each lane spreads its points into the box with shared-memory
-// atomics; then the warp adds the non-zero box cells to f_IB with one global atomic
-// per cell and component.
+// Spreading (Eq. 48) without shared-memory atomics.  The point's owner lane writes a
+// table row (the 16 products delta_x delta_y dV of its support, its force, the box
+// cell of its first support node).  Then the 16 lanes of each half-warp take one point
+// each, one support node per lane: half 0 point j, half 1 point j + H (H = half the
+// group), about a diameter apart on the circle.  Where the two supports could share a
+// node (anchors at most 3 apart on both axes) the halves take turns.  So no two lanes
+// of an instruction touch one cell and plain read-add-write is exact.  Finally the warp
+// adds the non-zero box cells to f_IB with one global vector atomic per cell.
 template <int SC>
 __global__ void __launch_bounds__(kIbmWarps * 32) ibm_spread2_kernel(IbmArgs A) {
-  extern __shared__ float smem2[];
+  extern __shared__ __align__(16) float smem2[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int i = blockIdx.x * kIbmWarps + wib;
   if (i >= A.np) return;  // whole warp
-  const int S = SC ? SC : A.box, P = S + 1, cells = S * P;
-  float* box = smem2 + (size_t)wib * 2 * cells;
-  const bool has0 = lane < A.nl;
-  const long long b0 = (long long)i * A.nl + lane;
-  long long X0x = 0, X0y = 0;
-  float F0x = 0.0f, F0y = 0.0f;
-  if (has0) {
-    X0x = A.Xb[b0 * 2];
-    X0y = A.Xb[b0 * 2 + 1];
-    F0x = A.dFb[b0 * 2];
-    F0y = A.dFb[b0 * 2 + 1];
-  }
-  for (int t = lane; t < 2 * cells; t += 32) box[t] = 0.0f;
+  const int S = SC ? SC : A.box, P = box_pitch(S), cells = S * P;
+  float* base = smem2 + (size_t)wib * spread2_warp_floats(S);
+  float2* box = reinterpret_cast<float2*>(base);
+  float* tw = base + 2 * cells;                                   // [32][kTw]
+  float4* tp = reinterpret_cast<float4*>(tw + 32 * kTw);          // [32]
   const int ox = fix_anchor(A.Xcf[(long long)i * 2 + 0]) - A.rcell - 2;
   const int oy = fix_anchor(A.Xcf[(long long)i * 2 + 1]) - A.rcell - 2;
-  __syncwarp();
-  for (int k = lane; k < A.nl; k += 32) {
-    const long long b = (long long)i * A.nl + k;
-    const bool first = k == lane;
-    const long long Xx = first ? X0x : A.Xb[b * 2], Xy = first ? X0y : A.Xb[b * 2 + 1];
-    const float fx = (first ? F0x : A.dFb[b * 2]) * A.dV;
-    const float fy = (first ? F0y : A.dFb[b * 2 + 1]) * A.dV;
-    const int bx = fix_anchor(Xx) - 1, by = fix_anchor(Xy) - 1;
-    const float rx = fix_frac(Xx), ry = fix_frac(Xy);
-    if (bx - ox < 0 || by - oy < 0 || bx - ox + 3 >= S || by - oy + 3 >= S) {
-      atomicOr(A.status, ST_CAPACITY);
-      continue;
-    }
-    float wx[4];
+  const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  for (int q = lane; q < cells / 2; q += 32) reinterpret_cast<float4*>(box)[q] = z4;
+  const int h = lane >> 4, sx = lane & 3, sy = (lane >> 2) & 3;
+  for (int g0 = 0; g0 < A.nl; g0 += 32) {
+    const int cnt = min(32, A.nl - g0), H = (cnt + 1) >> 1;
+    // owner lane: the table row of point g0 + lane
+    int lbx = 0, lby = 0;
+    bool valid = false;
+    if (lane < cnt) {
+      const long long b = (long long)i * A.nl + g0 + lane;
+      const long long Xx = A.Xb[b * 2], Xy = A.Xb[b * 2 + 1];
+      const float fx = A.dFb[b * 2] * A.dV, fy = A.dFb[b * 2 + 1] * A.dV;
+      const int bx = fix_anchor(Xx) - 1, by = fix_anchor(Xy) - 1;
+      const float rx = fix_frac(Xx), ry = fix_frac(Xy);
+      lbx = bx - ox;
+      lby = by - oy;
+      valid = lbx >= 0 && lby >= 0 && lbx + 3 < S && lby + 3 < S;
+      if (!valid) atomicOr(A.status, ST_CAPACITY);
+      float wx[4], wy[4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) wx[t] = delta4((float)(t - 1) - rx);
-#pragma unroll
-    for (int sy = 0; sy < 4; ++sy) {
-      const int gy = by + sy;
-      if (!A.g.per[1] && (gy < 0 || gy >= A.g.ny)) continue;
-      const float wy = delta4((float)(sy - 1) - ry);
-      float* r0 = box + (gy - oy) * P + (bx - ox);
-#pragma unroll
-      for (int sx = 0; sx < 4; ++sx) {
-        const int gx = bx + sx;
-        if (!A.g.per[0] && (gx < 0 || gx >= A.g.nx)) continue;
-        const float w = wx[sx] * wy;
-        atomicAdd(r0 + sx, fx * w);
-        atomicAdd(r0 + cells + sx, fy * w);
+      for (int t = 0; t < 4; ++t) {
+        const int gx = bx + t, gy = by + t;
+        wx[t] = (!A.g.per[0] && (gx < 0 || gx >= A.g.nx)) ? 0.0f : delta4((float)(t - 1) - rx);
+        wy[t] = (!A.g.per[1] && (gy < 0 || gy >= A.g.ny)) ? 0.0f : delta4((float)(t - 1) - ry);
       }
+      float* row = tw + lane * kTw;
+#pragma unroll
+      for (int t = 0; t < 16; ++t) row[t] = wx[t & 3] * wy[t >> 2];
+      tp[lane] = make_float4(fx, fy, __int_as_float(valid ? lby * P + lbx : 0), 0.0f);
+    }
+    // the two supports of a pass could share a node: anchors at most 3 apart on both axes
+    const int pbx = __shfl_sync(0xffffffffu, lbx, min(lane + H, 31));
+    const int pby = __shfl_sync(0xffffffffu, lby, min(lane + H, 31));
+    const bool clash = lane < H && lane + H < cnt && abs(lbx - pbx) <= 3 && abs(lby - pby) <= 3;
+    const unsigned cmask = __ballot_sync(0xffffffffu, clash);
+    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+    __syncwarp();
+    for (int j = 0; j < H; ++j) {
+      const int p = j + h * H;
+      const bool act = p < cnt && ((vmask >> p) & 1u);
+      float4 pd = z4;
+      float w = 0.0f;
+      if (act) {
+        pd = tp[p];
+        w = tw[p * kTw + (lane & 15)];
+      }
+      const int cell = __float_as_int(pd.z) + sy * P + sx;
+      if ((cmask >> j) & 1u) {
+        if (h == 0 && act) {
+          float2 v = box[cell];
+          v.x += w * pd.x;
+          v.y += w * pd.y;
+          box[cell] = v;
+        }
+        __syncwarp();
+        if (h == 1 && act) {
+          float2 v = box[cell];
+          v.x += w * pd.x;
+          v.y += w * pd.y;
+          box[cell] = v;
+        }
+      } else if (act) {
+        float2 v = box[cell];
+        v.x += w * pd.x;
+        v.y += w * pd.y;
+        box[cell] = v;
+      }
+      __syncwarp();
     }
   }
-  __syncwarp();
+  float2* fib2 = reinterpret_cast<float2*>(A.fib);
   for (int t = lane; t < S * S; t += 32) {
     const int r = t / S, c = t - r * S;
-    const float v0 = box[r * P + c], v1 = box[cells + r * P + c];
-    if (v0 == 0.0f && v1 == 0.0f) continue;
+    const float2 v = box[r * P + c];
+    if (v.x == 0.0f && v.y == 0.0f) continue;
     int gx = ox + c, gy = oy + r;
     if (gx < 0 || gx >= A.g.nx) gx = ((gx % A.g.nx) + A.g.nx) % A.g.nx;  // only periodic
     if (gy < 0 || gy >= A.g.ny) gy = ((gy % A.g.ny) + A.g.ny) % A.g.ny;  // axes reach here
-    const long long n = (long long)gx + (long long)A.g.nx * gy;
-    if (v0 != 0.0f) atomicAdd(&A.fib[n], v0);
-    if (v1 != 0.0f) atomicAdd(&A.fib[A.g.N + n], v1);
+    atomicAdd(fib2 + ((long long)gx + (long long)A.g.nx * gy), v);
   }
 }
+
+// F_h, T_h of particle i from its points, and the write of the warp's sums (lane 0)
+template <int D>
+__device__ __forceinline__ void forces_finish(const IbmArgs& A, int i, int lane, FF (&P)[3], FF (&L)[3]) {
+  FF sF[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, sT[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  for (int k = lane; k < A.nl; k += 32) {
+    const long long b = (long long)i * A.nl + k;
+    float r[3] = {0.0f, 0.0f, 0.0f}, F[3] = {0.0f, 0.0f, 0.0f};
+    for (int c = 0; c < D; ++c) {
+      r[c] = A.ref_f[k * D + c];
+      F[c] = A.Fb[b * D + c];
+      ff_add(sF[c], F[c]);
+    }
+    if (D == 3) {
+      ff_add(sT[0], r[1] * F[2] - r[2] * F[1]);
+      ff_add(sT[1], r[2] * F[0] - r[0] * F[2]);
+    }
+    ff_add(sT[2], r[0] * F[1] - r[1] * F[0]);
+  }
+  // only the components that exist in this dimension (2D: x, y and the z rotation)
+  for (int c = 0; c < D; ++c) {
+    P[c] = ff_warp_sum(P[c]);
+    sF[c] = ff_warp_sum(sF[c]);
+  }
+  for (int c = (D == 2 ? 2 : 0); c < 3; ++c) {
+    L[c] = ff_warp_sum(L[c]);
+    sT[c] = ff_warp_sum(sT[c]);
+  }
+  if (lane == 0) {
+    const double dV = (double)A.dV;
+    for (int c = 0; c < D; ++c) {
+      A.Pint[(long long)i * D + c] = ff_value(P[c]);
+      A.FhN[(long long)i * D + c] = -dV * ff_value(sF[c]);
+    }
+    for (int c = 0; c < 3; ++c) {
+      const bool used = !(D == 2 && c < 2);
+      A.Lint[(long long)i * 3 + c] = used ? ff_value(L[c]) : 0.0;
+      A.ThN[(long long)i * 3 + c] = used ? -dV * ff_value(sT[c]) : 0.0;
+    }
+  }
+}
+
 
 // Per particle (one warp), after the last MDF iteration:
 //   F_h = -dV sum_b F_b, T_h = -dV sum_b r_b x F_b            (Eq. 14-15, via BTDF)
@@ -412,16 +527,7 @@ __global__ void __launch_bounds__(256) ibm_forces_kernel(IbmArgs A) {
     if (!ok) continue;
     const long long nn = (long long)gc[0] + (long long)A.g.nx * ((long long)gc[1] + (long long)A.g.ny * gc[2]);
     float u[3] = {0.0f, 0.0f, 0.0f};
-    if (D == 2) {  // u* from the particle's box buffer (box coordinates, unwrapped)
-      const int S = A.box, P = S + 1, cells = S * P;
-      const int lc = (lo[0] + t % ext[0]) - (an[0] - A.rcell - 2);
-      const int lr = (lo[1] + (t / ext[0]) % ext[1]) - (an[1] - A.rcell - 2);
-      const float* ub = A.ubox + (size_t)i * 2 * cells + lr * P + lc;
-      u[0] = ub[0] + 0.5f * A.fib[nn];
-      u[1] = ub[cells] + 0.5f * A.fib[A.g.N + nn];
-    } else {
-      for (int c = 0; c < D; ++c) u[c] = A.ustar[c * A.g.N + nn] + 0.5f * A.fib[c * A.g.N + nn];
-    }
+    for (int c = 0; c < D; ++c) u[c] = A.ustar[c * A.g.N + nn] + 0.5f * A.fib[c * A.g.N + nn];
     for (int c = 0; c < D; ++c) ff_add(P[c], u[c]);
     if (D == 3) {
       ff_add(L[0], r[1] * u[2] - r[2] * u[1]);
@@ -429,42 +535,72 @@ __global__ void __launch_bounds__(256) ibm_forces_kernel(IbmArgs A) {
     }
     ff_add(L[2], r[0] * u[1] - r[1] * u[0]);
   }
-  FF sF[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, sT[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-  for (int k = lane; k < A.nl; k += 32) {
-    const long long b = (long long)i * A.nl + k;
-    float r[3] = {0.0f, 0.0f, 0.0f}, F[3] = {0.0f, 0.0f, 0.0f};
-    for (int c = 0; c < D; ++c) {
-      r[c] = A.ref_f[k * D + c];
-      F[c] = A.Fb[b * D + c];
-      ff_add(sF[c], F[c]);
+  forces_finish<D>(A, i, lane, P, L);
+}
+
+// 2D form of the same sums, with u* from the particle's box buffer.  Each lane takes
+// its candidate nodes kForceBatch at a time, so their loads are in flight together.
+constexpr int kForceBatch = 6;
+
+template <int SC>
+__global__ void __launch_bounds__(256) ibm_forces2_kernel(IbmArgs A) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= A.np) return;
+  const int S = SC ? SC : A.box, W = box_pitch(S), cells = S * W, ext = S - 4;  // ext = 2 rcell + 2
+  const long long vx = A.Xcf[(long long)i * 2], vy = A.Xcf[(long long)i * 2 + 1];
+  const int anx = fix_anchor(vx), any = fix_anchor(vy);
+  const float frx = fix_frac(vx), fry = fix_frac(vy);
+  const int lox = anx - A.rcell, loy = any - A.rcell;
+  const float R2f = A.radius_f * A.radius_f;
+  const float band = 1e-4f * R2f + 1e-5f;
+  const float2* ub = reinterpret_cast<const float2*>(A.ubox) + (size_t)i * cells;
+  const float2* fib2 = reinterpret_cast<const float2*>(A.fib);
+  FF P[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, L[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  for (int t0 = 0; t0 < ext * ext; t0 += 32 * kForceBatch) {
+    float rx[kForceBatch], ry[kForceBatch], u0[kForceBatch], u1[kForceBatch];
+    bool in[kForceBatch];
+#pragma unroll
+    for (int q = 0; q < kForceBatch; ++q) {
+      const int t = t0 + lane + 32 * q;
+      in[q] = false;
+      rx[q] = ry[q] = u0[q] = u1[q] = 0.0f;
+      if (t >= ext * ext) continue;
+      const int cx = t % ext, cy = t / ext;
+      int gx = lox + cx, gy = loy + cy;
+      rx[q] = (float)(gx - anx) - frx;
+      ry[q] = (float)(gy - any) - fry;
+      const float d2 = rx[q] * rx[q] + ry[q] * ry[q];
+      bool inside = d2 < R2f;
+      if (fabsf(d2 - R2f) < band) {
+        const double dx = (double)gx - A.Xc[(long long)i * 2], dy = (double)gy - A.Xc[(long long)i * 2 + 1];
+        inside = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) < __dmul_rn(A.radius, A.radius);
+      }
+      if (!inside) continue;
+      if (gx < 0 || gx >= A.g.nx) {
+        if (!A.g.per[0]) continue;
+        gx = ((gx % A.g.nx) + A.g.nx) % A.g.nx;
+      }
+      if (gy < 0 || gy >= A.g.ny) {
+        if (!A.g.per[1]) continue;
+        gy = ((gy % A.g.ny) + A.g.ny) % A.g.ny;
+      }
+      const long long nn = (long long)gx + (long long)A.g.nx * gy;
+      const int o = (cy + 2) * W + (cx + 2);  // the box starts two nodes before lox, loy
+      const float2 us = ub[o], fv = fib2[nn];
+      u0[q] = us.x + 0.5f * fv.x;
+      u1[q] = us.y + 0.5f * fv.y;
+      in[q] = true;
     }
-    if (D == 3) {
-      ff_add(sT[0], r[1] * F[2] - r[2] * F[1]);
-      ff_add(sT[1], r[2] * F[0] - r[0] * F[2]);
-    }
-    ff_add(sT[2], r[0] * F[1] - r[1] * F[0]);
-  }
-  // only the components that exist in this dimension (2D: x, y and the z rotation)
-  for (int c = 0; c < D; ++c) {
-    P[c] = ff_warp_sum(P[c]);
-    sF[c] = ff_warp_sum(sF[c]);
-  }
-  for (int c = (D == 2 ? 2 : 0); c < 3; ++c) {
-    L[c] = ff_warp_sum(L[c]);
-    sT[c] = ff_warp_sum(sT[c]);
-  }
-  if (lane == 0) {
-    const double dV = (double)A.dV;
-    for (int c = 0; c < D; ++c) {
-      A.Pint[(long long)i * D + c] = ff_value(P[c]);
-      A.FhN[(long long)i * D + c] = -dV * ff_value(sF[c]);
-    }
-    for (int c = 0; c < 3; ++c) {
-      const bool used = !(D == 2 && c < 2);
-      A.Lint[(long long)i * 3 + c] = used ? ff_value(L[c]) : 0.0;
-      A.ThN[(long long)i * 3 + c] = used ? -dV * ff_value(sT[c]) : 0.0;
+#pragma unroll
+    for (int q = 0; q < kForceBatch; ++q) {
+      if (!in[q]) continue;
+      ff_add(P[0], u0[q]);
+      ff_add(P[1], u1[q]);
+      ff_add(L[2], rx[q] * u1[q] - ry[q] * u0[q]);
     }
   }
+  forces_finish<2>(A, i, lane, P, L);
 }
 
 // One warp per particle: regenerate its Lagrangian points for the next step,
@@ -560,11 +696,16 @@ cudaError_t launch_ibm_interp(const IbmArgs& A, int m, cudaStream_t s) {
   if (A.npts == 0) return cudaSuccess;
   if (A.D == 2) {
     const unsigned grid = (unsigned)((A.np + kIbmWarps - 1) / kIbmWarps);
-    const size_t sm = ibm_box2_smem(A.box);
-#define IBMLBM_INTERP2(SC)                                                          \
-  do {                                                                               \
-    if (A.parity == 0) ibm_interp2_kernel<SC, 0><<<grid, kIbmWarps * 32, sm, s>>>(A, m); \
-    else ibm_interp2_kernel<SC, 1><<<grid, kIbmWarps * 32, sm, s>>>(A, m);            \
+    const int mode = m <= 1 ? 0 : 1;
+    const size_t sm = sizeof(float) * kIbmWarps * (size_t)interp2_warp_floats(mode, A.box);
+#define IBMLBM_INTERP2(SC)                                                                   \
+  do {                                                                                        \
+    if (mode == 0) {                                                                          \
+      if (A.parity == 0) ibm_interp2_kernel<SC, 0, 0><<<grid, kIbmWarps * 32, sm, s>>>(A, m); \
+      else ibm_interp2_kernel<SC, 1, 0><<<grid, kIbmWarps * 32, sm, s>>>(A, m);               \
+    } else {                                                                                  \
+      ibm_interp2_kernel<SC, 0, 1><<<grid, kIbmWarps * 32, sm, s>>>(A, m);                    \
+    }                                                                                         \
   } while (0)
     if (A.box == 16) IBMLBM_INTERP2(16);
     else if (A.box == 22) IBMLBM_INTERP2(22);
@@ -594,11 +735,12 @@ cudaError_t prepare_ibm_spread(int D, size_t smem) {
   cudaError_t e;
   if (D == 2) {
     const void* fns[] = {
-        (const void*)ibm_spread2_kernel<16>, (const void*)ibm_spread2_kernel<22>,
-        (const void*)ibm_spread2_kernel<0>,  (const void*)ibm_interp2_kernel<16, 0>,
-        (const void*)ibm_interp2_kernel<16, 1>, (const void*)ibm_interp2_kernel<22, 0>,
-        (const void*)ibm_interp2_kernel<22, 1>, (const void*)ibm_interp2_kernel<0, 0>,
-        (const void*)ibm_interp2_kernel<0, 1>};
+        (const void*)ibm_spread2_kernel<16>,        (const void*)ibm_spread2_kernel<22>,
+        (const void*)ibm_spread2_kernel<0>,         (const void*)ibm_interp2_kernel<16, 0, 0>,
+        (const void*)ibm_interp2_kernel<16, 1, 0>,  (const void*)ibm_interp2_kernel<16, 0, 1>,
+        (const void*)ibm_interp2_kernel<22, 0, 0>,  (const void*)ibm_interp2_kernel<22, 1, 0>,
+        (const void*)ibm_interp2_kernel<22, 0, 1>,  (const void*)ibm_interp2_kernel<0, 0, 0>,
+        (const void*)ibm_interp2_kernel<0, 1, 0>,   (const void*)ibm_interp2_kernel<0, 0, 1>};
     e = cudaSuccess;
     for (const void* fn : fns)
       if (e == cudaSuccess)
@@ -614,7 +756,7 @@ cudaError_t launch_ibm_spread(const IbmArgs& A, cudaStream_t s) {
   if (A.np == 0) return cudaSuccess;
   if (A.D == 2) {
     const unsigned grid = (unsigned)((A.np + kIbmWarps - 1) / kIbmWarps);
-    const size_t sm = ibm_box2_smem(A.box);
+    const size_t sm = sizeof(float) * kIbmWarps * (size_t)spread2_warp_floats(A.box);
     if (A.box == 16)
       ibm_spread2_kernel<16><<<grid, kIbmWarps * 32, sm, s>>>(A);
     else if (A.box == 22)
@@ -630,10 +772,16 @@ cudaError_t launch_ibm_spread(const IbmArgs& A, cudaStream_t s) {
 cudaError_t launch_ibm_forces(const IbmArgs& A, cudaStream_t s) {
   if (A.np == 0) return cudaSuccess;
   const unsigned grid = (unsigned)(((long long)A.np * 32 + 255) / 256);
-  if (A.D == 2)
-    ibm_forces_kernel<2><<<grid, 256, 0, s>>>(A);
-  else
+  if (A.D == 2) {
+    if (A.box == 16)
+      ibm_forces2_kernel<16><<<grid, 256, 0, s>>>(A);
+    else if (A.box == 22)
+      ibm_forces2_kernel<22><<<grid, 256, 0, s>>>(A);
+    else
+      ibm_forces2_kernel<0><<<grid, 256, 0, s>>>(A);
+  } else {
     ibm_forces_kernel<3><<<grid, 256, 0, s>>>(A);
+  }
   return cudaGetLastError();
 }
 

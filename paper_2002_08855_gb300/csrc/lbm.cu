@@ -151,25 +151,36 @@ __device__ __forceinline__ void step_node(const LbmArgs& A, const NodeCoord& c) 
   // the IB force is read for every node together with the PDFs (one memory latency);
   // it is zero wherever no Lagrangian point spread into the node
   load_pdfs<L, PARITY, INNER>(A.g, f, c.x, c.y, c.z, c.n, fa);
+  if (L::dim == 2) {  // interleaved [N][2]
+    const float2 v = reinterpret_cast<const float2*>(fib)[c.n];
+    fv[0] = v.x;
+    fv[1] = v.y;
+  } else {
 #pragma unroll
-  for (int k = 0; k < L::dim; ++k) fv[k] = fib[k * N + c.n];
+    for (int k = 0; k < L::dim; ++k) fv[k] = fib[k * N + c.n];
+  }
   float F[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) F[k] = A.body[k] + fv[k];
   collide<L>(fa, F, A.omega, A.kforce);
   store_post<L, PARITY, INNER>(A.g, f, c.x, c.y, c.z, c.n, fa);
+  if (L::dim == 2) {
+    if (fv[0] != 0.0f || fv[1] != 0.0f) reinterpret_cast<float2*>(fib)[c.n] = make_float2(0.0f, 0.0f);
+  } else {
 #pragma unroll
-  for (int k = 0; k < L::dim; ++k)
-    if (fv[k] != 0.0f) fib[k * N + c.n] = 0.0f;
+    for (int k = 0; k < L::dim; ++k)
+      if (fv[k] != 0.0f) fib[k * N + c.n] = 0.0f;
+  }
 }
 
 // One full time step on every node: read f (AA parity) and the IB force, collide,
-// stream in place, clear the IB force.  Also clears the node mask (one store per 32
-// nodes) for the particle update to mark the next step's nodes.
+// stream in place, clear the IB force.  In 3D it also clears the node mask (one store
+// per 32 nodes) for the particle update to mark the next step's nodes (2D keeps no
+// node mask).
 template <class L, int PARITY>
 __global__ void __launch_bounds__(kLbmBlock) lbm_step_kernel(LbmArgs A, int cpr) {
   const NodeCoord c = node_coord(A.g, cpr);
-  if ((c.x & 31) == 0 && c.valid) A.mask[c.row * A.g.wpr + (c.x >> 5)] = 0u;
+  if (L::dim == 3 && (c.x & 31) == 0 && c.valid) A.mask[c.row * A.g.wpr + (c.x >> 5)] = 0u;
   if (PARITY == 1 && block_inner(A.g, c.x - (int)threadIdx.x, c.y, c.z, L::dim)) {
     step_node<L, PARITY, true>(A, c);
     return;
@@ -178,7 +189,6 @@ __global__ void __launch_bounds__(kLbmBlock) lbm_step_kernel(LbmArgs A, int cpr)
   step_node<L, PARITY, false>(A, c);
 }
 
-// u* = sum_a e_a f_a (Eq. 5) on flagged nodes only.
 // u* = sum_a e_a f_a (Eq. 5) on the flagged nodes only: one thread per node in large
 // blocks; threads of unflagged nodes leave after reading their mask word.  The mask
 // is cleared by lbm_step later in the step.

@@ -45,8 +45,11 @@ def test_workspace_size_of_the_2048x4096_cavity(lib):
     w = inputs.cavity_2d_large(0.1)
     n = binding.workspace_size(w)
     pdfs = 9 * 2048 * 4096 * 4
-    fields = 2 * 2 * 2048 * 4096 * 4  # u* and f_IB
-    assert pdfs + fields < n < (pdfs + fields) * 1.1
+    fib = 2 * 2048 * 4096 * 4  # f_IB (2D keeps u* per particle box, not on the grid)
+    points = w.n_particles * w.n_lag * 2 * (8 + 8 + 4 + 4 + 4 + 4 + 4)  # X_b x2, U_b x2, F_b, dF_b, D_I u*
+    boxes = w.n_particles * 2 * 16 * 20 * 4  # u* of each particle's 16 x 16 node box (row pitch 20)
+    need = pdfs + fib + points + boxes
+    assert need < n < need * 1.05
 
 
 @pytest.mark.parametrize("field,value,code", [
