@@ -162,8 +162,8 @@ Layout carve(const ibm_lbm_config* c, const Derived& d) {
   const size_t N = (size_t)d.g.N, np = (size_t)c->n_particles, D = d.D;
   const size_t npts = (size_t)d.npts;
   l.f = cv.take(sizeof(float) * d.Q * N);
-  l.ustar = cv.take(D == 3 ? sizeof(float) * D * N : 0);  // 2D keeps u* per particle box (ubox)
-  l.fib = cv.take(sizeof(float) * D * N);
+  l.ustar = cv.take(D == 3 ? sizeof(float) * 4 * N : 0);  // 3D [N][4]; 2D keeps u* per particle box
+  l.fib = cv.take(sizeof(float) * (D == 3 ? 4 : 2) * N);     // 2D [N][2], 3D [N][4]
   l.mask = cv.take(D == 3 ? sizeof(uint32_t) * (size_t)d.g.rows * d.g.wpr : 0);  // 3D only
   l.X0 = cv.take(sizeof(double) * np * D);
   l.X1 = cv.take(sizeof(double) * np * D);
@@ -276,6 +276,7 @@ struct ibm_lbm_handle {
     a.rcell = d.rcell;
     a.dV = (float)d.dV;
     a.box = d.box;
+    a.mark_radius = d.mark_radius;
     a.ustar = at<float>(l.ustar);
     a.fib = at<float>(l.fib);
     a.f = at<float>(l.f);
@@ -376,6 +377,13 @@ struct ibm_lbm_handle {
 
 namespace {
 
+// 3D node mask (lbm_moments and the f_IB read of lbm_step use it): cleared before the
+// regeneration marks the nodes of the new particle positions
+cudaError_t clear_mask(ibm_lbm_handle* h, cudaStream_t s) {
+  return cudaMemsetAsync(h->at<uint32_t>(h->l.mask), 0,
+                         sizeof(uint32_t) * (size_t)h->d.g.rows * h->d.g.wpr, s);
+}
+
 // Enqueue one step of the given parity.  With ev != nullptr an event is recorded
 // after each part (for ibm_lbm_time_parts).  Returns the number of kernels launched.
 int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, int* nk) {
@@ -396,9 +404,12 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
       ++k;
     }
     for (int m = 1; m <= h->cfg.mdf_iters; ++m) {
-      CUDA_TRY(launch_ibm_interp(ia, m, s));
-      CUDA_TRY(launch_ibm_spread(ia, s));
-      k += 2;
+      CUDA_TRY(launch_ibm_interp(ia, m, s));  // 3D: interpolation and spreading
+      ++k;
+      if (h->d.D == 2) {
+        CUDA_TRY(launch_ibm_spread(ia, s));
+        ++k;
+      }
     }
     CUDA_TRY(launch_ibm_forces(ia, s));
     ++k;
@@ -424,6 +435,7 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
     ++k;
     CUDA_TRY(cudaStreamWaitEvent(s, h->join, 0));
     if (h->d.D == 3) {
+      CUDA_TRY(clear_mask(h, s));
       CUDA_TRY(launch_regen(h->regen(1 - parity), 0, s));
       ++k;
     }
@@ -442,6 +454,7 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
   }
   if (ev) CUDA_TRY(cudaEventRecord(ev[4], s));
   if (particles) {
+    if (h->d.D == 3) CUDA_TRY(clear_mask(h, s));
     CUDA_TRY(launch_regen(h->regen(1 - parity), 0, s));
     ++k;
   }
@@ -480,6 +493,7 @@ int capture_graph(ibm_lbm_handle* h, int parity) {
 // points and node marks of the current state (after init or a new particle state)
 int regenerate_points(ibm_lbm_handle* h) {
   if (h->cfg.n_particles == 0) return IBMLBM_OK;
+  if (h->d.D == 3) CUDA_TRY(clear_mask(h, h->s));
   CUDA_TRY(launch_regen(h->regen((int)(h->step & 1)), 1, h->s));
   h->launches += 1;
   return IBMLBM_OK;

@@ -6,10 +6,11 @@
 //
 // Data layout in HBM (one workspace, carved by the host):
 //   f      [Q][N]  float  PDFs, one copy, AA-pattern in-place streaming
-//   ustar  [D][N]  float  u* = sum_a e_a f_a, written only on flagged nodes
-//   fib    float  IB force density, zero outside the IBM phase: 2D [N][2]
-//                 (interleaved), 3D [3][N]
-//   mask   [rows][wpr] u32  one bit per node: nodes within R + 2 sqrt(D) of a
+//   ustar  [N][4]  float  3D: u* = sum_a e_a f_a on the marked nodes (2D keeps u* of
+//                         each particle's node box instead)
+//   fib    float  IB force density, zero outside the IBM phase: 2D [N][2],
+//                 3D [N][4] (fourth component unused)
+//   mask   [rows][wpr] u32  3D: one bit per node, the nodes within R + 2 sqrt(3) of a
 //                           particle centre (support of every Lagrangian point
 //                           and the particle interior)
 //   particle state in double, Lagrangian point data [npts][D]; point positions as
@@ -155,6 +156,7 @@ struct IbmArgs {
   int rcell;         // ceil(D_p / 2)
   float dV;          // point volume (Eq. 13 reading)
   int box;           // side of the spreading box (nodes)
+  float mark_radius; // 3D: radius of the marked ball (u* is valid inside it)
   const float* ustar;    // 3D: u* on flagged nodes (lbm_moments)
   float* fib;
   const float* f;        // 2D: the PDFs, for u* of each particle's box

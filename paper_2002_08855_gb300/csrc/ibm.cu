@@ -1,12 +1,12 @@
 // Immersed-boundary kernels (Sec. 2.2, Sec. 4) and the particle update (Sec. 2.3).
 //
-// Multi-direct forcing, iteration m = 1..M:
-//   ibm_interp: one thread per Lagrangian point gathers the 4^D support nodes,
-//     u_b = sum delta(x - X_b) (u* + dt f_IB / (2 rho_f))       (Eq. 7, 12, 47)
-//     dF_b = 2 rho_f (U_b - u_b) / dt, F_b += dF_b              (Eq. 10)
-//   ibm_spread: one block per particle accumulates dF_b delta dV on a shared-memory
-//     box around the particle and adds the non-zero box cells to f_IB with one
-//     global atomic per cell and component                      (Eq. 11, 13, 48)
+// Multi-direct forcing, iteration m = 1..M, per particle:
+//   interpolation  u_b = sum delta(x - X_b) (u* + dt f_IB / (2 rho_f))   (Eq. 7, 12, 47)
+//                  dF_b = 2 rho_f (U_b - u_b) / dt, F_b += dF_b           (Eq. 10)
+//   spreading      f_IB += sum_b dF_b delta(x - X_b) dV                    (Eq. 11, 13, 48)
+// Each particle's node box lives in shared memory: 2D one warp per particle (one
+// interpolation and one spreading launch per iteration), 3D one block per sphere (both
+// in one launch).  The box cells reach f_IB with one global atomic per cell.
 // Gathering u* + f_IB/2 equals the paper's u^(m-1) = u^(m-2) + dt D_E dF/(2 rho_f)
 // by linearity, so no separate velocity field is updated between iterations.
 #include <cmath>
@@ -51,127 +51,6 @@ __device__ __forceinline__ void axis_support(long long Xfix, int n, int per, Axi
     }
     s.idx[t] = i;
     s.ok[t] = ok;
-  }
-}
-
-template <int D>
-__global__ void __launch_bounds__(256) ibm_interp_kernel(IbmArgs A, int m) {
-  const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (b >= A.npts) return;
-  AxisSup sx, sy, sz;
-  axis_support(A.Xb[b * D + 0], A.g.nx, A.g.per[0], sx);
-  axis_support(A.Xb[b * D + 1], A.g.ny, A.g.per[1], sy);
-  if (D == 3) {
-    axis_support(A.Xb[b * D + 2], A.g.nz, A.g.per[2], sz);
-  } else {
-    sz.idx[0] = 0;
-    sz.w[0] = 1.0f;
-    sz.ok[0] = true;
-  }
-  float acc[3] = {0.0f, 0.0f, 0.0f};
-  const long long N = A.g.N;
-#pragma unroll
-  for (int tz = 0; tz < (D == 3 ? 4 : 1); ++tz) {
-    if (!sz.ok[tz]) continue;
-#pragma unroll
-    for (int ty = 0; ty < 4; ++ty) {
-      if (!sy.ok[ty]) continue;
-      const float wyz = sy.w[ty] * sz.w[tz];
-      const long long rowbase = (long long)A.g.nx * ((long long)sy.idx[ty] + (long long)A.g.ny * sz.idx[tz]);
-#pragma unroll
-      for (int tx = 0; tx < 4; ++tx) {
-        if (!sx.ok[tx]) continue;
-        const long long n = rowbase + sx.idx[tx];
-        const float w = sx.w[tx] * wyz;
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          float v = A.ustar[c * N + n];
-          if (m > 1) v += 0.5f * A.fib[c * N + n];
-          acc[c] += w * v;
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < D; ++c) {
-    const float dF = 2.0f * (A.Ub[b * D + c] - acc[c]);
-    A.dFb[b * D + c] = dF;
-    A.Fb[b * D + c] = (m == 1) ? dF : A.Fb[b * D + c] + dF;
-    if (m == 1) A.ubs[b * D + c] = acc[c];
-  }
-}
-
-size_t ibm_spread_smem(int D, int nl, int box) {
-  size_t cells = 1;
-  for (int k = 0; k < D; ++k) cells *= (size_t)box;
-  return sizeof(float) * ((size_t)D * cells + (size_t)nl * D * 4) + sizeof(int) * (size_t)nl * D;
-}
-
-template <int D>
-__global__ void __launch_bounds__(256) ibm_spread_kernel(IbmArgs A) {
-  extern __shared__ float smem[];
-  const int S = A.box;
-  const int cells = (D == 3) ? S * S * S : S * S;
-  float* box = smem;                                       // [D][cells]
-  float* wts = box + D * cells;                            // [nl][D][4]
-  int* base = reinterpret_cast<int*>(wts + A.nl * D * 4);  // [nl][D]
-  const int i = blockIdx.x;
-  int org[3] = {0, 0, 0};
-  for (int k = 0; k < D; ++k) org[k] = fix_anchor(A.Xcf[(long long)i * D + k]) - A.rcell - 2;
-
-  for (int t = threadIdx.x; t < D * cells; t += blockDim.x) box[t] = 0.0f;
-  for (int t = threadIdx.x; t < A.nl * D; t += blockDim.x) {
-    const long long b = (long long)i * A.nl + t / D;
-    const long long X = A.Xb[b * D + (t % D)];
-    const float fr = fix_frac(X);
-    base[t] = fix_anchor(X) - 1;
-#pragma unroll
-    for (int s = 0; s < 4; ++s) wts[t * 4 + s] = delta4((float)(s - 1) - fr);
-  }
-  __syncthreads();
-
-  constexpr int P = (D == 3) ? 64 : 16;
-  const int n[3] = {A.g.nx, A.g.ny, A.g.nz};
-  for (int q = threadIdx.x; q < A.nl * P; q += blockDim.x) {
-    const int k = q / P, s = q % P;
-    const int st[3] = {s & 3, (s >> 2) & 3, s >> 4};
-    int loc[3] = {0, 0, 0};
-    float w = A.dV;
-    bool ok = true;
-    for (int a = 0; a < D; ++a) {
-      const int gcoord = base[k * D + a] + st[a];
-      if (!A.g.per[a] && (gcoord < 0 || gcoord >= n[a])) ok = false;
-      loc[a] = gcoord - org[a];
-      if (loc[a] < 0 || loc[a] >= S) {
-        ok = false;
-        atomicOr(A.status, ST_CAPACITY);
-      }
-      w *= wts[(k * D + a) * 4 + st[a]];
-    }
-    if (!ok) continue;
-    const int cell = loc[0] + S * (loc[1] + S * loc[2]);
-    const long long b = (long long)i * A.nl + k;
-    for (int c = 0; c < D; ++c) atomicAdd(&box[c * cells + cell], A.dFb[b * D + c] * w);
-  }
-  __syncthreads();
-
-  for (int t = threadIdx.x; t < cells; t += blockDim.x) {
-    int gc[3] = {org[0] + t % S, org[1] + (t / S) % S, (D == 3) ? org[2] + t / (S * S) : 0};
-    bool ok = true;
-    for (int a = 0; a < D; ++a) {
-      if (gc[a] < 0 || gc[a] >= n[a]) {
-        if (A.g.per[a])
-          gc[a] = ((gc[a] % n[a]) + n[a]) % n[a];
-        else
-          ok = false;
-      }
-    }
-    if (!ok) continue;
-    const long long nn = (long long)gc[0] + (long long)A.g.nx * ((long long)gc[1] + (long long)A.g.ny * gc[2]);
-    for (int c = 0; c < D; ++c) {
-      const float v = box[c * cells + t];
-      if (v != 0.0f) atomicAdd(&A.fib[c * A.g.N + nn], v);
-    }
   }
 }
 
@@ -432,6 +311,261 @@ __global__ void __launch_bounds__(kIbmWarps * 32) ibm_spread2_kernel(IbmArgs A) 
   }
 }
 
+// ------------------------------------------------------------------ 3D
+// One block per sphere and MDF iteration m (Eq. 47, 10, 48 in one launch):
+//   1. stage u^(m-1) = u* + f_IB/2 (m = 1: u*) of the nodes of the sphere's box that
+//      lie in the marked ball (every support node does) into shared memory, one box
+//      row per warp and round, one node per lane (u* and f_IB are [N][4]);
+//   2. interpolate every point, one point per half-warp, lane (sx, sy) of the 4 x 4
+//      support columns, the 4 z levels in a loop; dF_b = 2 (U_b - u_b);
+//   3. spread dF_b dV into the same box (reused), accumulated as 32-bit fixed point
+//      with integer shared-memory atomics.  The scale of the sphere is 2^30 over
+//      (max |dF_b dV| times N_L times 1/8), a bound on any node's sum (every weight
+//      is at most 1/8), so no sum overflows and the rounding is that of single
+//      precision;
+//   4. add the non-zero box cells to f_IB with one vector atomic per cell.
+// Box rows are box3_pitch(S) cells apart (4 modulo 8), so the 16 columns of a support
+// fall on 16 banks.  Each point's row of the table holds its 12 weights, its first
+// box cell and dF_b dV.
+constexpr int kMdf3Threads = 512;
+constexpr int kMdf3Warps = kMdf3Threads / 32;
+constexpr int kTab3 = 16;  // table floats per point
+constexpr int kRows3 = 2;  // box rows each warp stages per round
+
+__host__ __device__ inline int box3_pitch(int S) {
+  int p = S;
+  while ((p & 7) != 4) ++p;
+  return p;
+}
+size_t ibm_mdf3_smem(int nl, int box) {
+  const size_t plane = (size_t)box3_pitch(box) * box;
+  return sizeof(float) * (3 * plane * box + (size_t)kTab3 * nl + 32);
+}
+
+template <int SC, int MODE>
+__global__ void __launch_bounds__(kMdf3Threads) ibm_mdf3_kernel(IbmArgs A, int m) {
+  extern __shared__ __align__(16) float sm3[];
+  const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int S = SC ? SC : A.box, Py = box3_pitch(S), Pz = Py * S, cells = Pz * S;
+  float* box = sm3;                          // [3][cells]
+  int* boxi = reinterpret_cast<int*>(sm3);   // the same memory as fixed point (step 3)
+  float* tab = sm3 + 3 * cells;              // [nl][kTab3]
+  float* red = tab + (size_t)kTab3 * A.nl;   // [32] reduction scratch
+  const float4* us4 = reinterpret_cast<const float4*>(A.ustar);
+  float4* fib4 = reinterpret_cast<float4*>(A.fib);
+  const int nn[3] = {A.g.nx, A.g.ny, A.g.nz};
+  int an[3], org[3];
+  float fr[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const long long v = A.Xcf[(long long)i * 3 + k];
+    an[k] = fix_anchor(v);
+    fr[k] = fix_frac(v);
+    org[k] = an[k] - A.rcell - 2;
+  }
+  const float Rm2 = A.mark_radius * A.mark_radius;
+  // this lane's column of every box row: grid x, and whether it is inside the domain
+  // (S <= 26 here: a larger box does not fit in shared memory and is rejected at init)
+  int gx = org[0] + lane;
+  bool xok = lane < S;
+  if (gx < 0 || gx >= nn[0]) {
+    if (A.g.per[0]) gx = ((gx % nn[0]) + nn[0]) % nn[0]; else xok = false;
+  }
+  const float dx = (float)(org[0] + lane - an[0]) - fr[0];
+
+  // 1. stage the ball of the box, kRows3 rows per warp and round
+  const int rows = S * S;
+  for (int r0 = warp; r0 < rows; r0 += kMdf3Warps * kRows3) {
+    float4 v[kRows3];
+    int cell[kRows3];
+#pragma unroll
+    for (int u = 0; u < kRows3; ++u) {
+      const int r = r0 + u * kMdf3Warps;
+      cell[u] = -1;
+      v[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (r >= rows || lane >= S) continue;
+      const int ly = r % S, lz = r / S;
+      const float dy = (float)(org[1] + ly - an[1]) - fr[1], dz = (float)(org[2] + lz - an[2]) - fr[2];
+      if (dx * dx + dy * dy + dz * dz > Rm2) continue;  // outside the marked ball
+      cell[u] = lane + Py * ly + Pz * lz;
+      int gy = org[1] + ly, gz = org[2] + lz;
+      bool ok = xok;
+      if (gy < 0 || gy >= nn[1]) {
+        if (A.g.per[1]) gy = ((gy % nn[1]) + nn[1]) % nn[1]; else ok = false;
+      }
+      if (gz < 0 || gz >= nn[2]) {
+        if (A.g.per[2]) gz = ((gz % nn[2]) + nn[2]) % nn[2]; else ok = false;
+      }
+      if (!ok) continue;  // beyond a wall: zero
+      const long long n = (long long)gx + (long long)nn[0] * ((long long)gy + (long long)nn[1] * gz);
+      v[u] = us4[n];
+      if (MODE == 1) {
+        const float4 f = fib4[n];
+        v[u].x += 0.5f * f.x;
+        v[u].y += 0.5f * f.y;
+        v[u].z += 0.5f * f.z;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kRows3; ++u)
+      if (cell[u] >= 0) {
+        box[cell[u]] = v[u].x;
+        box[cells + cell[u]] = v[u].y;
+        box[2 * cells + cell[u]] = v[u].z;
+      }
+  }
+  // table: weights and first box cell of every point
+  for (int k = tid; k < A.nl; k += kMdf3Threads) {
+    const long long b = (long long)i * A.nl + k;
+    float* row = tab + (size_t)k * kTab3;
+    int base = 0;
+    bool valid = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const long long X = A.Xb[b * 3 + a];
+      const int s0 = fix_anchor(X) - 1;
+      const float f = fix_frac(X);
+      const int l0 = s0 - org[a];
+      if (l0 < 0 || l0 + 3 >= S) valid = false;
+      base += l0 * (a == 0 ? 1 : a == 1 ? Py : Pz);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int gc = s0 + t;
+        row[4 * a + t] = (!A.g.per[a] && (gc < 0 || gc >= nn[a])) ? 0.0f : delta4((float)(t - 1) - f);
+      }
+    }
+    if (!valid) {
+      atomicOr(A.status, ST_CAPACITY);
+      base = 0;
+#pragma unroll
+      for (int t = 0; t < 12; ++t) row[t] = 0.0f;
+    }
+    row[12] = __int_as_float(base);
+  }
+  __syncthreads();
+
+  // 2. interpolation: warp w takes points 2 (w + kMdf3Warps j) + h, half h
+  const int h = lane >> 4, sx = lane & 3, sy = (lane >> 2) & 3;
+  const int colo = sx + Py * sy;
+  float mx = 0.0f;
+  for (int p0 = 2 * warp; p0 < A.nl; p0 += 2 * kMdf3Warps) {
+    const int p = p0 + h;
+    const bool act = p < A.nl;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+    if (act) {
+      const float* row = tab + (size_t)p * kTab3;
+      const float wxy = row[sx] * row[4 + sy];
+      const int c0 = __float_as_int(row[12]) + colo;
+#pragma unroll
+      for (int sz = 0; sz < 4; ++sz) {
+        const float w = wxy * row[8 + sz];
+        const int c = c0 + Pz * sz;
+        a0 += w * box[c];
+        a1 += w * box[cells + c];
+        a2 += w * box[2 * cells + c];
+      }
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if (act && (lane & 15) == 0) {  // u_b into the table
+      float* row = tab + (size_t)p * kTab3;
+      row[13] = a0;
+      row[14] = a1;
+      row[15] = a2;
+    }
+  }
+  __syncthreads();
+  // dF_b = 2 (U_b - u_b), F_b, one thread per point; the table keeps dF_b dV
+  for (int k = tid; k < A.nl; k += kMdf3Threads) {
+    const long long b = (long long)i * A.nl + k;
+    float* row = tab + (size_t)k * kTab3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float u = row[13 + c];
+      const float d = 2.0f * (A.Ub[b * 3 + c] - u);
+      A.dFb[b * 3 + c] = d;
+      A.Fb[b * 3 + c] = (m == 1) ? d : A.Fb[b * 3 + c] + d;
+      if (m == 1) A.ubs[b * 3 + c] = u;
+      row[13 + c] = d * A.dV;
+      mx = fmaxf(mx, fabsf(d * A.dV));
+    }
+  }
+  // largest |dF dV| of the sphere
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) red[warp] = mx;
+  __syncthreads();  // the box is free
+  float gmax = 0.0f;
+#pragma unroll
+  for (int w = 0; w < kMdf3Warps; ++w) gmax = fmaxf(gmax, red[w]);
+  if (!(gmax > 1e-30f) || !isfinite(gmax)) {  // below 1e-30 the spread is negligible
+    if (!isfinite(gmax) && tid == 0) atomicOr(A.status, ST_NONFINITE);
+    return;  // nothing to spread (the same decision in every thread of the block)
+  }
+  const float scale = 1073741824.0f / (gmax * 0.125f * (float)A.nl);  // 2^30 / bound
+  const float inv = 1.0f / scale;
+  {
+    int4* b4 = reinterpret_cast<int4*>(boxi);
+    const int4 z = make_int4(0, 0, 0, 0);
+    for (int q = tid; q < 3 * cells / 4; q += kMdf3Threads) b4[q] = z;
+  }
+  __syncthreads();
+
+  // 3. spreading, same assignment of points to half-warps
+  for (int p0 = 2 * warp; p0 < A.nl; p0 += 2 * kMdf3Warps) {
+    const int p = p0 + h;
+    if (p >= A.nl) continue;
+    const float* row = tab + (size_t)p * kTab3;
+    const float wxy = row[sx] * row[4 + sy] * scale;
+    const int c0 = __float_as_int(row[12]) + colo;
+    const float f0 = row[13], f1 = row[14], f2 = row[15];
+#pragma unroll
+    for (int sz = 0; sz < 4; ++sz) {
+      const float w = wxy * row[8 + sz];
+      if (w == 0.0f) continue;
+      const int c = c0 + Pz * sz;
+      atomicAdd(&boxi[c], __float2int_rn(w * f0));
+      atomicAdd(&boxi[cells + c], __float2int_rn(w * f1));
+      atomicAdd(&boxi[2 * cells + c], __float2int_rn(w * f2));
+    }
+  }
+  __syncthreads();
+
+  // 4. flush the non-zero cells to f_IB, one box row per warp and round
+  for (int r = warp; r < rows; r += kMdf3Warps) {
+    if (lane >= S) continue;
+    const int ly = r % S, lz = r / S;
+    const int c = lane + Py * ly + Pz * lz;
+    const int v0 = boxi[c], v1 = boxi[cells + c], v2 = boxi[2 * cells + c];
+    if ((v0 | v1 | v2) == 0) continue;
+    // non-zero cells lie inside the domain or across a periodic face
+    int gy = org[1] + ly, gz = org[2] + lz;
+    if (gy < 0 || gy >= nn[1]) gy = ((gy % nn[1]) + nn[1]) % nn[1];
+    if (gz < 0 || gz >= nn[2]) gz = ((gz % nn[2]) + nn[2]) % nn[2];
+    const long long n = (long long)gx + (long long)nn[0] * ((long long)gy + (long long)nn[1] * gz);
+    atomicAdd(fib4 + n, make_float4((float)v0 * inv, (float)v1 * inv, (float)v2 * inv, 0.0f));
+  }
+}
+
+cudaError_t launch_ibm_mdf3(const IbmArgs& A, int m, cudaStream_t s) {
+  if (A.np == 0 || m < 1) return cudaSuccess;
+  const size_t sm = ibm_mdf3_smem(A.nl, A.box);
+#define IBMLBM_MDF3(SC)                                                 \
+  do {                                                                   \
+    if (m == 1) ibm_mdf3_kernel<SC, 0><<<A.np, kMdf3Threads, sm, s>>>(A, m); \
+    else ibm_mdf3_kernel<SC, 1><<<A.np, kMdf3Threads, sm, s>>>(A, m);        \
+  } while (0)
+  if (A.box == 18) IBMLBM_MDF3(18);
+  else if (A.box == 14) IBMLBM_MDF3(14);
+  else IBMLBM_MDF3(0);
+#undef IBMLBM_MDF3
+  return cudaGetLastError();
+}
+
 // F_h, T_h of particle i from its points, and the write of the warp's sums (lane 0)
 template <int D>
 __device__ __forceinline__ void forces_finish(const IbmArgs& A, int i, int lane, FF (&P)[3], FF (&L)[3]) {
@@ -526,8 +660,9 @@ __global__ void __launch_bounds__(256) ibm_forces_kernel(IbmArgs A) {
     }
     if (!ok) continue;
     const long long nn = (long long)gc[0] + (long long)A.g.nx * ((long long)gc[1] + (long long)A.g.ny * gc[2]);
-    float u[3] = {0.0f, 0.0f, 0.0f};
-    for (int c = 0; c < D; ++c) u[c] = A.ustar[c * A.g.N + nn] + 0.5f * A.fib[c * A.g.N + nn];
+    const float4 us = reinterpret_cast<const float4*>(A.ustar)[nn];  // 3D: [N][4]
+    const float4 fv = reinterpret_cast<const float4*>(A.fib)[nn];
+    const float u[3] = {us.x + 0.5f * fv.x, us.y + 0.5f * fv.y, us.z + 0.5f * fv.z};
     for (int c = 0; c < D; ++c) ff_add(P[c], u[c]);
     if (D == 3) {
       ff_add(L[0], r[1] * u[2] - r[2] * u[1]);
@@ -712,8 +847,7 @@ cudaError_t launch_ibm_interp(const IbmArgs& A, int m, cudaStream_t s) {
     else IBMLBM_INTERP2(0);
 #undef IBMLBM_INTERP2
   } else {
-    const unsigned grid = (unsigned)((A.npts + 255) / 256);
-    ibm_interp_kernel<3><<<grid, 256, 0, s>>>(A, m);
+    return launch_ibm_mdf3(A, m, s);  // interpolation and spreading in one launch
   }
   return cudaGetLastError();
 }
@@ -723,7 +857,7 @@ cudaError_t launch_ibm_interp(const IbmArgs& A, int m, cudaStream_t s) {
 // shared memory of the spreading kernel used for this dimension (the 2D
 // interpolation kernel uses the same amount)
 size_t spread_smem(int D, int nl, int box) {
-  return D == 2 ? ibm_box2_smem(box) : ibm_spread_smem(D, nl, box);
+  return D == 2 ? ibm_box2_smem(box) : ibm_mdf3_smem(nl, box);
 }
 
 cudaError_t prepare_ibm_spread(int D, size_t smem) {
@@ -746,7 +880,13 @@ cudaError_t prepare_ibm_spread(int D, size_t smem) {
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   } else {
-    e = cudaFuncSetAttribute(ibm_spread_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const void* fns[] = {(const void*)ibm_mdf3_kernel<18, 0>, (const void*)ibm_mdf3_kernel<18, 1>,
+                         (const void*)ibm_mdf3_kernel<14, 0>, (const void*)ibm_mdf3_kernel<14, 1>,
+                         (const void*)ibm_mdf3_kernel<0, 0>,  (const void*)ibm_mdf3_kernel<0, 1>};
+    e = cudaSuccess;
+    for (const void* fn : fns)
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
   if (e == cudaSuccess) g = smem;
   return e;
@@ -763,9 +903,7 @@ cudaError_t launch_ibm_spread(const IbmArgs& A, cudaStream_t s) {
       ibm_spread2_kernel<22><<<grid, kIbmWarps * 32, sm, s>>>(A);
     else
       ibm_spread2_kernel<0><<<grid, kIbmWarps * 32, sm, s>>>(A);
-  } else {
-    ibm_spread_kernel<3><<<A.np, 256, ibm_spread_smem(3, A.nl, A.box), s>>>(A);
-  }
+  }  // 3D spreads inside launch_ibm_interp
   return cudaGetLastError();
 }
 

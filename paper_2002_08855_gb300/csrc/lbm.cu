@@ -145,7 +145,6 @@ template <class L, int PARITY, bool INNER>
 __device__ __forceinline__ void step_node(const LbmArgs& A, const NodeCoord& c) {
   float* __restrict__ f = A.f;
   float* __restrict__ fib = A.fib;
-  const long long N = A.g.N;
   float fa[L::Q];
   float fv[3] = {0.0f, 0.0f, 0.0f};
   // the IB force is read for every node together with the PDFs (one memory latency);
@@ -155,9 +154,13 @@ __device__ __forceinline__ void step_node(const LbmArgs& A, const NodeCoord& c) 
     const float2 v = reinterpret_cast<const float2*>(fib)[c.n];
     fv[0] = v.x;
     fv[1] = v.y;
-  } else {
-#pragma unroll
-    for (int k = 0; k < L::dim; ++k) fv[k] = fib[k * N + c.n];
+  } else {  // [N][4]; non-zero only on nodes the particle update marked
+    if ((A.mask[c.row * A.g.wpr + (c.x >> 5)] >> (c.x & 31)) & 1u) {
+      const float4 v = reinterpret_cast<const float4*>(fib)[c.n];
+      fv[0] = v.x;
+      fv[1] = v.y;
+      fv[2] = v.z;
+    }
   }
   float F[3];
 #pragma unroll
@@ -166,21 +169,16 @@ __device__ __forceinline__ void step_node(const LbmArgs& A, const NodeCoord& c) 
   store_post<L, PARITY, INNER>(A.g, f, c.x, c.y, c.z, c.n, fa);
   if (L::dim == 2) {
     if (fv[0] != 0.0f || fv[1] != 0.0f) reinterpret_cast<float2*>(fib)[c.n] = make_float2(0.0f, 0.0f);
-  } else {
-#pragma unroll
-    for (int k = 0; k < L::dim; ++k)
-      if (fv[k] != 0.0f) fib[k * N + c.n] = 0.0f;
+  } else if (fv[0] != 0.0f || fv[1] != 0.0f || fv[2] != 0.0f) {
+    reinterpret_cast<float4*>(fib)[c.n] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   }
 }
 
-// One full time step on every node: read f (AA parity) and the IB force, collide,
-// stream in place, clear the IB force.  In 3D it also clears the node mask (one store
-// per 32 nodes) for the particle update to mark the next step's nodes (2D keeps no
-// node mask).
+// One full time step on every node: read f (AA parity) and the IB force (3D: on marked
+// nodes only), collide, stream in place, clear the IB force.
 template <class L, int PARITY>
 __global__ void __launch_bounds__(kLbmBlock) lbm_step_kernel(LbmArgs A, int cpr) {
   const NodeCoord c = node_coord(A.g, cpr);
-  if (L::dim == 3 && (c.x & 31) == 0 && c.valid) A.mask[c.row * A.g.wpr + (c.x >> 5)] = 0u;
   if (PARITY == 1 && block_inner(A.g, c.x - (int)threadIdx.x, c.y, c.z, L::dim)) {
     step_node<L, PARITY, true>(A, c);
     return;
@@ -191,7 +189,7 @@ __global__ void __launch_bounds__(kLbmBlock) lbm_step_kernel(LbmArgs A, int cpr)
 
 // u* = sum_a e_a f_a (Eq. 5) on the flagged nodes only: one thread per node in large
 // blocks; threads of unflagged nodes leave after reading their mask word.  The mask
-// is cleared by lbm_step later in the step.
+// is cleared before the particle update marks the next step's nodes.
 constexpr int kMomBlock = 512;
 
 template <class L, int PARITY>
@@ -209,8 +207,10 @@ __global__ void __launch_bounds__(kMomBlock) lbm_moments_kernel(LbmArgs A) {
   float fa[L::Q], us[3], s1;
   load_pdfs<L, PARITY>(A.g, A.f, x, y, (int)z, n, fa);
   moments<L>(fa, us, s1);
-#pragma unroll
-  for (int k = 0; k < L::dim; ++k) A.ustar[k * A.g.N + n] = us[k];
+  if (L::dim == 3)
+    reinterpret_cast<float4*>(A.ustar)[n] = make_float4(us[0], us[1], us[2], 0.0f);
+  else
+    reinterpret_cast<float2*>(A.ustar)[n] = make_float2(us[0], us[1]);
 }
 
 // p (Eq. 6 with u = u*) and u* (Eq. 5) on every node, as doubles.

@@ -32,6 +32,9 @@ CASES = [
     (2, (50, 44, 1), (1, 1, 0), [[1.2, 42.9], [25.0, 20.0]], 10.0, 31),  # wraps both axes
     (3, (30, 28, 26), (0, 0, 0), [[14.2, 13.6, 12.9]], 12.0, 452),
     (3, (24, 26, 28), (1, 0, 1), [[1.5, 12.2, 26.8]], 8.0, 200),
+    # near contact: the supports of neighbouring particles share nodes
+    (2, (64, 48, 1), (0, 0, 0), [[20.2, 23.9], [31.1, 25.3]], 10.0, 31),
+    (3, (40, 36, 34), (0, 0, 0), [[12.5, 17.2, 16.9], [25.3, 17.9, 17.4], [18.9, 28.1, 16.2]], 12.0, 452),
 ]
 
 
