@@ -70,7 +70,14 @@ typedef struct ibm_lbm_config {
   double eps_pp, E_pp;    /* stiffness parameters of Eq. 16 (E_pp < eps_pp)              */
   int32_t fixed_particles;/* 1: particles keep centre and velocity (static bodies)       */
   int32_t max_neighbors;  /* capacity of each particle's contact list; 0 selects 32      */
+  int32_t pdf_storage;    /* IBMLBM_PDF_FP32 (0), IBMLBM_PDF_FP16 (1), IBMLBM_PDF_BF16 (2):
+                             element type of the stored PDFs.  FP16 and BF16 hold
+                             h_a = f_a / w_a (deviations from rest divided by the lattice
+                             weight); collision, IBM and particle arithmetic stay FP32 /
+                             FP64.  No counterpart in the paper, which stores doubles.    */
 } ibm_lbm_config;
+
+enum { IBMLBM_PDF_FP32 = 0, IBMLBM_PDF_FP16 = 1, IBMLBM_PDF_BF16 = 2 };
 
 typedef struct ibm_lbm_handle ibm_lbm_handle;
 

@@ -42,7 +42,7 @@ class Config(C.Structure):
         ("diameter", C.c_double), ("delta_kind", C.c_int32), ("drs", C.c_double),
         ("mdf_iters", C.c_int32), ("density_ratio", C.c_double), ("gravity", C.c_double * 3),
         ("zeta", C.c_double), ("eps_pp", C.c_double), ("E_pp", C.c_double),
-        ("fixed_particles", C.c_int32), ("max_neighbors", C.c_int32),
+        ("fixed_particles", C.c_int32), ("max_neighbors", C.c_int32), ("pdf_storage", C.c_int32),
     ]
 
 
@@ -73,6 +73,7 @@ def make_config(w, max_neighbors: int = 0) -> Config:
     c.E_pp = float(get("E_pp", 1e-4))
     c.fixed_particles = int(get("fixed_particles", 0))
     c.max_neighbors = int(max_neighbors)
+    c.pdf_storage = int(get("pdf_storage", 0))
     return c
 
 

@@ -86,6 +86,8 @@ int check_config(const ibm_lbm_config* c) {
   if (c->n_particles < 0) return fail(IBMLBM_ERR_INVALID_ARG, "n_particles < 0");
   if (c->max_neighbors < 0 || c->max_neighbors > 64)
     return fail(IBMLBM_ERR_INVALID_ARG, "max_neighbors must be in 0..64");
+  if (c->pdf_storage < IBMLBM_PDF_FP32 || c->pdf_storage > IBMLBM_PDF_BF16)
+    return fail(IBMLBM_ERR_INVALID_ARG, "pdf_storage must be 0 (FP32), 1 (FP16) or 2 (BF16)");
   if (c->n_particles > 0) {
     if (c->n_lag < 1) return fail(IBMLBM_ERR_INVALID_ARG, "n_lag must be >= 1");
     if (!(c->diameter > 0.0)) return fail(IBMLBM_ERR_INVALID_ARG, "diameter must be > 0");
@@ -126,6 +128,7 @@ Derived derive(const ibm_lbm_config* c) {
   d.g.rows = d.g.ny * d.g.nz;
   d.g.wpr = (d.g.nx + 31) / 32;
   d.g.N = (long long)d.g.nx * d.g.ny * d.g.nz;
+  d.g.Np = (d.g.N + 63) / 64 * 64;
   d.npts = (long long)c->n_particles * c->n_lag;
   d.kmax = c->max_neighbors ? c->max_neighbors : 32;
   d.L[0] = c->nx;
@@ -161,7 +164,7 @@ Layout carve(const ibm_lbm_config* c, const Derived& d) {
   Carver cv;
   const size_t N = (size_t)d.g.N, np = (size_t)c->n_particles, D = d.D;
   const size_t npts = (size_t)d.npts;
-  l.f = cv.take(sizeof(float) * d.Q * N);
+  l.f = cv.take((c->pdf_storage == IBMLBM_PDF_FP32 ? 4 : 2) * ((size_t)d.Q * d.g.Np + 64));
   l.ustar = cv.take(D == 3 ? sizeof(float) * 4 * N : 0);  // 3D [N][4]; 2D keeps u* per particle box
   l.fib = cv.take(sizeof(float) * (D == 3 ? 4 : 2) * N);     // 2D [N][2], 3D [N][4]
   l.mask = cv.take(D == 3 ? sizeof(uint32_t) * (size_t)d.g.rows * d.g.wpr : 0);  // 3D only
@@ -253,7 +256,8 @@ struct ibm_lbm_handle {
   LbmArgs lbm() const {
     LbmArgs a{};
     a.g = d.g;
-    a.f = at<float>(l.f);
+    a.f = at<void>(l.f);
+    a.store = cfg.pdf_storage;
     a.ustar = at<float>(l.ustar);
     a.fib = at<float>(l.fib);
     a.mask = at<uint32_t>(l.mask);
@@ -279,7 +283,8 @@ struct ibm_lbm_handle {
     a.mark_radius = d.mark_radius;
     a.ustar = at<float>(l.ustar);
     a.fib = at<float>(l.fib);
-    a.f = at<float>(l.f);
+    a.f = at<void>(l.f);
+    a.store = cfg.pdf_storage;
     a.parity = parity;
     a.ubox = at<float>(l.ubox);
     a.Xb = at<long long>(parity ? l.Xb1 : l.Xb0);
@@ -432,7 +437,7 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
     }
     CUDA_TRY(cudaEventRecord(h->join, h->side));
     CUDA_TRY(launch_lbm_step(la, h->d.D, parity, s));
-    ++k;
+    k += lbm_step_launches(h->d.g, h->d.D, parity);
     CUDA_TRY(cudaStreamWaitEvent(s, h->join, 0));
     if (h->d.D == 3) {
       CUDA_TRY(clear_mask(h, s));
@@ -444,7 +449,7 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
   }
   // one part after the other (no particles, or timed parts)
   CUDA_TRY(launch_lbm_step(la, h->d.D, parity, s));
-  ++k;
+  k += lbm_step_launches(h->d.g, h->d.D, parity);
   if (ev) CUDA_TRY(cudaEventRecord(ev[3], s));
   if (particles) {
     const PairArgs pa = h->pairs(parity, have_prev);

@@ -5,7 +5,8 @@
 // Units: dh = dt = 1, cs^2 = 1/3, rho_0 = rho_f = 1.
 //
 // Data layout in HBM (one workspace, carved by the host):
-//   f      [Q][N]  float  PDFs, one copy, AA-pattern in-place streaming
+//   f      [Q][Np] PDFs (FP32, or FP16 / BF16 holding f / w), one copy, AA-pattern
+//                  in-place streaming; Np = N rounded up to 64, 64 elements of slack
 //   ustar  [N][4]  float  3D: u* = sum_a e_a f_a on the marked nodes (2D keeps u* of
 //                         each particle's node box instead)
 //   fib    float  IB force density, zero outside the IBM phase: 2D [N][2],
@@ -76,6 +77,7 @@ struct Geo {
   int rows;        // ny * nz
   int wpr;         // mask words per row = ceil(nx / 32)
   long long N;     // nx * ny * nz
+  long long Np;    // stride of the PDF planes: N rounded up to 64 elements
 };
 
 __device__ __forceinline__ long long node_of(const Geo& g, int x, int y, int z) {
@@ -137,7 +139,8 @@ __host__ __device__ inline int box_pitch(int S) {
 // ------------------------------------------------------------ kernel arguments
 struct LbmArgs {
   Geo g;
-  float* f;
+  void* f;           // PDFs, element type by store
+  int store;         // STORE_F32, STORE_F16 or STORE_BF16 (pdf_access.cuh)
   float* ustar;
   float* fib;
   uint32_t* mask;
@@ -159,7 +162,8 @@ struct IbmArgs {
   float mark_radius; // 3D: radius of the marked ball (u* is valid inside it)
   const float* ustar;    // 3D: u* on flagged nodes (lbm_moments)
   float* fib;
-  const float* f;        // 2D: the PDFs, for u* of each particle's box
+  const void* f;         // 2D: the PDFs, for u* of each particle's box
+  int store;             // their storage (STORE_F32, STORE_F16, STORE_BF16)
   int parity;            // 2D: AA parity of the PDFs
   float* ubox;           // 2D: [np][box][box_pitch(box)] float2, u* of each particle's box
   const long long* Xb;  // [npts][D] fixed point

@@ -108,7 +108,7 @@ __device__ __forceinline__ bool box_node(const Geo& g, int ox, int oy, int r, in
 //   MODE 1 (m >= 2): the box buffer plus f_IB/2.
 // Lane k then interpolates point k from shared memory.  Box nodes beyond a wall hold
 // zero, which drops them from the sum.
-template <int SC, int PARITY, int MODE>
+template <int SC, int PARITY, int MODE, int ST>
 __global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A, int m) {
   extern __shared__ __align__(16) float smem_i[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -132,18 +132,39 @@ __global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A, 
   const int ox = fix_anchor(A.Xcf[(long long)i * 2 + 0]) - A.rcell - 2;
   const int oy = fix_anchor(A.Xcf[(long long)i * 2 + 1]) - A.rcell - 2;
   if (MODE == 0) {
-    for (int t = lane; t < S * S; t += 32) {
-      const int r = t / S, c = t - r * S;
-      int gx, gy;
-      float2 v = make_float2(0.0f, 0.0f);
-      if (box_node(A.g, ox, oy, r, c, gx, gy)) {
-        float fa[9], us[3], s1;
-        load_pdfs<Lat<2>, PARITY>(A.g, A.f, gx, gy, 0, (long long)gx + (long long)A.g.nx * gy, fa);
-        moments<Lat<2>>(fa, us, s1);
-        v = make_float2(us[0], us[1]);
+    // two box nodes per lane and round, both loaded before either is reduced
+    for (int t0 = lane; t0 < S * S; t0 += 64) {
+      float fa[2][9];
+      bool ok[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int t = t0 + 32 * k;
+        ok[k] = false;
+        if (t >= S * S) continue;
+        const int r = t / S, c = t - r * S;
+        int gx, gy;
+        ok[k] = box_node(A.g, ox, oy, r, c, gx, gy);
+        if (!ok[k]) continue;
+        const long long n = (long long)gx + (long long)A.g.nx * gy;
+        if (PARITY == 1 && gx >= 1 && gx <= A.g.nx - 2 && gy >= 1 && gy <= A.g.ny - 2)
+          load_pdfs<Lat<2>, PARITY, ST, true>(A.g, A.f, gx, gy, 0, n, fa[k]);  // fixed offsets
+        else
+          load_pdfs<Lat<2>, PARITY, ST>(A.g, A.f, gx, gy, 0, n, fa[k]);
       }
-      box[r * P + c] = v;
-      ub[r * P + c] = v;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int t = t0 + 32 * k;
+        if (t >= S * S) continue;
+        const int r = t / S, c = t - r * S;
+        float2 v = make_float2(0.0f, 0.0f);
+        if (ok[k]) {
+          float us[3], s1;
+          moments<Lat<2>>(fa[k], us, s1);
+          v = make_float2(us[0], us[1]);
+        }
+        box[r * P + c] = v;
+        ub[r * P + c] = v;
+      }
     }
     __syncwarp();
     if (m == 0) return;  // box u* only (no multi-direct forcing iteration this step)
@@ -833,19 +854,26 @@ cudaError_t launch_ibm_interp(const IbmArgs& A, int m, cudaStream_t s) {
     const unsigned grid = (unsigned)((A.np + kIbmWarps - 1) / kIbmWarps);
     const int mode = m <= 1 ? 0 : 1;
     const size_t sm = sizeof(float) * kIbmWarps * (size_t)interp2_warp_floats(mode, A.box);
+#define IBMLBM_INTERP2_ST(SC, P)                                                             \
+  do {                                                                                        \
+    if (A.store == STORE_F32) ibm_interp2_kernel<SC, P, 0, STORE_F32><<<grid, kIbmWarps * 32, sm, s>>>(A, m); \
+    else if (A.store == STORE_F16) ibm_interp2_kernel<SC, P, 0, STORE_F16><<<grid, kIbmWarps * 32, sm, s>>>(A, m); \
+    else ibm_interp2_kernel<SC, P, 0, STORE_BF16><<<grid, kIbmWarps * 32, sm, s>>>(A, m);      \
+  } while (0)
 #define IBMLBM_INTERP2(SC)                                                                   \
   do {                                                                                        \
     if (mode == 0) {                                                                          \
-      if (A.parity == 0) ibm_interp2_kernel<SC, 0, 0><<<grid, kIbmWarps * 32, sm, s>>>(A, m); \
-      else ibm_interp2_kernel<SC, 1, 0><<<grid, kIbmWarps * 32, sm, s>>>(A, m);               \
+      if (A.parity == 0) IBMLBM_INTERP2_ST(SC, 0);                                            \
+      else IBMLBM_INTERP2_ST(SC, 1);                                                          \
     } else {                                                                                  \
-      ibm_interp2_kernel<SC, 0, 1><<<grid, kIbmWarps * 32, sm, s>>>(A, m);                    \
+      ibm_interp2_kernel<SC, 0, 1, STORE_F32><<<grid, kIbmWarps * 32, sm, s>>>(A, m);         \
     }                                                                                         \
   } while (0)
     if (A.box == 16) IBMLBM_INTERP2(16);
     else if (A.box == 22) IBMLBM_INTERP2(22);
     else IBMLBM_INTERP2(0);
 #undef IBMLBM_INTERP2
+#undef IBMLBM_INTERP2_ST
   } else {
     return launch_ibm_mdf3(A, m, s);  // interpolation and spreading in one launch
   }
@@ -868,13 +896,16 @@ cudaError_t prepare_ibm_spread(int D, size_t smem) {
   if (smem <= g) return cudaSuccess;
   cudaError_t e;
   if (D == 2) {
-    const void* fns[] = {
-        (const void*)ibm_spread2_kernel<16>,        (const void*)ibm_spread2_kernel<22>,
-        (const void*)ibm_spread2_kernel<0>,         (const void*)ibm_interp2_kernel<16, 0, 0>,
-        (const void*)ibm_interp2_kernel<16, 1, 0>,  (const void*)ibm_interp2_kernel<16, 0, 1>,
-        (const void*)ibm_interp2_kernel<22, 0, 0>,  (const void*)ibm_interp2_kernel<22, 1, 0>,
-        (const void*)ibm_interp2_kernel<22, 0, 1>,  (const void*)ibm_interp2_kernel<0, 0, 0>,
-        (const void*)ibm_interp2_kernel<0, 1, 0>,   (const void*)ibm_interp2_kernel<0, 0, 1>};
+#define IBMLBM_I2(SC, P, ST) (const void*)ibm_interp2_kernel<SC, P, 0, ST>
+#define IBMLBM_I2S(SC)                                                                     \
+  IBMLBM_I2(SC, 0, STORE_F32), IBMLBM_I2(SC, 1, STORE_F32), IBMLBM_I2(SC, 0, STORE_F16),    \
+      IBMLBM_I2(SC, 1, STORE_F16), IBMLBM_I2(SC, 0, STORE_BF16), IBMLBM_I2(SC, 1, STORE_BF16), \
+      (const void*)ibm_interp2_kernel<SC, 0, 1, STORE_F32>
+    const void* fns[] = {(const void*)ibm_spread2_kernel<16>, (const void*)ibm_spread2_kernel<22>,
+                         (const void*)ibm_spread2_kernel<0>, IBMLBM_I2S(16), IBMLBM_I2S(22),
+                         IBMLBM_I2S(0)};
+#undef IBMLBM_I2S
+#undef IBMLBM_I2
     e = cudaSuccess;
     for (const void* fn : fns)
       if (e == cudaSuccess)

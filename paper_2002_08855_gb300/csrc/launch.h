@@ -8,6 +8,7 @@
 namespace ibmlbm {
 
 cudaError_t launch_lbm_step(const LbmArgs& A, int D, int parity, cudaStream_t s);
+int lbm_step_launches(const Geo& g, int D, int parity);  // kernels launch_lbm_step launches
 cudaError_t launch_lbm_moments(const LbmArgs& A, int D, int parity, cudaStream_t s);
 cudaError_t launch_lbm_fields(const LbmArgs& A, int D, int parity, double* p, double* u,
                               cudaStream_t s);

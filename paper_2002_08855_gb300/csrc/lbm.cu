@@ -19,43 +19,43 @@ namespace ibmlbm {
 constexpr int kLbmBlock = 128;
 
 // inverse of load_pdfs: slot of f_a(x) under the layout of the given parity
-template <class L, int PARITY>
-__device__ __forceinline__ void put_pdfs(const Geo& g, float* __restrict__ f, int x, int y,
+template <class L, int PARITY, int ST>
+__device__ __forceinline__ void put_pdfs(const Geo& g, void* __restrict__ f, int x, int y,
                                          int z, long long n, const float (&fa)[L::Q]) {
-  const long long N = g.N;
+  const long long N = g.Np;  // plane stride
 #pragma unroll
   for (int a = 0; a < L::Q; ++a) {
     if (PARITY == 0 || a == 0) {
-      f[a * N + n] = fa[a];
+      pdf_store<L, ST>(f, a * N + n, a, fa[a]);
     } else {
       long long src;
       if (neighbour<L>(g, a, 1, x, y, z, n, src))
-        f[opp<L>(a) * N + src] = fa[a];
+        pdf_store<L, ST>(f, opp<L>(a) * N + src, a, fa[a]);
       else
-        f[a * N + n] = fa[a];
+        pdf_store<L, ST>(f, a * N + n, a, fa[a]);
     }
   }
 }
 
 // post-collision store of the given parity (after which the opposite parity holds)
-template <class L, int PARITY, bool INNER = false>
-__device__ __forceinline__ void store_post(const Geo& g, float* __restrict__ f, int x, int y,
+template <class L, int PARITY, int ST, bool INNER = false>
+__device__ __forceinline__ void store_post(const Geo& g, void* __restrict__ f, int x, int y,
                                            int z, long long n, const float (&fa)[L::Q]) {
-  const long long N = g.N;
+  const long long N = g.Np;  // plane stride
 #pragma unroll
   for (int a = 0; a < L::Q; ++a) {
     if (a == 0) {
-      f[n] = fa[0];
+      pdf_store<L, ST>(f, n, 0, fa[0]);
     } else if (PARITY == 0) {
-      f[opp<L>(a) * N + n] = fa[a];
+      pdf_store<L, ST>(f, opp<L>(a) * N + n, a, fa[a]);
     } else if (INNER) {
-      f[a * N + n + inner_offset<L>(g, a, -1)] = fa[a];
+      pdf_store<L, ST>(f, a * N + n + inner_offset<L>(g, a, -1), a, fa[a]);
     } else {
       long long dst;
       if (neighbour<L>(g, a, -1, x, y, z, n, dst))
-        f[a * N + dst] = fa[a];
+        pdf_store<L, ST>(f, a * N + dst, a, fa[a]);
       else
-        f[opp<L>(a) * N + n] = fa[a];
+        pdf_store<L, ST>(f, opp<L>(a) * N + n, a, fa[a]);
     }
   }
 }
@@ -135,56 +135,138 @@ __device__ __forceinline__ NodeCoord node_coord(const Geo& g, int cpr) {
 
 // ------------------------------------------------------------------ kernels
 
-// whole block (one row segment) at least one node away from every domain face
-__device__ __forceinline__ bool block_inner(const Geo& g, int x0, int y, int z, int dim) {
-  return x0 >= 1 && x0 + kLbmBlock <= g.nx - 1 && y >= 1 && y <= g.ny - 2 &&
-         (dim == 2 || (z >= 1 && z <= g.nz - 2));
-}
-
-template <class L, int PARITY, bool INNER>
-__device__ __forceinline__ void step_node(const LbmArgs& A, const NodeCoord& c) {
-  float* __restrict__ f = A.f;
-  float* __restrict__ fib = A.fib;
-  float fa[L::Q];
-  float fv[3] = {0.0f, 0.0f, 0.0f};
-  // the IB force is read for every node together with the PDFs (one memory latency);
-  // it is zero wherever no Lagrangian point spread into the node
-  load_pdfs<L, PARITY, INNER>(A.g, f, c.x, c.y, c.z, c.n, fa);
-  if (L::dim == 2) {  // interleaved [N][2]
-    const float2 v = reinterpret_cast<const float2*>(fib)[c.n];
+// IB force of one node: 2D [N][2]; 3D [N][4], non-zero only on nodes the particle
+// update marked (read only there)
+template <class L>
+__device__ __forceinline__ void ib_force(const LbmArgs& A, long long row, int x, long long n,
+                                         float (&fv)[3]) {
+  fv[0] = fv[1] = fv[2] = 0.0f;
+  if (L::dim == 2) {
+    const float2 v = reinterpret_cast<const float2*>(A.fib)[n];
     fv[0] = v.x;
     fv[1] = v.y;
-  } else {  // [N][4]; non-zero only on nodes the particle update marked
-    if ((A.mask[c.row * A.g.wpr + (c.x >> 5)] >> (c.x & 31)) & 1u) {
-      const float4 v = reinterpret_cast<const float4*>(fib)[c.n];
-      fv[0] = v.x;
-      fv[1] = v.y;
-      fv[2] = v.z;
-    }
+  } else if ((A.mask[row * A.g.wpr + (x >> 5)] >> (x & 31)) & 1u) {
+    const float4 v = reinterpret_cast<const float4*>(A.fib)[n];
+    fv[0] = v.x;
+    fv[1] = v.y;
+    fv[2] = v.z;
   }
+}
+
+template <class L>
+__device__ __forceinline__ void ib_force_clear(const LbmArgs& A, long long n, const float (&fv)[3]) {
+  if (L::dim == 2) {
+    if (fv[0] != 0.0f || fv[1] != 0.0f) reinterpret_cast<float2*>(A.fib)[n] = make_float2(0.0f, 0.0f);
+  } else if (fv[0] != 0.0f || fv[1] != 0.0f || fv[2] != 0.0f) {
+    reinterpret_cast<float4*>(A.fib)[n] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  }
+}
+
+// one node with the general addressing (walls and periodic wraps per direction)
+template <class L, int PARITY, int ST>
+__device__ __forceinline__ void step_node(const LbmArgs& A, long long row, int x, int y, int z,
+                                          long long n) {
+  float fa[L::Q], fv[3];
+  load_pdfs<L, PARITY, ST>(A.g, A.f, x, y, z, n, fa);
+  ib_force<L>(A, row, x, n, fv);
   float F[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) F[k] = A.body[k] + fv[k];
   collide<L>(fa, F, A.omega, A.kforce);
-  store_post<L, PARITY, INNER>(A.g, f, c.x, c.y, c.z, c.n, fa);
-  if (L::dim == 2) {
-    if (fv[0] != 0.0f || fv[1] != 0.0f) reinterpret_cast<float2*>(fib)[c.n] = make_float2(0.0f, 0.0f);
-  } else if (fv[0] != 0.0f || fv[1] != 0.0f || fv[2] != 0.0f) {
-    reinterpret_cast<float4*>(fib)[c.n] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  store_post<L, PARITY, ST>(A.g, A.f, x, y, z, n, fa);
+  ib_force_clear<L>(A, n, fv);
+}
+
+// In an odd step, rows whose nodes have neighbours across a y or z domain face (the
+// first and last node of every other row also do, across an x face)
+template <class L>
+__device__ __forceinline__ bool odd_edge_row(const Geo& g, int y, int z) {
+  return y == 0 || y == g.ny - 1 || (L::dim == 3 && (z == 0 || z == g.nz - 1));
+}
+
+// One full time step (Eq. 1, 4-8, 17-18) of K adjacent nodes per thread: read the
+// nodes' PDFs (AA parity) and IB force, collide, store in place.  All K nodes' loads are
+// issued before any store, so a thread keeps K nodes' bytes in flight (K = 2 for the
+// 16-bit storages, whose requests are half as large).  In an odd step the nodes whose
+// neighbourhood crosses a domain face (rows on a y or z face, the first and last node
+// of a row) are left to lbm_step_edge_kernel, so every node here uses fixed neighbour
+// offsets; the AA pattern makes the nodes independent of each other.  The even step
+// is local everywhere.
+template <class L, int PARITY, int ST, int K>
+__global__ void __launch_bounds__(kLbmBlock) lbm_step_kernel(LbmArgs A, int spr) {
+  const Geo& g = A.g;
+  const unsigned b = blockIdx.x, uspr = (unsigned)spr, uny = (unsigned)g.ny;
+  const unsigned row = b / uspr, seg = b - row * uspr;
+  const unsigned uz = row / uny;
+  const int y = (int)(row - uz * uny), z = (int)uz;
+  if (PARITY == 1 && odd_edge_row<L>(g, y, z)) return;
+  const int x0 = K * ((int)seg * kLbmBlock + (int)threadIdx.x);
+  float fa[K][L::Q], fv[K][3];
+  bool act[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int x = x0 + k;
+    act[k] = x < g.nx && !(PARITY == 1 && (x == 0 || x == g.nx - 1));
+    if (!act[k]) continue;
+    const long long n = (long long)x + (long long)g.nx * row;
+    load_pdfs<L, PARITY, ST, PARITY == 1>(g, A.f, x, y, z, n, fa[k]);
+    ib_force<L>(A, row, x, n, fv[k]);  // with the PDFs: one memory latency
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (!act[k]) continue;
+    const int x = x0 + k;
+    const long long n = (long long)x + (long long)g.nx * row;
+    float F[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) F[c] = A.body[c] + fv[k][c];
+    collide<L>(fa[k], F, A.omega, A.kforce);
+    store_post<L, PARITY, ST, PARITY == 1>(g, A.f, x, y, z, n, fa[k]);
+    ib_force_clear<L>(A, n, fv[k]);
   }
 }
 
-// One full time step on every node: read f (AA parity) and the IB force (3D: on marked
-// nodes only), collide, stream in place, clear the IB force.
-template <class L, int PARITY>
-__global__ void __launch_bounds__(kLbmBlock) lbm_step_kernel(LbmArgs A, int cpr) {
-  const NodeCoord c = node_coord(A.g, cpr);
-  if (PARITY == 1 && block_inner(A.g, c.x - (int)threadIdx.x, c.y, c.z, L::dim)) {
-    step_node<L, PARITY, true>(A, c);
-    return;
+// The odd-step nodes lbm_step_kernel leaves: every node of the face rows, then the
+// two end nodes of every other row, one thread per node, general addressing.
+template <class L, int ST>
+__global__ void __launch_bounds__(kLbmBlock) lbm_step_edge_kernel(LbmArgs A, long long nface,
+                                                                 long long nends) {
+  const Geo& g = A.g;
+  const long long t = blockIdx.x * (long long)kLbmBlock + threadIdx.x;
+  int x, y, z;
+  if (t < nface * g.nx) {  // face rows
+    const long long k = t / g.nx;
+    x = (int)(t - k * g.nx);
+    if (L::dim == 2) {
+      y = k == 0 ? 0 : g.ny - 1;
+      z = 0;
+    } else {
+      const long long plane = g.ny;                      // rows of the z = 0 face
+      const long long zf = g.nz > 1 ? 2 * plane : plane;  // rows of both z faces
+      if (k < plane) {
+        y = (int)k;
+        z = 0;
+      } else if (k < zf) {
+        y = (int)(k - plane);
+        z = g.nz - 1;
+      } else {
+        const long long j = k - zf;  // y faces of the inner z planes
+        const int per = g.ny > 1 ? 2 : 1;
+        z = 1 + (int)(j / per);
+        y = (j % per) == 0 ? 0 : g.ny - 1;
+      }
+    }
+  } else {
+    const long long j = t - nface * g.nx;
+    if (j >= nends) return;
+    const int ends = g.nx > 1 ? 2 : 1;
+    const long long r = j / ends;  // inner row: y in 1..ny-2, z in 1..nz-2 (3D)
+    x = (j % ends) == 0 ? 0 : g.nx - 1;
+    y = 1 + (int)(r % (g.ny - 2));
+    z = L::dim == 3 ? 1 + (int)(r / (g.ny - 2)) : 0;
   }
-  if (!c.valid) return;
-  step_node<L, PARITY, false>(A, c);
+  const long long row = (long long)y + (long long)g.ny * z;
+  step_node<L, 1, ST>(A, row, x, y, z, (long long)x + (long long)g.nx * row);
 }
 
 // u* = sum_a e_a f_a (Eq. 5) on the flagged nodes only: one thread per node in large
@@ -192,7 +274,7 @@ __global__ void __launch_bounds__(kLbmBlock) lbm_step_kernel(LbmArgs A, int cpr)
 // is cleared before the particle update marks the next step's nodes.
 constexpr int kMomBlock = 512;
 
-template <class L, int PARITY>
+template <class L, int PARITY, int ST>
 __global__ void __launch_bounds__(kMomBlock) lbm_moments_kernel(LbmArgs A) {
   const long long n = blockIdx.x * (long long)kMomBlock + threadIdx.x;
   if (n >= A.g.N) return;
@@ -205,7 +287,11 @@ __global__ void __launch_bounds__(kMomBlock) lbm_moments_kernel(LbmArgs A) {
   const unsigned z = row / uny;
   const int y = (int)(row - z * uny);
   float fa[L::Q], us[3], s1;
-  load_pdfs<L, PARITY>(A.g, A.f, x, y, (int)z, n, fa);
+  if (PARITY == 1 && x >= 1 && x <= A.g.nx - 2 && y >= 1 && y <= A.g.ny - 2 &&
+      (L::dim == 2 || ((int)z >= 1 && (int)z <= A.g.nz - 2)))
+    load_pdfs<L, PARITY, ST, true>(A.g, A.f, x, y, (int)z, n, fa);  // fixed neighbour offsets
+  else
+    load_pdfs<L, PARITY, ST>(A.g, A.f, x, y, (int)z, n, fa);
   moments<L>(fa, us, s1);
   if (L::dim == 3)
     reinterpret_cast<float4*>(A.ustar)[n] = make_float4(us[0], us[1], us[2], 0.0f);
@@ -214,13 +300,13 @@ __global__ void __launch_bounds__(kMomBlock) lbm_moments_kernel(LbmArgs A) {
 }
 
 // p (Eq. 6 with u = u*) and u* (Eq. 5) on every node, as doubles.
-template <class L, int PARITY>
+template <class L, int PARITY, int ST>
 __global__ void __launch_bounds__(kLbmBlock) lbm_fields_kernel(LbmArgs A, int cpr, double* p,
                                                               double* u) {
   const NodeCoord c = node_coord(A.g, cpr);
   if (!c.valid) return;
   float fa[L::Q], us[3], s1;
-  load_pdfs<L, PARITY>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
+  load_pdfs<L, PARITY, ST>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
   moments<L>(fa, us, s1);
   const float uu = us[0] * us[0] + us[1] * us[1] + us[2] * us[2];
   if (p) p[c.n] = (double)pressure<L>(s1, uu);
@@ -231,18 +317,18 @@ __global__ void __launch_bounds__(kLbmBlock) lbm_fields_kernel(LbmArgs A, int cp
 }
 
 // canonical [Q][N] copy of the current PDFs
-template <class L, int PARITY>
+template <class L, int PARITY, int ST>
 __global__ void __launch_bounds__(kLbmBlock) lbm_get_kernel(LbmArgs A, int cpr, float* out) {
   const NodeCoord c = node_coord(A.g, cpr);
   if (!c.valid) return;
   float fa[L::Q];
-  load_pdfs<L, PARITY>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
+  load_pdfs<L, PARITY, ST>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
 #pragma unroll
   for (int a = 0; a < L::Q; ++a) out[a * A.g.N + c.n] = fa[a];
 }
 
 // write canonical [Q][N] PDFs into the layout of the current parity
-template <class L, int PARITY>
+template <class L, int PARITY, int ST>
 __global__ void __launch_bounds__(kLbmBlock) lbm_put_kernel(LbmArgs A, int cpr,
                                                            const float* in) {
   const NodeCoord c = node_coord(A.g, cpr);
@@ -250,11 +336,11 @@ __global__ void __launch_bounds__(kLbmBlock) lbm_put_kernel(LbmArgs A, int cpr,
   float fa[L::Q];
 #pragma unroll
   for (int a = 0; a < L::Q; ++a) fa[a] = in[a * A.g.N + c.n];
-  put_pdfs<L, PARITY>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
+  put_pdfs<L, PARITY, ST>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
 }
 
 // equilibrium of Eq. 4 for given p [N] and u [D][N] (doubles), current parity layout
-template <class L, int PARITY>
+template <class L, int PARITY, int ST>
 __global__ void __launch_bounds__(kLbmBlock) lbm_equilibrium_kernel(LbmArgs A, int cpr,
                                                                    const double* p,
                                                                    const double* u) {
@@ -272,7 +358,7 @@ __global__ void __launch_bounds__(kLbmBlock) lbm_equilibrium_kernel(LbmArgs A, i
     const float eu = L::e(a, 0) * uv[0] + L::e(a, 1) * uv[1] + L::e(a, 2) * uv[2];
     fa[a] = L::w(a) * (3.0f * pp + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
   }
-  put_pdfs<L, PARITY>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
+  put_pdfs<L, PARITY, ST>(A.g, A.f, c.x, c.y, c.z, c.n, fa);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -281,33 +367,91 @@ static dim3 lbm_grid(const Geo& g, int& cpr) {
   return dim3((unsigned)((long long)cpr * g.rows));
 }
 
-#define IBMLBM_DISPATCH(D, PARITY, KERNEL, ...)                                     \
-  do {                                                                              \
-    if ((D) == 2) {                                                                 \
-      if ((PARITY) == 0) KERNEL<Lat<2>, 0><<<grid, kLbmBlock, 0, s>>>(__VA_ARGS__); \
-      else KERNEL<Lat<2>, 1><<<grid, kLbmBlock, 0, s>>>(__VA_ARGS__);               \
-    } else {                                                                        \
-      if ((PARITY) == 0) KERNEL<Lat<3>, 0><<<grid, kLbmBlock, 0, s>>>(__VA_ARGS__); \
-      else KERNEL<Lat<3>, 1><<<grid, kLbmBlock, 0, s>>>(__VA_ARGS__);               \
-    }                                                                               \
+#define IBMLBM_DISPATCH_ST(L, PARITY, KERNEL, GRID, BLOCK, ...)                                  \
+  do {                                                                                          \
+    if (A.store == STORE_F32) KERNEL<L, PARITY, STORE_F32><<<GRID, BLOCK, 0, s>>>(__VA_ARGS__);   \
+    else if (A.store == STORE_F16) KERNEL<L, PARITY, STORE_F16><<<GRID, BLOCK, 0, s>>>(__VA_ARGS__); \
+    else KERNEL<L, PARITY, STORE_BF16><<<GRID, BLOCK, 0, s>>>(__VA_ARGS__);                       \
   } while (0)
 
+#define IBMLBM_DISPATCH_G(D, PARITY, KERNEL, GRID, BLOCK, ...)                               \
+  do {                                                                                       \
+    if ((D) == 2) {                                                                          \
+      if ((PARITY) == 0) IBMLBM_DISPATCH_ST(Lat<2>, 0, KERNEL, GRID, BLOCK, __VA_ARGS__);      \
+      else IBMLBM_DISPATCH_ST(Lat<2>, 1, KERNEL, GRID, BLOCK, __VA_ARGS__);                    \
+    } else {                                                                                 \
+      if ((PARITY) == 0) IBMLBM_DISPATCH_ST(Lat<3>, 0, KERNEL, GRID, BLOCK, __VA_ARGS__);      \
+      else IBMLBM_DISPATCH_ST(Lat<3>, 1, KERNEL, GRID, BLOCK, __VA_ARGS__);                    \
+    }                                                                                        \
+  } while (0)
+
+#define IBMLBM_DISPATCH(D, PARITY, KERNEL, ...) \
+  IBMLBM_DISPATCH_G(D, PARITY, KERNEL, grid, kLbmBlock, __VA_ARGS__)
+
+template <class L, int PARITY, int ST>
+static void launch_step_main(const LbmArgs& A, cudaStream_t s) {
+  constexpr int K = ST == STORE_F32 ? 1 : 2;
+  const int spr = (A.g.nx + K * kLbmBlock - 1) / (K * kLbmBlock);
+  const dim3 grid((unsigned)((long long)spr * A.g.rows));
+  lbm_step_kernel<L, PARITY, ST, K><<<grid, kLbmBlock, 0, s>>>(A, spr);
+}
+
+// odd-step face rows and inner-row ends (lbm_step_edge_kernel's index space)
+template <class L, int ST>
+static void launch_step_edge(const LbmArgs& A, cudaStream_t s) {
+  const Geo& g = A.g;
+  long long nface, inner;
+  if (L::dim == 2) {
+    nface = g.ny > 1 ? 2 : 1;
+    inner = g.ny > 2 ? g.ny - 2 : 0;
+  } else {
+    nface = (long long)g.ny * (g.nz > 1 ? 2 : 1) + (long long)(g.nz > 2 ? g.nz - 2 : 0) * (g.ny > 1 ? 2 : 1);
+    inner = (long long)(g.ny > 2 ? g.ny - 2 : 0) * (g.nz > 2 ? g.nz - 2 : 0);
+  }
+  const long long nends = inner * (g.nx > 1 ? 2 : 1);
+  const long long total = nface * g.nx + nends;
+  if (total == 0) return;
+  const dim3 grid((unsigned)((total + kLbmBlock - 1) / kLbmBlock));
+  lbm_step_edge_kernel<L, ST><<<grid, kLbmBlock, 0, s>>>(A, nface, nends);
+}
+
+// kernels launch_lbm_step launches: the main kernel, and in an odd step the edge kernel
+int lbm_step_launches(const Geo& g, int D, int parity) {
+  if (parity == 0) return 1;
+  const long long faces = D == 2 ? (g.ny > 1 ? 2 : 1)
+                                 : (long long)g.ny * (g.nz > 1 ? 2 : 1) +
+                                       (long long)(g.nz > 2 ? g.nz - 2 : 0) * (g.ny > 1 ? 2 : 1);
+  return faces * g.nx > 0 ? 2 : 1;
+}
+
+template <class L, int PARITY>
+static void launch_step_st(const LbmArgs& A, cudaStream_t s) {
+  if (A.store == STORE_F32) launch_step_main<L, PARITY, STORE_F32>(A, s);
+  else if (A.store == STORE_F16) launch_step_main<L, PARITY, STORE_F16>(A, s);
+  else launch_step_main<L, PARITY, STORE_BF16>(A, s);
+  if (PARITY == 1) {
+    if (A.store == STORE_F32) launch_step_edge<L, STORE_F32>(A, s);
+    else if (A.store == STORE_F16) launch_step_edge<L, STORE_F16>(A, s);
+    else launch_step_edge<L, STORE_BF16>(A, s);
+  }
+}
+
 cudaError_t launch_lbm_step(const LbmArgs& A, int D, int parity, cudaStream_t s) {
-  int cpr;
-  const dim3 grid = lbm_grid(A.g, cpr);
-  IBMLBM_DISPATCH(D, parity, lbm_step_kernel, A, cpr);
+  if (D == 2) {
+    if (parity == 0) launch_step_st<Lat<2>, 0>(A, s);
+    else launch_step_st<Lat<2>, 1>(A, s);
+  } else {
+    if (parity == 0) launch_step_st<Lat<3>, 0>(A, s);
+    else launch_step_st<Lat<3>, 1>(A, s);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_lbm_moments(const LbmArgs& A, int D, int parity, cudaStream_t s) {
   const dim3 grid((unsigned)((A.g.N + kMomBlock - 1) / kMomBlock));
-  if (D == 2) {
-    if (parity == 0) lbm_moments_kernel<Lat<2>, 0><<<grid, kMomBlock, 0, s>>>(A);
-    else lbm_moments_kernel<Lat<2>, 1><<<grid, kMomBlock, 0, s>>>(A);
-  } else {
-    if (parity == 0) lbm_moments_kernel<Lat<3>, 0><<<grid, kMomBlock, 0, s>>>(A);
-    else lbm_moments_kernel<Lat<3>, 1><<<grid, kMomBlock, 0, s>>>(A);
-  }
+  if (D != 3) return cudaErrorInvalidValue;  // 2D computes u* per particle box
+  if (parity == 0) IBMLBM_DISPATCH_ST(Lat<3>, 0, lbm_moments_kernel, grid, kMomBlock, A);
+  else IBMLBM_DISPATCH_ST(Lat<3>, 1, lbm_moments_kernel, grid, kMomBlock, A);
   return cudaGetLastError();
 }
 

@@ -1,15 +1,61 @@
 // Reading the PDFs of a node under the AA-pattern layout (device helpers shared by
 // the lattice kernels and the immersed-boundary kernels).
 //
-// AA pattern, one PDF array a[Q][N]:
+// AA pattern, one PDF array a[Q][N] (planes g.Np >= N elements apart):
 //   parity 0 (before an even step): f_a(x) is stored at a[a][x];
 //   parity 1 (before an odd step): f_a(x) is stored at a[opp(a)][x - e_a], or at
 //     a[a][x] when x - e_a lies beyond a wall (halfway bounce-back).
+//
+// Storage of one PDF (the run's pdf_storage): FP32 as is, or FP16 / BF16 holding
+// h_a = f_a / w_a (in the deviation gauge f = 0 at rest, so dividing by the weight
+// puts every direction on one scale); all arithmetic stays FP32.
 #pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "common.cuh"
 
 namespace ibmlbm {
+
+enum : int { STORE_F32 = 0, STORE_F16 = 1, STORE_BF16 = 2 };
+
+template <int ST>
+struct PdfType;
+template <>
+struct PdfType<STORE_F32> {
+  using T = float;
+};
+template <>
+struct PdfType<STORE_F16> {
+  using T = __half;
+};
+template <>
+struct PdfType<STORE_BF16> {
+  using T = __nv_bfloat16;
+};
+
+template <class L, int ST>
+__device__ __forceinline__ float pdf_load(const void* f, long long idx, int a) {
+  if constexpr (ST == STORE_F32) {
+    return static_cast<const float*>(f)[idx];
+  } else if constexpr (ST == STORE_F16) {
+    return L::w(a) * __half2float(static_cast<const __half*>(f)[idx]);
+  } else {
+    return L::w(a) * __bfloat162float(static_cast<const __nv_bfloat16*>(f)[idx]);
+  }
+}
+
+template <class L, int ST>
+__device__ __forceinline__ void pdf_store(void* f, long long idx, int a, float v) {
+  if constexpr (ST == STORE_F32) {
+    static_cast<float*>(f)[idx] = v;
+  } else if constexpr (ST == STORE_F16) {
+    static_cast<__half*>(f)[idx] = __float2half_rn(v * (1.0f / L::w(a)));
+  } else {
+    static_cast<__nv_bfloat16*>(f)[idx] = __float2bfloat16_rn(v * (1.0f / L::w(a)));
+  }
+}
 
 // index of the neighbour x - s*e_a (s = +1 for the pull source, -1 for the push
 // target); false if it lies beyond a wall
@@ -55,22 +101,22 @@ __device__ __forceinline__ long long inner_offset(const Geo& g, int a, int s) {
 
 // pre-collision PDFs f_a(x) of the current time under the layout of the given parity;
 // INNER: the node is at least one node away from every domain face
-template <class L, int PARITY, bool INNER = false>
-__device__ __forceinline__ void load_pdfs(const Geo& g, const float* __restrict__ f, int x,
+template <class L, int PARITY, int ST, bool INNER = false>
+__device__ __forceinline__ void load_pdfs(const Geo& g, const void* __restrict__ f, int x,
                                           int y, int z, long long n, float (&fa)[L::Q]) {
-  const long long N = g.N;
+  const long long N = g.Np;  // plane stride
 #pragma unroll
   for (int a = 0; a < L::Q; ++a) {
     if (PARITY == 0 || a == 0) {
-      fa[a] = f[a * N + n];
+      fa[a] = pdf_load<L, ST>(f, a * N + n, a);
     } else if (INNER) {
-      fa[a] = f[opp<L>(a) * N + n + inner_offset<L>(g, a, 1)];
+      fa[a] = pdf_load<L, ST>(f, opp<L>(a) * N + n + inner_offset<L>(g, a, 1), opp<L>(a));
     } else {
       long long src;
       if (neighbour<L>(g, a, 1, x, y, z, n, src))
-        fa[a] = f[opp<L>(a) * N + src];
+        fa[a] = pdf_load<L, ST>(f, opp<L>(a) * N + src, opp<L>(a));
       else
-        fa[a] = f[a * N + n];
+        fa[a] = pdf_load<L, ST>(f, a * N + n, a);
     }
   }
 }

@@ -52,9 +52,18 @@ def test_workspace_size_of_the_2048x4096_cavity(lib):
     assert need < n < need * 1.05
 
 
+def test_half_precision_storage_halves_the_pdf_bytes(lib):
+    w = inputs.cavity_2d_large(0.1)
+    n32 = binding.workspace_size(w)
+    n16 = binding.workspace_size(w.with_(pdf_storage=1))
+    assert n32 - n16 == 9 * 2048 * 4096 * 2
+    assert binding.workspace_size(w.with_(pdf_storage=2)) == n16
+
+
 @pytest.mark.parametrize("field,value,code", [
     ("dim", 4, "INVALID_ARG"), ("tau", 0.5, "INVALID_ARG"), ("nx", 0, "INVALID_ARG"),
     ("delta_kind", 3, "UNSUPPORTED"), ("n_lag", 0, "INVALID_ARG"), ("drs", 0.0, "INVALID_ARG"),
+    ("pdf_storage", 3, "INVALID_ARG"),
 ])
 def test_invalid_configurations_are_rejected(lib, field, value, code):
     w = inputs.cavity_2d_small().as_dict()

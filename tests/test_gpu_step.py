@@ -21,7 +21,9 @@ def test_cavity_128x256_200_steps():
     X0 = inputs.place_particles(w)
     sim = Simulation(w, X0)
     ref = oracle.Sim(w.as_dict(), X0)
-    sim.step(200)
+    sim.step(199)
+    X199 = sim.get_particles()["X"]
+    sim.step(1)  # its contact list is built from the centres of step 199
     sim.sync()
     ref.step(200)
     _, ug = sim.get_fields()
@@ -34,7 +36,7 @@ def test_cavity_128x256_200_steps():
     assert e_u < 1e-5
     assert e_X < 1e-5
     assert e_x < 1e-5
-    assert np.array_equal(sim.get_pairs(), oracle.pairs_bruteforce(w.as_dict(), pg["X"])) or True
+    assert np.array_equal(sim.get_pairs(), oracle.pairs_bruteforce(w.as_dict(), X199))
     sim.close()
 
 
