@@ -167,7 +167,7 @@ Layout carve(const ibm_lbm_config* c, const Derived& d) {
   l.f = cv.take((c->pdf_storage == IBMLBM_PDF_FP32 ? 4 : 2) * ((size_t)d.Q * d.g.Np + 64));
   l.ustar = cv.take(D == 3 ? sizeof(float) * 4 * N : 0);  // 3D [N][4]; 2D keeps u* per particle box
   l.fib = cv.take(sizeof(float) * (D == 3 ? 4 : 2) * N);     // 2D [N][2], 3D [N][4]
-  l.mask = cv.take(D == 3 ? sizeof(uint32_t) * (size_t)d.g.rows * d.g.wpr : 0);  // 3D only
+  l.mask = cv.take(D == 3 ? 2 * sizeof(uint32_t) * (size_t)d.g.rows * d.g.wpr : 0);  // 3D, one per parity
   l.X0 = cv.take(sizeof(double) * np * D);
   l.X1 = cv.take(sizeof(double) * np * D);
   l.U = cv.take(sizeof(double) * np * D);
@@ -253,14 +253,18 @@ struct ibm_lbm_handle {
   template <class T>
   T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
 
-  LbmArgs lbm() const {
+  // node mask of the step of the given parity (marked by the regeneration before it)
+  uint32_t* mask(int parity) const {
+    return at<uint32_t>(l.mask) + (size_t)parity * d.g.rows * d.g.wpr;
+  }
+  LbmArgs lbm(int parity) const {
     LbmArgs a{};
     a.g = d.g;
     a.f = at<void>(l.f);
     a.store = cfg.pdf_storage;
     a.ustar = at<float>(l.ustar);
     a.fib = at<float>(l.fib);
-    a.mask = at<uint32_t>(l.mask);
+    a.mask = mask(parity);
     a.omega = (float)(1.0 / cfg.tau);
     a.kforce = (float)(1.0 - 0.5 / cfg.tau);
     for (int k = 0; k < 3; ++k) a.body[k] = (k < d.D) ? (float)cfg.body_force[k] : 0.0f;
@@ -321,7 +325,7 @@ struct ibm_lbm_handle {
     a.Omf = at<float>(l.Omf);
     a.Xb_out = at<long long>(parity ? l.Xb1 : l.Xb0);
     a.Ub_out = at<float>(parity ? l.Ub1 : l.Ub0);
-    a.mask = at<uint32_t>(l.mask);
+    a.mask = mask(parity);
     return a;
   }
   PairArgs pairs(int parity, int have_prev) const {
@@ -382,11 +386,11 @@ struct ibm_lbm_handle {
 
 namespace {
 
-// 3D node mask (lbm_moments and the f_IB read of lbm_step use it): cleared before the
-// regeneration marks the nodes of the new particle positions
-cudaError_t clear_mask(ibm_lbm_handle* h, cudaStream_t s) {
-  return cudaMemsetAsync(h->at<uint32_t>(h->l.mask), 0,
-                         sizeof(uint32_t) * (size_t)h->d.g.rows * h->d.g.wpr, s);
+// 3D node mask of a parity (lbm_moments and the f_IB read of lbm_step use it):
+// cleared before the regeneration marks the nodes of the new particle positions
+cudaError_t clear_mask(ibm_lbm_handle* h, int parity, cudaStream_t s) {
+  if (h->d.D != 3) return cudaSuccess;  // 2D keeps no node mask
+  return cudaMemsetAsync(h->mask(parity), 0, sizeof(uint32_t) * (size_t)h->d.g.rows * h->d.g.wpr, s);
 }
 
 // Enqueue one step of the given parity.  With ev != nullptr an event is recorded
@@ -395,7 +399,7 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
   const cudaStream_t s = h->s;
   const bool particles = h->cfg.n_particles > 0;
   int k = 0;
-  const LbmArgs la = h->lbm();
+  const LbmArgs la = h->lbm(parity);
   const IbmArgs ia = h->ibm(parity);
   if (ev) CUDA_TRY(cudaEventRecord(ev[0], s));
   if (particles && h->d.D == 3) {  // 2D computes u* per particle box in the first interpolation
@@ -421,29 +425,23 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
   }
   if (ev) CUDA_TRY(cudaEventRecord(ev[2], s));
   if (particles && !ev) {
-    // The contact forces, the Newton-Euler update and (2D) the regeneration of the
-    // points read nothing lbm_step writes and write nothing it reads, so they run on
-    // the side stream while lbm_step streams the PDFs.  3D regeneration marks the node
-    // mask that lbm_step clears, so it waits for lbm_step.
+    // The contact forces, the Newton-Euler update and the regeneration of the points
+    // (into the other point buffer and the other node mask) read nothing lbm_step
+    // writes and write nothing it reads, so they run on the side stream while
+    // lbm_step streams the PDFs.
     CUDA_TRY(cudaEventRecord(h->fork, s));
     CUDA_TRY(cudaStreamWaitEvent(h->side, h->fork, 0));
     const PairArgs pa = h->pairs(parity, have_prev);
     CUDA_TRY(launch_pair_cells(pa, h->side));
     CUDA_TRY(launch_pair_contacts(pa, h->side));
     k += 3;
-    if (h->d.D == 2) {
-      CUDA_TRY(launch_regen(h->regen(1 - parity), 0, h->side));
-      ++k;
-    }
+    CUDA_TRY(clear_mask(h, 1 - parity, h->side));
+    CUDA_TRY(launch_regen(h->regen(1 - parity), 0, h->side));
+    ++k;
     CUDA_TRY(cudaEventRecord(h->join, h->side));
     CUDA_TRY(launch_lbm_step(la, h->d.D, parity, s));
     k += lbm_step_launches(h->d.g, h->d.D, parity);
     CUDA_TRY(cudaStreamWaitEvent(s, h->join, 0));
-    if (h->d.D == 3) {
-      CUDA_TRY(clear_mask(h, s));
-      CUDA_TRY(launch_regen(h->regen(1 - parity), 0, s));
-      ++k;
-    }
     *nk = k;
     return IBMLBM_OK;
   }
@@ -459,7 +457,7 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
   }
   if (ev) CUDA_TRY(cudaEventRecord(ev[4], s));
   if (particles) {
-    if (h->d.D == 3) CUDA_TRY(clear_mask(h, s));
+    CUDA_TRY(clear_mask(h, 1 - parity, s));
     CUDA_TRY(launch_regen(h->regen(1 - parity), 0, s));
     ++k;
   }
@@ -498,7 +496,7 @@ int capture_graph(ibm_lbm_handle* h, int parity) {
 // points and node marks of the current state (after init or a new particle state)
 int regenerate_points(ibm_lbm_handle* h) {
   if (h->cfg.n_particles == 0) return IBMLBM_OK;
-  if (h->d.D == 3) CUDA_TRY(clear_mask(h, h->s));
+  CUDA_TRY(clear_mask(h, (int)(h->step & 1), h->s));
   CUDA_TRY(launch_regen(h->regen((int)(h->step & 1)), 1, h->s));
   h->launches += 1;
   return IBMLBM_OK;
@@ -648,7 +646,7 @@ int ibm_lbm_set_pdfs(ibm_lbm_handle* h, const float* d_f) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (!d_f) return fail(IBMLBM_ERR_INVALID_ARG, "f is NULL");
-  CUDA_TRY(launch_lbm_put(h->lbm(), h->d.D, (int)(h->step & 1), d_f, h->s));
+  CUDA_TRY(launch_lbm_put(h->lbm((int)(h->step & 1)), h->d.D, (int)(h->step & 1), d_f, h->s));
   h->launches += 1;
   return IBMLBM_OK;
 }
@@ -657,7 +655,7 @@ int ibm_lbm_get_pdfs(ibm_lbm_handle* h, float* d_f) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (!d_f) return fail(IBMLBM_ERR_INVALID_ARG, "f is NULL");
-  CUDA_TRY(launch_lbm_get(h->lbm(), h->d.D, (int)(h->step & 1), d_f, h->s));
+  CUDA_TRY(launch_lbm_get(h->lbm((int)(h->step & 1)), h->d.D, (int)(h->step & 1), d_f, h->s));
   h->launches += 1;
   return IBMLBM_OK;
 }
@@ -666,7 +664,7 @@ int ibm_lbm_set_fields(ibm_lbm_handle* h, const double* d_p, const double* d_u) 
   int rc = check_handle(h);
   if (rc) return rc;
   if (!d_p || !d_u) return fail(IBMLBM_ERR_INVALID_ARG, "p or u is NULL");
-  CUDA_TRY(launch_lbm_equilibrium(h->lbm(), h->d.D, (int)(h->step & 1), d_p, d_u, h->s));
+  CUDA_TRY(launch_lbm_equilibrium(h->lbm((int)(h->step & 1)), h->d.D, (int)(h->step & 1), d_p, d_u, h->s));
   h->launches += 1;
   return IBMLBM_OK;
 }
@@ -675,7 +673,7 @@ int ibm_lbm_get_fields(ibm_lbm_handle* h, double* d_p, double* d_u) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (!d_p && !d_u) return IBMLBM_OK;
-  CUDA_TRY(launch_lbm_fields(h->lbm(), h->d.D, (int)(h->step & 1), d_p, d_u, h->s));
+  CUDA_TRY(launch_lbm_fields(h->lbm((int)(h->step & 1)), h->d.D, (int)(h->step & 1), d_p, d_u, h->s));
   h->launches += 1;
   return IBMLBM_OK;
 }

@@ -11,9 +11,9 @@
 //                         each particle's node box instead)
 //   fib    float  IB force density, zero outside the IBM phase: 2D [N][2],
 //                 3D [N][4] (fourth component unused)
-//   mask   [rows][wpr] u32  3D: one bit per node, the nodes within R + 2 sqrt(3) of a
-//                           particle centre (support of every Lagrangian point
-//                           and the particle interior)
+//   mask   [2][rows][wpr] u32  3D, one per step parity, one bit per node: the nodes
+//                           within R + 2 sqrt(3) of a particle centre (support of every
+//                           Lagrangian point and the particle interior)
 //   particle state in double, Lagrangian point data [npts][D]; point positions as
 //   32.32 fixed-point int64 (integer part = node anchor, low word = fraction), so
 //   per-point work needs no double-precision arithmetic.

@@ -761,7 +761,7 @@ __global__ void __launch_bounds__(256) ibm_forces2_kernel(IbmArgs A) {
 
 // One warp per particle: regenerate its Lagrangian points for the next step,
 //   X_b = X_c + r_b (32.32 fixed point), U_b = U_c + Omega x r_b (single precision),
-// and mark the nodes within mark_radius of the centre for the next lbm_moments.
+// and (3D) mark the nodes within mark_radius of the centre in the next step's node mask.
 // init != 0 first refreshes the fixed-point centre and the single-precision
 // velocities from the double-precision state (initial state, new particle state).
 template <int D>
@@ -799,7 +799,8 @@ __global__ void __launch_bounds__(256) regen_kernel(RegenArgs A, int init) {
   }
   // 3D: mark the nodes of the ball |x - X_c| <= mark_radius, row by row (single
   // precision relative to the centre's anchor node; the radius carries a safety
-  // margin).  2D computes u* per particle box and needs no marks.
+  // margin): the nodes where u* is needed and f_IB can be non-zero.  2D keeps u* per
+  // particle box and reads f_IB everywhere, so it marks nothing.
   if (D == 2) return;
   int an[3] = {0, 0, 0};
   float fr[3] = {0.0f, 0.0f, 0.0f};

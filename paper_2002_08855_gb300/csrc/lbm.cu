@@ -135,8 +135,9 @@ __device__ __forceinline__ NodeCoord node_coord(const Geo& g, int cpr) {
 
 // ------------------------------------------------------------------ kernels
 
-// IB force of one node: 2D [N][2]; 3D [N][4], non-zero only on nodes the particle
-// update marked (read only there)
+// IB force of one node.  2D [N][2], read for every node together with the PDFs (one
+// memory latency; a read that first waits for the node mask was measured slower);
+// 3D [N][4], read only on nodes the particle update marked (where it can be non-zero)
 template <class L>
 __device__ __forceinline__ void ib_force(const LbmArgs& A, long long row, int x, long long n,
                                          float (&fv)[3]) {
