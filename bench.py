@@ -10,8 +10,9 @@ Metric: MLUPS = N_grid * steps / (1e6 * seconds) (Eq. 52), whole job over all ra
 for plain FP32 PDF storage (the headline) and for the chosen form, FP16 storage of
 h = f / w with FP32 arithmetic, at its stated error.  Also reported: the roofline of
 the dominant kernel (lbm_step) against the measured HBM copy bandwidth, an
-end-to-end number through the C ABI with host buffers, and the FP64 CPU oracle timed
-on a bounded sample on the host cores.
+end-to-end number through the C ABI with host buffers, the FP64 CPU oracle timed
+on a bounded sample on the host cores, and the batched ensemble of 256 independent
+cavities (aggregate MLUPS).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 (N > 1: launch with torchrun; each rank runs an independent replica.)
@@ -274,6 +275,36 @@ def _chosen_form(args, w, X, dev, peak, peak_kind, local):
     }
 
 
+def _ensemble(args, dev, local):
+    """The batched ensemble: 256 independent D2Q9 cavities (sides 64..512, 1..200
+    circles of one diameter 8..16 per cavity, N_L = round(pi d)) stepped together with
+    fused launches; aggregate MLUPS over all members."""
+    import torch
+
+    from paper_2002_08855_gb300 import binding, inputs
+
+    ws = inputs.ensemble_2d()
+    Xs = [inputs.place_particles(w) for w in ws]
+    b = binding.Batch(ws, Xs, device=str(dev))
+    b.step(args.warmup)
+    b.sync()
+    n0 = b.launch_count()
+    with ClockSampler(local) as clk:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(b.stream)
+        b.step(args.steps)
+        ev1.record(b.stream)
+        ev1.synchronize()
+        b.sync()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    out = {"workload": "ensemble2d_256_cavities", "members": len(ws), "nodes": b.n_grid,
+           "particles": int(sum(w.n_particles for w in ws)), "value": b.n_grid / (ms * 1e3),
+           "unit": METRIC, "ms_per_step": ms, "gpu_launches_per_step": (b.launch_count() - n0) / args.steps,
+           "pdf_storage": "fp32", "clocks": clk.summary()}
+    b.close()
+    return out
+
+
 def run(args):
     import torch
 
@@ -340,6 +371,8 @@ def run(args):
 
     # the chosen form: the same workload with the PDFs stored as FP16 h = f / w
     chosen = _chosen_form(args, w, X, dev, peak, peak_kind, local)
+    # the batched ensemble of independent cavities
+    ensemble = _ensemble(args, dev, local)
 
     # end to end through the C ABI with host buffers: init from host centres, then per
     # step one ibm_lbm_step and a read of the particle state into pinned host memory
@@ -384,6 +417,7 @@ def run(args):
                     "d2h_bytes_per_step": int(pin_x.nbytes + pin_u.nbytes)},
             "cpu_baseline": base,
             "chosen_form": chosen,
+            "ensemble": ensemble,
         }
         print(json.dumps(line))
     if dist is not None:

@@ -223,6 +223,45 @@ int ibm_lbm_pair_search_static(int32_t dim, const int32_t* n_nodes, const int32_
                                int32_t max_neighbors, int32_t* d_pairs, int64_t cap,
                                int64_t* h_count, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched ensemble: many independent 2D cavities stepped together.  Each member is an
+ * ordinary run (its own cavity size, particle count, diameter, points per particle,
+ * relaxation time, ...), and every kernel of a batch step runs once for all members
+ * (one launch whose blocks look up their member), so a step costs about a dozen
+ * launches whatever the number of members; steps after the first replay a CUDA graph.
+ * All members must be 2D and share pdf_storage (FP32 or FP16) and mdf_iters.  The
+ * paper runs one cavity at a time; the batch is an execution mode of the same method
+ * and gives each member the results of that member run alone.
+ */
+typedef struct ibm_lbm_batch ibm_lbm_batch;
+
+/* Device bytes of a batch of n members (their workspaces and the batch's tables). */
+int ibm_lbm_batch_workspace_size(const ibm_lbm_config* cfgs, int32_t n, size_t* bytes);
+
+/* Create a batch in caller-provided device memory (256-byte aligned, borrowed until
+ * ibm_lbm_batch_destroy).  h_centres[i]: host [n_particles][2] centres of member i
+ * (NULL for a member without particles).  Every member's kernels run on stream.
+ * Errors: as ibm_lbm_init for any member; UNSUPPORTED for 3D or BF16 members;
+ * INVALID_ARG when members differ in pdf_storage or mdf_iters. */
+int ibm_lbm_batch_init(const ibm_lbm_config* cfgs, int32_t n, void* d_workspace, size_t bytes,
+                       void* stream, const double* const* h_centres, ibm_lbm_batch** out);
+
+/* Enqueue n_steps steps of every member; returns after enqueueing. */
+int ibm_lbm_batch_step(ibm_lbm_batch* b, int32_t n_steps);
+
+/* Wait for the stream and report the first member status (as ibm_lbm_sync). */
+int ibm_lbm_batch_sync(ibm_lbm_batch* b);
+
+/* Member i as a run handle, for the field and particle calls (get_fields,
+ * get_particles, get_pdfs, ...).  Owned by the batch; do not step or destroy it. */
+ibm_lbm_handle* ibm_lbm_batch_member(ibm_lbm_batch* b, int32_t i);
+
+/* Kernels the batch has launched so far. */
+int64_t ibm_lbm_batch_launch_count(const ibm_lbm_batch* b);
+
+/* Destroy the batch and its member handles (never fails). */
+void ibm_lbm_batch_destroy(ibm_lbm_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

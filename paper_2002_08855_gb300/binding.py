@@ -107,6 +107,14 @@ SIGNATURES = {
     "ibm_lbm_pair_search_static": (C.c_int, [C.c_int32, _ip, _ip, C.c_double, C.c_double,
                                              C.c_int32, _vp, C.c_int32, _vp, C.c_int64, _i64p,
                                              _vp]),
+    "ibm_lbm_batch_workspace_size": (C.c_int, [C.POINTER(Config), C.c_int32, C.POINTER(C.c_size_t)]),
+    "ibm_lbm_batch_init": (C.c_int, [C.POINTER(Config), C.c_int32, _vp, C.c_size_t, _vp,
+                                     C.POINTER(_dp), C.POINTER(_vp)]),
+    "ibm_lbm_batch_step": (C.c_int, [_vp, C.c_int32]),
+    "ibm_lbm_batch_sync": (C.c_int, [_vp]),
+    "ibm_lbm_batch_member": (_vp, [_vp, C.c_int32]),
+    "ibm_lbm_batch_launch_count": (C.c_int64, [_vp]),
+    "ibm_lbm_batch_destroy": (None, [_vp]),
 }
 
 
@@ -278,6 +286,86 @@ class Simulation:
         if getattr(self, "h", None) and self.h.value:
             self.stream.synchronize()
             lib().ibm_lbm_destroy(self.h)
+            self.h = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchMember(Simulation):
+    """One member of a Batch: the field and particle calls of a run (stepping is the
+    batch's)."""
+
+    def __init__(self, batch, i, w):
+        self.torch = batch.torch
+        self.cfg = make_config(w)
+        self.dim = self.cfg.dim
+        self.q = 9 if self.dim == 2 else 19
+        self.N = self.cfg.nx * self.cfg.ny * self.cfg.nz
+        self.np = self.cfg.n_particles
+        self.nl = self.cfg.n_lag
+        self.device = batch.device
+        self.stream = batch.stream
+        ptr = lib().ibm_lbm_batch_member(batch.h, int(i))
+        if not ptr:
+            raise IbmLbmError(-1, "batch_member", lib().ibm_lbm_last_error().decode())
+        self.h = C.c_void_p(ptr)
+
+    def step(self, n: int = 1):
+        raise RuntimeError("batch members step with their batch")
+
+    def close(self):
+        self.h = C.c_void_p(None)  # owned by the batch
+
+
+class Batch:
+    """Many independent 2D cavities stepped together (fused launches, one CUDA graph
+    per step parity).  members[i] gives the field and particle calls of member i."""
+
+    def __init__(self, workloads, centres, device: str = "cuda", stream=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        n = len(workloads)
+        cfgs = (Config * n)(*[make_config(w) for w in workloads])
+        size = C.c_size_t(0)
+        _check(lib().ibm_lbm_batch_workspace_size(cfgs, n, C.byref(size)), "batch_workspace_size")
+        self.workspace = torch.empty(size.value, dtype=torch.uint8, device=self.device)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        self._xc = []
+        ptrs = (_dp * n)()
+        for i, (w, X) in enumerate(zip(workloads, centres)):
+            if w.n_particles > 0:
+                xc = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(w.n_particles, 2))
+                self._xc.append(xc)
+                ptrs[i] = _ptr(xc, C.c_double)
+        self.h = C.c_void_p(None)
+        _check(lib().ibm_lbm_batch_init(cfgs, n, C.c_void_p(self.workspace.data_ptr()), size.value,
+                                        C.c_void_p(self.stream.cuda_stream), ptrs, C.byref(self.h)),
+               "batch_init")
+        self.members = [BatchMember(self, i, w) for i, w in enumerate(workloads)]
+        self.n_grid = sum(w.n_grid for w in workloads)
+
+    def step(self, n: int = 1):
+        _check(lib().ibm_lbm_batch_step(self.h, int(n)), "batch_step")
+
+    def sync(self):
+        _check(lib().ibm_lbm_batch_sync(self.h), "batch_sync")
+
+    def launch_count(self) -> int:
+        return int(lib().ibm_lbm_batch_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.stream.synchronize()
+            for m in self.members:
+                m.close()
+            lib().ibm_lbm_batch_destroy(self.h)
             self.h = C.c_void_p(None)
 
     def __del__(self):

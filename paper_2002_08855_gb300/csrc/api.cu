@@ -7,6 +7,7 @@
 //   -> regen (points and node marks of the next step)
 // All of it is enqueued on the caller's stream; after the first step each step
 // parity is captured once as a CUDA graph and replayed.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -974,6 +975,362 @@ int ibm_lbm_pair_search(int32_t dim, const int32_t* n_nodes, const int32_t* peri
   if (st & ST_CAPACITY) return fail(IBMLBM_ERR_CAPACITY, "a particle has more than max_neighbors partners");
   if (total > cap) return fail(IBMLBM_ERR_CAPACITY, "more pairs than cap");
   return IBMLBM_OK;
+}
+
+}  // extern "C"
+
+// ============================================================= batched ensemble
+// Many independent 2D cavities stepped together (the ensemble of SURVEY-style config
+// 5): every member is an ordinary run in its own slice of one workspace, and every
+// kernel of a step runs once for all members (fused launches, see Fuse).
+namespace {
+
+struct BatchPlan {
+  std::vector<size_t> off;        // member workspace offsets
+  std::vector<size_t> size;       // member workspace sizes
+  size_t tables = 0, total = 0;   // offset of the device tables, total bytes
+};
+
+// the launch types of a batched step, in the order of their block maps
+enum { BK_LBM, BK_EDGE, BK_WARP, BK_LANE, BK_PCLEAR, BK_PINS, BK_PSEARCH, BK_PFORCE, BK_COUNT };
+
+unsigned member_blocks(int type, const Derived& d, const ibm_lbm_config& c) {
+  const int np = c.n_particles;
+  switch (type) {
+    case BK_LBM: return lbm_step_blocks(d.g, c.pdf_storage);
+    case BK_EDGE: return lbm_edge_blocks(d.g, 2);
+    case BK_WARP: return np > 0 ? ibm_warp_blocks(np) : 0;
+    case BK_LANE: return np > 0 ? ibm_lane_blocks(np) : 0;
+    case BK_PCLEAR: {
+      if (np == 0) return 0;
+      PairArgs a{};
+      for (int k = 0; k < 3; ++k) a.nc[k] = d.nc[k];
+      return pair_clear_blocks(a);
+    }
+    case BK_PINS: return pair_thread_blocks(np, 256);
+    case BK_PSEARCH: return pair_warp_blocks(np);
+    default: return pair_thread_blocks(np, 128);
+  }
+}
+
+int check_batch(const ibm_lbm_config* cfgs, int32_t n) {
+  if (!cfgs || n <= 0) return fail(IBMLBM_ERR_INVALID_ARG, "a batch needs n > 0 configurations");
+  for (int32_t i = 0; i < n; ++i) {
+    int rc = check_config(&cfgs[i]);
+    if (rc) return rc;
+    if (cfgs[i].dim != 2) return fail(IBMLBM_ERR_UNSUPPORTED, "batch members must be 2D");
+    if (cfgs[i].pdf_storage == IBMLBM_PDF_BF16)
+      return fail(IBMLBM_ERR_UNSUPPORTED, "batch members store PDFs as FP32 or FP16");
+    if (cfgs[i].pdf_storage != cfgs[0].pdf_storage || cfgs[i].mdf_iters != cfgs[0].mdf_iters)
+      return fail(IBMLBM_ERR_INVALID_ARG, "batch members must share pdf_storage and mdf_iters");
+  }
+  return IBMLBM_OK;
+}
+
+size_t batch_table_bytes(const ibm_lbm_config* cfgs, int32_t n) {
+  size_t blocks = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    const Derived d = derive(&cfgs[i]);
+    for (int t = 0; t < BK_COUNT; ++t) blocks += member_blocks(t, d, cfgs[i]);
+  }
+  // args: Lbm x2, Ibm x2, Regen x2, Pair x4 per member; maps: first[] per type, cav[] per block
+  const size_t args = (size_t)n * (2 * sizeof(LbmArgs) + 2 * sizeof(IbmArgs) + 2 * sizeof(RegenArgs) +
+                                   4 * sizeof(PairArgs));
+  return args + sizeof(int) * (blocks + (size_t)BK_COUNT * n) + 4096;
+}
+
+BatchPlan plan_batch(const ibm_lbm_config* cfgs, int32_t n) {
+  BatchPlan p;
+  Carver cv;
+  for (int32_t i = 0; i < n; ++i) {
+    const size_t b = carve(&cfgs[i], derive(&cfgs[i])).total;
+    p.size.push_back(b);
+    p.off.push_back(cv.take(b));
+  }
+  p.tables = cv.take(batch_table_bytes(cfgs, n));
+  p.total = cv.off;
+  return p;
+}
+
+}  // namespace
+
+struct ibm_lbm_batch {
+  int n;
+  std::vector<ibm_lbm_handle*> m;
+  cudaStream_t s;
+  cudaStream_t side;
+  cudaEvent_t fork, join;
+  int store, mdf;
+  size_t smem;                   // 2D IBM shared memory for the largest box
+  unsigned blocks[BK_COUNT];
+  // device tables
+  LbmArgs* lbm_args[2];
+  IbmArgs* ibm_args[2];
+  RegenArgs* regen_args[2];      // [p]: regeneration into parity p
+  PairArgs* pair_args[2][2];     // [parity][have_prev]
+  int* first[BK_COUNT];
+  int* cav[BK_COUNT];
+  long long step;
+  int have_prev;
+  int64_t launches;
+  bool graph_ok[2], graph_tried[2];
+  cudaGraphExec_t graph[2];
+  int graph_kernels[2];
+};
+
+namespace {
+
+Fuse fuse(const ibm_lbm_batch* b, int type, const void* args) { return Fuse{args, b->cav[type], b->first[type]}; }
+
+int enqueue_batch_step(ibm_lbm_batch* b, int parity, int have_prev, int* nk) {
+  const cudaStream_t s = b->s;
+  int k = 0;
+  const unsigned* B = b->blocks;
+  const void* ia = b->ibm_args[parity];
+  if (B[BK_WARP]) {
+    if (b->mdf == 0) {
+      CUDA_TRY(launch_ibm_interp_fused(fuse(b, BK_WARP, ia), B[BK_WARP], b->smem, 0, parity, b->store, s));
+      ++k;
+    }
+    for (int m = 1; m <= b->mdf; ++m) {
+      CUDA_TRY(launch_ibm_interp_fused(fuse(b, BK_WARP, ia), B[BK_WARP], b->smem, m, parity, b->store, s));
+      CUDA_TRY(launch_ibm_spread_fused(fuse(b, BK_WARP, ia), B[BK_WARP], b->smem, s));
+      k += 2;
+    }
+    CUDA_TRY(launch_ibm_forces_fused(fuse(b, BK_LANE, ia), B[BK_LANE], s));
+    ++k;
+    // contacts, particle update and regeneration beside the collision (as in a single run)
+    CUDA_TRY(cudaEventRecord(b->fork, s));
+    CUDA_TRY(cudaStreamWaitEvent(b->side, b->fork, 0));
+    const void* pa = b->pair_args[parity][have_prev];
+    CUDA_TRY(launch_pairs_fused(fuse(b, BK_PCLEAR, pa), B[BK_PCLEAR], fuse(b, BK_PINS, pa), B[BK_PINS],
+                                fuse(b, BK_PSEARCH, pa), B[BK_PSEARCH], fuse(b, BK_PFORCE, pa),
+                                B[BK_PFORCE], b->side));
+    k += 4;
+    CUDA_TRY(launch_regen_fused(fuse(b, BK_LANE, b->regen_args[1 - parity]), B[BK_LANE], b->side));
+    ++k;
+    CUDA_TRY(cudaEventRecord(b->join, b->side));
+  }
+  const void* la = b->lbm_args[parity];
+  CUDA_TRY(launch_lbm_step_fused(fuse(b, BK_LBM, la), B[BK_LBM], fuse(b, BK_EDGE, la), B[BK_EDGE], b->store,
+                                 parity, s));
+  k += (parity == 1 && B[BK_EDGE]) ? 2 : 1;
+  if (B[BK_WARP]) CUDA_TRY(cudaStreamWaitEvent(s, b->join, 0));
+  *nk = k;
+  return IBMLBM_OK;
+}
+
+int capture_batch_graph(ibm_lbm_batch* b, int parity) {
+  cudaGraph_t graph = nullptr;
+  int nk = 0;
+  if (cudaStreamBeginCapture(b->s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return IBMLBM_ERR_CUDA;
+  }
+  const int rc = enqueue_batch_step(b, parity, 1, &nk);
+  const cudaError_t e = cudaStreamEndCapture(b->s, &graph);
+  if (rc != IBMLBM_OK || e != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return IBMLBM_ERR_CUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return IBMLBM_ERR_CUDA;
+  }
+  cudaGraphDestroy(graph);
+  b->graph[parity] = exec;
+  b->graph_kernels[parity] = nk;
+  b->graph_ok[parity] = true;
+  return IBMLBM_OK;
+}
+
+void destroy_batch(ibm_lbm_batch* b) {
+  for (ibm_lbm_handle* h : b->m) ibm_lbm_destroy(h);
+  for (int p = 0; p < 2; ++p)
+    if (b->graph_ok[p]) cudaGraphExecDestroy(b->graph[p]);
+  if (b->side) {
+    cudaStreamSynchronize(b->side);
+    cudaStreamDestroy(b->side);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ibm_lbm_batch_workspace_size(const ibm_lbm_config* cfgs, int32_t n, size_t* bytes) {
+  int rc = check_batch(cfgs, n);
+  if (rc) return rc;
+  if (!bytes) return fail(IBMLBM_ERR_INVALID_ARG, "bytes is NULL");
+  *bytes = plan_batch(cfgs, n).total;
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_batch_init(const ibm_lbm_config* cfgs, int32_t n, void* d_workspace, size_t bytes,
+                       void* stream, const double* const* h_centres, ibm_lbm_batch** out) {
+  int rc = check_batch(cfgs, n);
+  if (rc) return rc;
+  if (!out) return fail(IBMLBM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  const BatchPlan plan = plan_batch(cfgs, n);
+  if (!d_workspace || bytes < plan.total)
+    return fail(IBMLBM_ERR_WORKSPACE, "batch workspace missing or too small");
+  if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0)
+    return fail(IBMLBM_ERR_WORKSPACE, "batch workspace must be 256-byte aligned");
+  ibm_lbm_batch* b = new ibm_lbm_batch();
+  b->n = n;
+  b->s = static_cast<cudaStream_t>(stream);
+  b->side = nullptr;
+  b->fork = b->join = nullptr;
+  b->store = cfgs[0].pdf_storage;
+  b->mdf = cfgs[0].mdf_iters;
+  b->step = 0;
+  b->have_prev = 0;
+  b->launches = 0;
+  b->graph_ok[0] = b->graph_ok[1] = b->graph_tried[0] = b->graph_tried[1] = false;
+  char* ws = static_cast<char*>(d_workspace);
+  auto bail = [&](int code) {
+    const std::string msg = g_err;
+    destroy_batch(b);
+    g_err = msg;
+    return code;
+  };
+#define BATCH_TRY(expr)                                                                  \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return bail(fail(IBMLBM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_))); \
+  } while (0)
+  BATCH_TRY(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+  BATCH_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+  BATCH_TRY(cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming));
+  int maxbox = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    ibm_lbm_handle* h = nullptr;
+    rc = ibm_lbm_init(&cfgs[i], ws + plan.off[i], plan.size[i], stream,
+                      h_centres ? h_centres[i] : nullptr, &h);
+    if (rc) return bail(rc);
+    b->m.push_back(h);
+    if (cfgs[i].n_particles > 0) maxbox = std::max(maxbox, h->d.box);
+  }
+  b->smem = maxbox ? ibm_box2_smem(maxbox) : 0;
+  if (maxbox && b->smem > 227 * 1024) return bail(fail(IBMLBM_ERR_UNSUPPORTED, "particle too large"));
+  if (maxbox) BATCH_TRY(prepare_ibm_spread(2, b->smem));
+  // host copies of the tables, then one copy to the device
+  std::vector<char> host(batch_table_bytes(cfgs, n), 0);
+  size_t o = 0;
+  auto put = [&](const void* src, size_t len) {
+    const size_t at_ = o;
+    std::memcpy(host.data() + o, src, len);
+    o = (o + len + 15) / 16 * 16;
+    return at_;
+  };
+  size_t o_lbm[2], o_ibm[2], o_regen[2], o_pair[2][2], o_first[BK_COUNT], o_cav[BK_COUNT];
+  for (int p = 0; p < 2; ++p) {
+    std::vector<LbmArgs> la;
+    std::vector<IbmArgs> ia;
+    std::vector<RegenArgs> ra;
+    for (ibm_lbm_handle* h : b->m) {
+      la.push_back(h->lbm(p));
+      ia.push_back(h->ibm(p));
+      ra.push_back(h->regen(p));
+    }
+    o_lbm[p] = put(la.data(), sizeof(LbmArgs) * n);
+    o_ibm[p] = put(ia.data(), sizeof(IbmArgs) * n);
+    o_regen[p] = put(ra.data(), sizeof(RegenArgs) * n);
+    for (int hp = 0; hp < 2; ++hp) {
+      std::vector<PairArgs> pa;
+      for (ibm_lbm_handle* h : b->m) pa.push_back(h->pairs(p, hp));
+      o_pair[p][hp] = put(pa.data(), sizeof(PairArgs) * n);
+    }
+  }
+  for (int t = 0; t < BK_COUNT; ++t) {
+    std::vector<int> first(n), cav;
+    for (int32_t i = 0; i < n; ++i) {
+      first[i] = (int)cav.size();
+      const unsigned c = member_blocks(t, b->m[i]->d, cfgs[i]);
+      cav.insert(cav.end(), c, i);
+    }
+    b->blocks[t] = (unsigned)cav.size();
+    o_first[t] = put(first.data(), sizeof(int) * n);
+    o_cav[t] = cav.empty() ? o : put(cav.data(), sizeof(int) * cav.size());
+  }
+  if (o > host.size()) return bail(fail(IBMLBM_ERR_WORKSPACE, "batch tables overflow"));
+  char* dt = ws + plan.tables;
+  BATCH_TRY(cudaMemcpyAsync(dt, host.data(), o, cudaMemcpyHostToDevice, b->s));
+  BATCH_TRY(cudaStreamSynchronize(b->s));
+  for (int p = 0; p < 2; ++p) {
+    b->lbm_args[p] = reinterpret_cast<LbmArgs*>(dt + o_lbm[p]);
+    b->ibm_args[p] = reinterpret_cast<IbmArgs*>(dt + o_ibm[p]);
+    b->regen_args[p] = reinterpret_cast<RegenArgs*>(dt + o_regen[p]);
+    for (int hp = 0; hp < 2; ++hp) b->pair_args[p][hp] = reinterpret_cast<PairArgs*>(dt + o_pair[p][hp]);
+  }
+  for (int t = 0; t < BK_COUNT; ++t) {
+    b->first[t] = reinterpret_cast<int*>(dt + o_first[t]);
+    b->cav[t] = reinterpret_cast<int*>(dt + o_cav[t]);
+  }
+#undef BATCH_TRY
+  *out = b;
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_batch_step(ibm_lbm_batch* b, int32_t n_steps) {
+  if (!b) return fail(IBMLBM_ERR_INVALID_ARG, "batch is NULL");
+  if (n_steps < 0) return fail(IBMLBM_ERR_INVALID_ARG, "n_steps < 0");
+  for (int32_t t = 0; t < n_steps; ++t) {
+    const int parity = (int)(b->step & 1);
+    if (b->have_prev && !b->graph_tried[parity]) {
+      b->graph_tried[parity] = true;
+      capture_batch_graph(b, parity);  // on failure the steps run as eager launches
+    }
+    if (b->have_prev && b->graph_ok[parity]) {
+      CUDA_TRY(cudaGraphLaunch(b->graph[parity], b->s));
+      b->launches += b->graph_kernels[parity];
+    } else {
+      int nk = 0;
+      const int rc = enqueue_batch_step(b, parity, b->have_prev, &nk);
+      if (rc) return rc;
+      b->launches += nk;
+    }
+    b->step += 1;
+    b->have_prev = 1;
+    for (ibm_lbm_handle* h : b->m) {  // the members' own clocks (their I/O reads by parity)
+      h->step += 1;
+      h->have_prev = 1;
+    }
+  }
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_batch_sync(ibm_lbm_batch* b) {
+  if (!b) return fail(IBMLBM_ERR_INVALID_ARG, "batch is NULL");
+  CUDA_TRY(cudaStreamSynchronize(b->s));
+  int first_rc = IBMLBM_OK;
+  for (ibm_lbm_handle* h : b->m) {
+    const int rc = ibm_lbm_sync(h);
+    if (rc && !first_rc) first_rc = rc;
+  }
+  return first_rc;
+}
+
+ibm_lbm_handle* ibm_lbm_batch_member(ibm_lbm_batch* b, int32_t i) {
+  if (!b || i < 0 || i >= b->n) {
+    fail(IBMLBM_ERR_INVALID_ARG, "no such batch member");
+    return nullptr;
+  }
+  return b->m[i];
+}
+
+int64_t ibm_lbm_batch_launch_count(const ibm_lbm_batch* b) { return b ? b->launches : 0; }
+
+void ibm_lbm_batch_destroy(ibm_lbm_batch* b) {
+  if (b) destroy_batch(b);
 }
 
 }  // extern "C"

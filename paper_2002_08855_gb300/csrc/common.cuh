@@ -223,6 +223,24 @@ struct PartState {
   int fixed;
 };
 
+// ------------------------------------------------------------ fused launches
+// A batch steps many independent runs (its members) together, and each kernel then
+// runs once for all members: block b of the launch belongs to member cav[b] and is
+// block b - first[cav[b]] of that member's own grid.  args holds the members'
+// argument structs (in device memory).
+struct Fuse {
+  const void* args;   // [members]
+  const int* cav;     // [blocks]
+  const int* first;   // [members]
+};
+
+// In a kernel templated on bool FUSED: A = this block's argument struct (the kernel
+// parameter A0 for a single run), BLK = the block's index in its member's grid.
+#define IBMLBM_BIND(FUSED, TYPE, A, A0, F, BLK)                                        \
+  const int bind_m_ = (FUSED) ? (F).cav[blockIdx.x] : 0;                             \
+  const TYPE& A = (FUSED) ? static_cast<const TYPE*>((F).args)[bind_m_] : (A0);      \
+  const unsigned BLK = (FUSED) ? blockIdx.x - (unsigned)(F).first[bind_m_] : blockIdx.x
+
 // Capacity of one search-cell bucket: eight times the mean occupancy plus eight
 // (at least 16); a bucket that overflows is reported as CAPACITY.
 inline int cell_capacity(long long n, long long ncells) {

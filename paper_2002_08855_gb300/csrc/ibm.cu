@@ -108,11 +108,12 @@ __device__ __forceinline__ bool box_node(const Geo& g, int ox, int oy, int r, in
 //   MODE 1 (m >= 2): the box buffer plus f_IB/2.
 // Lane k then interpolates point k from shared memory.  Box nodes beyond a wall hold
 // zero, which drops them from the sum.
-template <int SC, int PARITY, int MODE, int ST>
-__global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A, int m) {
+template <int SC, int PARITY, int MODE, int ST, bool FUSED>
+__global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A0, int m, Fuse FU) {
+  IBMLBM_BIND(FUSED, IbmArgs, A, A0, FU, blk);
   extern __shared__ __align__(16) float smem_i[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int i = blockIdx.x * kIbmWarps + wib;
+  const int i = (int)blk * kIbmWarps + wib;
   if (i >= A.np) return;  // whole warp
   const int S = SC ? SC : A.box, P = box_pitch(S), cells = S * P;
   float2* box = reinterpret_cast<float2*>(smem_i + (size_t)wib * interp2_warp_floats(MODE, S));
@@ -237,11 +238,12 @@ __global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A, 
 // node (anchors at most 3 apart on both axes) the halves take turns.  So no two lanes
 // of an instruction touch one cell and plain read-add-write is exact.  Finally the warp
 // adds the non-zero box cells to f_IB with one global vector atomic per cell.
-template <int SC>
-__global__ void __launch_bounds__(kIbmWarps * 32) ibm_spread2_kernel(IbmArgs A) {
+template <int SC, bool FUSED>
+__global__ void __launch_bounds__(kIbmWarps * 32) ibm_spread2_kernel(IbmArgs A0, Fuse FU) {
+  IBMLBM_BIND(FUSED, IbmArgs, A, A0, FU, blk);
   extern __shared__ __align__(16) float smem2[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int i = blockIdx.x * kIbmWarps + wib;
+  const int i = (int)blk * kIbmWarps + wib;
   if (i >= A.np) return;  // whole warp
   const int S = SC ? SC : A.box, P = box_pitch(S), cells = S * P;
   float* base = smem2 + (size_t)wib * spread2_warp_floats(S);
@@ -698,9 +700,10 @@ __global__ void __launch_bounds__(256) ibm_forces_kernel(IbmArgs A) {
 // its candidate nodes kForceBatch at a time, so their loads are in flight together.
 constexpr int kForceBatch = 6;
 
-template <int SC>
-__global__ void __launch_bounds__(256) ibm_forces2_kernel(IbmArgs A) {
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+template <int SC, bool FUSED>
+__global__ void __launch_bounds__(256) ibm_forces2_kernel(IbmArgs A0, Fuse FU) {
+  IBMLBM_BIND(FUSED, IbmArgs, A, A0, FU, blk);
+  const int i = (int)((blk * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= A.np) return;
   const int S = SC ? SC : A.box, W = box_pitch(S), cells = S * W, ext = S - 4;  // ext = 2 rcell + 2
@@ -764,9 +767,10 @@ __global__ void __launch_bounds__(256) ibm_forces2_kernel(IbmArgs A) {
 // and (3D) mark the nodes within mark_radius of the centre in the next step's node mask.
 // init != 0 first refreshes the fixed-point centre and the single-precision
 // velocities from the double-precision state (initial state, new particle state).
-template <int D>
-__global__ void __launch_bounds__(256) regen_kernel(RegenArgs A, int init) {
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+template <int D, bool FUSED>
+__global__ void __launch_bounds__(256) regen_kernel(RegenArgs A0, int init, Fuse FU) {
+  IBMLBM_BIND(FUSED, RegenArgs, A, A0, FU, blk);
+  const int i = (int)((blk * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= A.np) return;
   const long long pi = i;
@@ -857,9 +861,9 @@ cudaError_t launch_ibm_interp(const IbmArgs& A, int m, cudaStream_t s) {
     const size_t sm = sizeof(float) * kIbmWarps * (size_t)interp2_warp_floats(mode, A.box);
 #define IBMLBM_INTERP2_ST(SC, P)                                                             \
   do {                                                                                        \
-    if (A.store == STORE_F32) ibm_interp2_kernel<SC, P, 0, STORE_F32><<<grid, kIbmWarps * 32, sm, s>>>(A, m); \
-    else if (A.store == STORE_F16) ibm_interp2_kernel<SC, P, 0, STORE_F16><<<grid, kIbmWarps * 32, sm, s>>>(A, m); \
-    else ibm_interp2_kernel<SC, P, 0, STORE_BF16><<<grid, kIbmWarps * 32, sm, s>>>(A, m);      \
+    if (A.store == STORE_F32) ibm_interp2_kernel<SC, P, 0, STORE_F32, false><<<grid, kIbmWarps * 32, sm, s>>>(A, m, Fuse{}); \
+    else if (A.store == STORE_F16) ibm_interp2_kernel<SC, P, 0, STORE_F16, false><<<grid, kIbmWarps * 32, sm, s>>>(A, m, Fuse{}); \
+    else ibm_interp2_kernel<SC, P, 0, STORE_BF16, false><<<grid, kIbmWarps * 32, sm, s>>>(A, m, Fuse{});      \
   } while (0)
 #define IBMLBM_INTERP2(SC)                                                                   \
   do {                                                                                        \
@@ -867,7 +871,7 @@ cudaError_t launch_ibm_interp(const IbmArgs& A, int m, cudaStream_t s) {
       if (A.parity == 0) IBMLBM_INTERP2_ST(SC, 0);                                            \
       else IBMLBM_INTERP2_ST(SC, 1);                                                          \
     } else {                                                                                  \
-      ibm_interp2_kernel<SC, 0, 1, STORE_F32><<<grid, kIbmWarps * 32, sm, s>>>(A, m);         \
+      ibm_interp2_kernel<SC, 0, 1, STORE_F32, false><<<grid, kIbmWarps * 32, sm, s>>>(A, m, Fuse{});         \
     }                                                                                         \
   } while (0)
     if (A.box == 16) IBMLBM_INTERP2(16);
@@ -897,14 +901,21 @@ cudaError_t prepare_ibm_spread(int D, size_t smem) {
   if (smem <= g) return cudaSuccess;
   cudaError_t e;
   if (D == 2) {
-#define IBMLBM_I2(SC, P, ST) (const void*)ibm_interp2_kernel<SC, P, 0, ST>
+#define IBMLBM_I2(SC, P, ST) (const void*)ibm_interp2_kernel<SC, P, 0, ST, false>
 #define IBMLBM_I2S(SC)                                                                     \
   IBMLBM_I2(SC, 0, STORE_F32), IBMLBM_I2(SC, 1, STORE_F32), IBMLBM_I2(SC, 0, STORE_F16),    \
       IBMLBM_I2(SC, 1, STORE_F16), IBMLBM_I2(SC, 0, STORE_BF16), IBMLBM_I2(SC, 1, STORE_BF16), \
-      (const void*)ibm_interp2_kernel<SC, 0, 1, STORE_F32>
-    const void* fns[] = {(const void*)ibm_spread2_kernel<16>, (const void*)ibm_spread2_kernel<22>,
-                         (const void*)ibm_spread2_kernel<0>, IBMLBM_I2S(16), IBMLBM_I2S(22),
-                         IBMLBM_I2S(0)};
+      (const void*)ibm_interp2_kernel<SC, 0, 1, STORE_F32, false>
+    const void* fns[] = {(const void*)ibm_spread2_kernel<16, false>, (const void*)ibm_spread2_kernel<22, false>,
+                         (const void*)ibm_spread2_kernel<0, false>, IBMLBM_I2S(16), IBMLBM_I2S(22),
+                         IBMLBM_I2S(0),
+                         // fused over the members of a batch (runtime box size)
+                         (const void*)ibm_spread2_kernel<0, true>,
+                         (const void*)ibm_interp2_kernel<0, 0, 0, STORE_F32, true>,
+                         (const void*)ibm_interp2_kernel<0, 1, 0, STORE_F32, true>,
+                         (const void*)ibm_interp2_kernel<0, 0, 0, STORE_F16, true>,
+                         (const void*)ibm_interp2_kernel<0, 1, 0, STORE_F16, true>,
+                         (const void*)ibm_interp2_kernel<0, 0, 1, STORE_F32, true>};
 #undef IBMLBM_I2S
 #undef IBMLBM_I2
     e = cudaSuccess;
@@ -930,11 +941,11 @@ cudaError_t launch_ibm_spread(const IbmArgs& A, cudaStream_t s) {
     const unsigned grid = (unsigned)((A.np + kIbmWarps - 1) / kIbmWarps);
     const size_t sm = sizeof(float) * kIbmWarps * (size_t)spread2_warp_floats(A.box);
     if (A.box == 16)
-      ibm_spread2_kernel<16><<<grid, kIbmWarps * 32, sm, s>>>(A);
+      ibm_spread2_kernel<16, false><<<grid, kIbmWarps * 32, sm, s>>>(A, Fuse{});
     else if (A.box == 22)
-      ibm_spread2_kernel<22><<<grid, kIbmWarps * 32, sm, s>>>(A);
+      ibm_spread2_kernel<22, false><<<grid, kIbmWarps * 32, sm, s>>>(A, Fuse{});
     else
-      ibm_spread2_kernel<0><<<grid, kIbmWarps * 32, sm, s>>>(A);
+      ibm_spread2_kernel<0, false><<<grid, kIbmWarps * 32, sm, s>>>(A, Fuse{});
   }  // 3D spreads inside launch_ibm_interp
   return cudaGetLastError();
 }
@@ -944,11 +955,11 @@ cudaError_t launch_ibm_forces(const IbmArgs& A, cudaStream_t s) {
   const unsigned grid = (unsigned)(((long long)A.np * 32 + 255) / 256);
   if (A.D == 2) {
     if (A.box == 16)
-      ibm_forces2_kernel<16><<<grid, 256, 0, s>>>(A);
+      ibm_forces2_kernel<16, false><<<grid, 256, 0, s>>>(A, Fuse{});
     else if (A.box == 22)
-      ibm_forces2_kernel<22><<<grid, 256, 0, s>>>(A);
+      ibm_forces2_kernel<22, false><<<grid, 256, 0, s>>>(A, Fuse{});
     else
-      ibm_forces2_kernel<0><<<grid, 256, 0, s>>>(A);
+      ibm_forces2_kernel<0, false><<<grid, 256, 0, s>>>(A, Fuse{});
   } else {
     ibm_forces_kernel<3><<<grid, 256, 0, s>>>(A);
   }
@@ -959,9 +970,46 @@ cudaError_t launch_regen(const RegenArgs& A, int init, cudaStream_t s) {
   if (A.np == 0) return cudaSuccess;
   const unsigned grid = (unsigned)(((long long)A.np * 32 + 255) / 256);
   if (A.D == 2)
-    regen_kernel<2><<<grid, 256, 0, s>>>(A, init);
+    regen_kernel<2, false><<<grid, 256, 0, s>>>(A, init, Fuse{});
   else
-    regen_kernel<3><<<grid, 256, 0, s>>>(A, init);
+    regen_kernel<3, false><<<grid, 256, 0, s>>>(A, init, Fuse{});
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------- fused over the members of a 2D batch
+// blocks of each 2D IBM kernel for one run of np particles
+unsigned ibm_warp_blocks(int np) { return (unsigned)((np + kIbmWarps - 1) / kIbmWarps); }
+unsigned ibm_lane_blocks(int np) { return (unsigned)(((long long)np * 32 + 255) / 256); }
+
+cudaError_t launch_ibm_interp_fused(const Fuse& F, unsigned blocks, size_t smem, int m, int parity,
+                                    int store, cudaStream_t s) {
+  const IbmArgs none{};
+  if (m <= 1) {
+    if (store == STORE_F32) {
+      if (parity == 0) ibm_interp2_kernel<0, 0, 0, STORE_F32, true><<<blocks, kIbmWarps * 32, smem, s>>>(none, m, F);
+      else ibm_interp2_kernel<0, 1, 0, STORE_F32, true><<<blocks, kIbmWarps * 32, smem, s>>>(none, m, F);
+    } else {
+      if (parity == 0) ibm_interp2_kernel<0, 0, 0, STORE_F16, true><<<blocks, kIbmWarps * 32, smem, s>>>(none, m, F);
+      else ibm_interp2_kernel<0, 1, 0, STORE_F16, true><<<blocks, kIbmWarps * 32, smem, s>>>(none, m, F);
+    }
+  } else {
+    ibm_interp2_kernel<0, 0, 1, STORE_F32, true><<<blocks, kIbmWarps * 32, smem, s>>>(none, m, F);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ibm_spread_fused(const Fuse& F, unsigned blocks, size_t smem, cudaStream_t s) {
+  ibm_spread2_kernel<0, true><<<blocks, kIbmWarps * 32, smem, s>>>(IbmArgs{}, F);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ibm_forces_fused(const Fuse& F, unsigned blocks, cudaStream_t s) {
+  ibm_forces2_kernel<0, true><<<blocks, 256, 0, s>>>(IbmArgs{}, F);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_regen_fused(const Fuse& F, unsigned blocks, cudaStream_t s) {
+  regen_kernel<2, true><<<blocks, 256, 0, s>>>(RegenArgs{}, 0, F);
   return cudaGetLastError();
 }
 

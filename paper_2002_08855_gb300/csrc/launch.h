@@ -32,6 +32,27 @@ cudaError_t launch_pair_contacts(const PairArgs& A, cudaStream_t s);
 cudaError_t launch_pair_compact(const PairArgs& A, int* pairs, long long cap, cudaStream_t s);
 cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t s);
 
+// fused launches over the members of a 2D batch (block counts per member, then the
+// launches; see Fuse in common.cuh)
+unsigned lbm_step_blocks(const Geo& g, int store);
+unsigned lbm_edge_blocks(const Geo& g, int D);
+cudaError_t launch_lbm_step_fused(const Fuse& F, unsigned blocks, const Fuse& FE, unsigned eblocks,
+                                  int store, int parity, cudaStream_t s);
+size_t ibm_box2_smem(int box);
+unsigned ibm_warp_blocks(int np);
+unsigned ibm_lane_blocks(int np);
+cudaError_t launch_ibm_interp_fused(const Fuse& F, unsigned blocks, size_t smem, int m, int parity,
+                                    int store, cudaStream_t s);
+cudaError_t launch_ibm_spread_fused(const Fuse& F, unsigned blocks, size_t smem, cudaStream_t s);
+cudaError_t launch_ibm_forces_fused(const Fuse& F, unsigned blocks, cudaStream_t s);
+cudaError_t launch_regen_fused(const Fuse& F, unsigned blocks, cudaStream_t s);
+unsigned pair_clear_blocks(const PairArgs& A);
+unsigned pair_thread_blocks(int n, int b);
+unsigned pair_warp_blocks(int n);
+cudaError_t launch_pairs_fused(const Fuse& Fc, unsigned bc, const Fuse& Fi, unsigned bi,
+                               const Fuse& Fs, unsigned bs, const Fuse& Ff, unsigned bf,
+                               cudaStream_t s);
+
 // sets the calling thread's text for ibm_lbm_last_error()
 void set_last_error(const std::string& msg);
 

@@ -193,10 +193,12 @@ __device__ __forceinline__ bool odd_edge_row(const Geo& g, int y, int z) {
 // of a row) are left to lbm_step_edge_kernel, so every node here uses fixed neighbour
 // offsets; the AA pattern makes the nodes independent of each other.  The even step
 // is local everywhere.
-template <class L, int PARITY, int ST, int K>
-__global__ void __launch_bounds__(kLbmBlock) lbm_step_kernel(LbmArgs A, int spr) {
+template <class L, int PARITY, int ST, int K, bool FUSED>
+__global__ void __launch_bounds__(kLbmBlock) lbm_step_kernel(LbmArgs A0, int spr0, Fuse FU) {
+  IBMLBM_BIND(FUSED, LbmArgs, A, A0, FU, blk);
   const Geo& g = A.g;
-  const unsigned b = blockIdx.x, uspr = (unsigned)spr, uny = (unsigned)g.ny;
+  const int spr = FUSED ? (g.nx + K * kLbmBlock - 1) / (K * kLbmBlock) : spr0;
+  const unsigned b = blk, uspr = (unsigned)spr, uny = (unsigned)g.ny;
   const unsigned row = b / uspr, seg = b - row * uspr;
   const unsigned uz = row / uny;
   const int y = (int)(row - uz * uny), z = (int)uz;
@@ -229,11 +231,27 @@ __global__ void __launch_bounds__(kLbmBlock) lbm_step_kernel(LbmArgs A, int spr)
 
 // The odd-step nodes lbm_step_kernel leaves: every node of the face rows, then the
 // two end nodes of every other row, one thread per node, general addressing.
-template <class L, int ST>
-__global__ void __launch_bounds__(kLbmBlock) lbm_step_edge_kernel(LbmArgs A, long long nface,
-                                                                 long long nends) {
+// face rows and inner-row end nodes of an odd step (lbm_step_edge_kernel's index space)
+__host__ __device__ inline void edge_counts(const Geo& g, int dim, long long& nface, long long& nends) {
+  long long inner;
+  if (dim == 2) {
+    nface = g.ny > 1 ? 2 : 1;
+    inner = g.ny > 2 ? g.ny - 2 : 0;
+  } else {
+    nface = (long long)g.ny * (g.nz > 1 ? 2 : 1) + (long long)(g.nz > 2 ? g.nz - 2 : 0) * (g.ny > 1 ? 2 : 1);
+    inner = (long long)(g.ny > 2 ? g.ny - 2 : 0) * (g.nz > 2 ? g.nz - 2 : 0);
+  }
+  nends = inner * (g.nx > 1 ? 2 : 1);
+}
+
+template <class L, int ST, bool FUSED>
+__global__ void __launch_bounds__(kLbmBlock) lbm_step_edge_kernel(LbmArgs A0, long long nface0,
+                                                                 long long nends0, Fuse FU) {
+  IBMLBM_BIND(FUSED, LbmArgs, A, A0, FU, blk);
   const Geo& g = A.g;
-  const long long t = blockIdx.x * (long long)kLbmBlock + threadIdx.x;
+  long long nface = nface0, nends = nends0;
+  if (FUSED) edge_counts(g, L::dim, nface, nends);
+  const long long t = blk * (long long)kLbmBlock + threadIdx.x;
   int x, y, z;
   if (t < nface * g.nx) {  // face rows
     const long long k = t / g.nx;
@@ -389,31 +407,54 @@ static dim3 lbm_grid(const Geo& g, int& cpr) {
 #define IBMLBM_DISPATCH(D, PARITY, KERNEL, ...) \
   IBMLBM_DISPATCH_G(D, PARITY, KERNEL, grid, kLbmBlock, __VA_ARGS__)
 
-template <class L, int PARITY, int ST>
-static void launch_step_main(const LbmArgs& A, cudaStream_t s) {
-  constexpr int K = ST == STORE_F32 ? 1 : 2;
-  const int spr = (A.g.nx + K * kLbmBlock - 1) / (K * kLbmBlock);
-  const dim3 grid((unsigned)((long long)spr * A.g.rows));
-  lbm_step_kernel<L, PARITY, ST, K><<<grid, kLbmBlock, 0, s>>>(A, spr);
+template <int ST>
+constexpr int step_k() { return ST == STORE_F32 ? 1 : 2; }
+
+// blocks of lbm_step_kernel (2D) and of the odd-step edge kernel for one run
+unsigned lbm_step_blocks(const Geo& g, int store) {
+  const int K = store == STORE_F32 ? 1 : 2;
+  return (unsigned)((long long)((g.nx + K * kLbmBlock - 1) / (K * kLbmBlock)) * g.rows);
+}
+unsigned lbm_edge_blocks(const Geo& g, int D) {
+  long long nface, nends;
+  edge_counts(g, D, nface, nends);
+  return (unsigned)((nface * g.nx + nends + kLbmBlock - 1) / kLbmBlock);
 }
 
-// odd-step face rows and inner-row ends (lbm_step_edge_kernel's index space)
+template <class L, int PARITY, int ST>
+static void launch_step_main(const LbmArgs& A, cudaStream_t s) {
+  constexpr int K = step_k<ST>();
+  const int spr = (A.g.nx + K * kLbmBlock - 1) / (K * kLbmBlock);
+  const dim3 grid((unsigned)((long long)spr * A.g.rows));
+  lbm_step_kernel<L, PARITY, ST, K, false><<<grid, kLbmBlock, 0, s>>>(A, spr, Fuse{});
+}
+
 template <class L, int ST>
 static void launch_step_edge(const LbmArgs& A, cudaStream_t s) {
-  const Geo& g = A.g;
-  long long nface, inner;
-  if (L::dim == 2) {
-    nface = g.ny > 1 ? 2 : 1;
-    inner = g.ny > 2 ? g.ny - 2 : 0;
-  } else {
-    nface = (long long)g.ny * (g.nz > 1 ? 2 : 1) + (long long)(g.nz > 2 ? g.nz - 2 : 0) * (g.ny > 1 ? 2 : 1);
-    inner = (long long)(g.ny > 2 ? g.ny - 2 : 0) * (g.nz > 2 ? g.nz - 2 : 0);
-  }
-  const long long nends = inner * (g.nx > 1 ? 2 : 1);
-  const long long total = nface * g.nx + nends;
+  long long nface, nends;
+  edge_counts(A.g, L::dim, nface, nends);
+  const long long total = nface * A.g.nx + nends;
   if (total == 0) return;
   const dim3 grid((unsigned)((total + kLbmBlock - 1) / kLbmBlock));
-  lbm_step_edge_kernel<L, ST><<<grid, kLbmBlock, 0, s>>>(A, nface, nends);
+  lbm_step_edge_kernel<L, ST, false><<<grid, kLbmBlock, 0, s>>>(A, nface, nends, Fuse{});
+}
+
+// fused over the members of a 2D batch (FP32 or FP16 storage, one for all members)
+cudaError_t launch_lbm_step_fused(const Fuse& F, unsigned blocks, const Fuse& FE, unsigned eblocks,
+                                  int store, int parity, cudaStream_t s) {
+  const LbmArgs none{};
+#define IBMLBM_STEPF(P, ST)                                                                        \
+  do {                                                                                               \
+    lbm_step_kernel<Lat<2>, P, ST, step_k<ST>(), true><<<blocks, kLbmBlock, 0, s>>>(none, 0, F);   \
+    if (P == 1 && eblocks) lbm_step_edge_kernel<Lat<2>, ST, true><<<eblocks, kLbmBlock, 0, s>>>(none, 0, 0, FE); \
+  } while (0)
+  if (store == STORE_F32) {
+    if (parity == 0) IBMLBM_STEPF(0, STORE_F32); else IBMLBM_STEPF(1, STORE_F32);
+  } else {
+    if (parity == 0) IBMLBM_STEPF(0, STORE_F16); else IBMLBM_STEPF(1, STORE_F16);
+  }
+#undef IBMLBM_STEPF
+  return cudaGetLastError();
 }
 
 // kernels launch_lbm_step launches: the main kernel, and in an odd step the edge kernel

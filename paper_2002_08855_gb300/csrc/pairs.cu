@@ -37,9 +37,10 @@ __device__ __forceinline__ int cell_of(const PairArgs& A, int i) {
   return c;
 }
 
-template <int D>
-__global__ void pair_insert_kernel(PairArgs A) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+template <int D, bool FUSED>
+__global__ void pair_insert_kernel(PairArgs A0, Fuse FU) {
+  IBMLBM_BIND(FUSED, PairArgs, A, A0, FU, blk);
+  const int i = (int)(blk * blockDim.x + threadIdx.x);
   if (i >= A.n) return;
   const int c = cell_of<D>(A, i);
   const int slot = atomicAdd(&A.cell_count[c], 1);
@@ -148,13 +149,14 @@ __device__ void advance_particle(const PairArgs& A, int i, const double* X, cons
 // tests occupied slots l, l+32, ... of the concatenated buckets.  Accepted partners
 // are appended in lane order and sorted by index.  Writes the sorted list, its length
 // and the number of partners j > i.
-template <int D>
-__global__ void __launch_bounds__(256) pair_search_kernel(PairArgs A) {
+template <int D, bool FUSED>
+__global__ void __launch_bounds__(256) pair_search_kernel(PairArgs A0, Fuse FU) {
+  IBMLBM_BIND(FUSED, PairArgs, A, A0, FU, blk);
   __shared__ int s_list[8][kMaxNeighbors];
   __shared__ int s_cell[8][32];
   __shared__ int s_off[8][33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int i = (int)((blk * (long long)blockDim.x + threadIdx.x) >> 5);
   if (i >= A.n) return;  // whole warp
   int* list = s_list[w];
   int* sc = s_cell[w];
@@ -243,9 +245,10 @@ __global__ void __launch_bounds__(256) pair_search_kernel(PairArgs A) {
 
 // Eq. 16 contact force on particle i from its sorted partner list (summed in index
 // order) and from one mirror image per wall, then (in a time step) the particle update.
-template <int D>
-__global__ void __launch_bounds__(128) pair_force_kernel(PairArgs A) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+template <int D, bool FUSED>
+__global__ void __launch_bounds__(128) pair_force_kernel(PairArgs A0, Fuse FU) {
+  IBMLBM_BIND(FUSED, PairArgs, A, A0, FU, blk);
+  const int i = (int)(blk * blockDim.x + threadIdx.x);
   if (i >= A.n) return;
   double Xi[3] = {0.0, 0.0, 0.0};
   for (int k = 0; k < D; ++k) Xi[k] = A.X[(long long)i * D + k];
@@ -351,9 +354,9 @@ cudaError_t launch_pair_cells(const PairArgs& A, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   const unsigned g = blocks_for(A.n, 256);
   if (A.D == 2)
-    pair_insert_kernel<2><<<g, 256, 0, s>>>(A);
+    pair_insert_kernel<2, false><<<g, 256, 0, s>>>(A, Fuse{});
   else
-    pair_insert_kernel<3><<<g, 256, 0, s>>>(A);
+    pair_insert_kernel<3, false><<<g, 256, 0, s>>>(A, Fuse{});
   return cudaGetLastError();
 }
 
@@ -363,16 +366,40 @@ cudaError_t launch_pair_contacts(const PairArgs& A, cudaStream_t s) {
   if (A.n == 0) return cudaSuccess;
   const unsigned gw = blocks_for((long long)A.n * 32, 256);
   if (A.D == 2)
-    pair_search_kernel<2><<<gw, 256, 0, s>>>(A);
+    pair_search_kernel<2, false><<<gw, 256, 0, s>>>(A, Fuse{});
   else
-    pair_search_kernel<3><<<gw, 256, 0, s>>>(A);
+    pair_search_kernel<3, false><<<gw, 256, 0, s>>>(A, Fuse{});
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !A.Fc) return e;
   const unsigned g = blocks_for(A.n, 128);
   if (A.D == 2)
-    pair_force_kernel<2><<<g, 128, 0, s>>>(A);
+    pair_force_kernel<2, false><<<g, 128, 0, s>>>(A, Fuse{});
   else
-    pair_force_kernel<3><<<g, 128, 0, s>>>(A);
+    pair_force_kernel<3, false><<<g, 128, 0, s>>>(A, Fuse{});
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------- fused over the members of a 2D batch
+// zero each member's cell counts (one thread per cell)
+__global__ void pair_clear_kernel(Fuse FU) {
+  IBMLBM_BIND(true, PairArgs, A, PairArgs{}, FU, blk);
+  const long long c = blk * (long long)blockDim.x + threadIdx.x;
+  if (c < (long long)A.nc[0] * A.nc[1] * A.nc[2]) A.cell_count[c] = 0;
+}
+
+unsigned pair_clear_blocks(const PairArgs& A) { return blocks_for((long long)A.nc[0] * A.nc[1] * A.nc[2], 256); }
+unsigned pair_thread_blocks(int n, int b) { return n > 0 ? blocks_for(n, b) : 0; }
+unsigned pair_warp_blocks(int n) { return n > 0 ? blocks_for((long long)n * 32, 256) : 0; }
+
+// clear + insert + search + force for every member (the force blocks also advance the
+// particles, as in a time step)
+cudaError_t launch_pairs_fused(const Fuse& Fc, unsigned bc, const Fuse& Fi, unsigned bi,
+                               const Fuse& Fs, unsigned bs, const Fuse& Ff, unsigned bf,
+                               cudaStream_t s) {
+  if (bc) pair_clear_kernel<<<bc, 256, 0, s>>>(Fc);
+  if (bi) pair_insert_kernel<2, true><<<bi, 256, 0, s>>>(PairArgs{}, Fi);
+  if (bs) pair_search_kernel<2, true><<<bs, 256, 0, s>>>(PairArgs{}, Fs);
+  if (bf) pair_force_kernel<2, true><<<bf, 128, 0, s>>>(PairArgs{}, Ff);
   return cudaGetLastError();
 }
 

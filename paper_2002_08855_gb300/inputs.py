@@ -229,6 +229,27 @@ def cavity_3d(scale: int = 1) -> Workload:
                     seed=SEED_BASE + 300 + scale)
 
 
+def ensemble_2d(n: int = 256, seed: int = SEED_BASE + 500, side=(64, 512), diam=(8.0, 16.0),
+                max_particles: int = 200, phi_max: float = 0.3) -> list:
+    """Batched ensemble: n independent D2Q9 closed cavities, sides uniform integers in
+    [side], per cavity one diameter uniform in [diam] with N_L = round(pi d) points and
+    a particle count uniform in 1..max_particles, capped at solid fraction phi_max;
+    density ratio 1.5, tau = 0.6, gravity 1e-5, 3 MDF iterations, 1000 steps."""
+    rng = SplitMix64(seed)
+    out = []
+    for c in range(n):
+        nx = side[0] + rng.randint(side[1] - side[0] + 1)
+        ny = side[0] + rng.randint(side[1] - side[0] + 1)
+        d = diam[0] + (diam[1] - diam[0]) * rng.uniform()
+        cap = int(phi_max * nx * ny / (math.pi * d * d / 4.0))
+        npart = max(1, min(1 + rng.randint(max_particles), cap))
+        out.append(Workload(name=f"ens{c}_{nx}x{ny}_np{npart}", dim=2, nx=nx, ny=ny, tau=0.6,
+                            n_particles=npart, n_lag=int(round(math.pi * d)), diameter=d,
+                            delta_kind=4, drs=2.6, mdf_iters=3, density_ratio=1.5,
+                            gravity=(0.0, -1e-5, 0.0), steps=1000, seed=seed + 1 + c))
+    return out
+
+
 def random_pdfs(q: int, n: int, seed: int, scale: float = 1e-2) -> np.ndarray:
     """[q][n] float32 PDFs drawn uniformly in [-scale, scale) (deviation gauge)."""
     rng = np.random.Generator(np.random.PCG64(seed))

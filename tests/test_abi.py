@@ -86,3 +86,28 @@ def test_pair_scratch_size_host_only(lib):
     nodes = (C.c_int32 * 3)(2048, 4096, 1)
     assert lib.ibm_lbm_pair_search_scratch_size(2, nodes, 10.0, 2.0, 42723, 0, C.byref(n)) == 0
     assert n.value > 42723 * 32 * 4
+
+
+def _batch_sizes(ws):
+    cfgs = (binding.Config * len(ws))(*[binding.make_config(w) for w in ws])
+    n = C.c_size_t(0)
+    rc = binding.lib().ibm_lbm_batch_workspace_size(cfgs, len(ws), C.byref(n))
+    return rc, n.value
+
+
+def test_batch_workspace_holds_every_member(lib):
+    ws = inputs.ensemble_2d(8)
+    rc, total = _batch_sizes(ws)
+    assert rc == 0
+    members = sum((binding.workspace_size(w) + 255) // 256 * 256 for w in ws)
+    assert members < total < members + 4 * 1024 * 1024
+
+
+@pytest.mark.parametrize("change,code", [
+    (dict(dim=3, nz=8), -2), (dict(pdf_storage=2), -2), (dict(mdf_iters=2), -1)])
+def test_batch_rejects_mixed_or_unsupported_members(lib, change, code):
+    ws = inputs.ensemble_2d(3)
+    ws[1] = ws[1].with_(**change)
+    rc, _ = _batch_sizes(ws)
+    assert rc == code
+    assert lib.ibm_lbm_last_error().decode()
