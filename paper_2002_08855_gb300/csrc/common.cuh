@@ -235,10 +235,13 @@ struct Fuse {
 };
 
 // In a kernel templated on bool FUSED: A = this block's argument struct (the kernel
-// parameter A0 for a single run), BLK = the block's index in its member's grid.
+// parameter A0 for a single run; for a member, a local copy, so the fields the kernel
+// uses are loaded once instead of at every use), BLK = the block's index in its
+// member's grid.
 #define IBMLBM_BIND(FUSED, TYPE, A, A0, F, BLK)                                        \
   const int bind_m_ = (FUSED) ? (F).cav[blockIdx.x] : 0;                             \
-  const TYPE& A = (FUSED) ? static_cast<const TYPE*>((F).args)[bind_m_] : (A0);      \
+  const TYPE bind_copy_ = (FUSED) ? static_cast<const TYPE*>((F).args)[bind_m_] : TYPE{}; \
+  const TYPE& A = (FUSED) ? bind_copy_ : (A0);                                       \
   const unsigned BLK = (FUSED) ? blockIdx.x - (unsigned)(F).first[bind_m_] : blockIdx.x
 
 // Capacity of one search-cell bucket: eight times the mean occupancy plus eight

@@ -108,9 +108,8 @@ __device__ __forceinline__ bool box_node(const Geo& g, int ox, int oy, int r, in
 //   MODE 1 (m >= 2): the box buffer plus f_IB/2.
 // Lane k then interpolates point k from shared memory.  Box nodes beyond a wall hold
 // zero, which drops them from the sum.
-template <int SC, int PARITY, int MODE, int ST, bool FUSED>
-__global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A0, int m, Fuse FU) {
-  IBMLBM_BIND(FUSED, IbmArgs, A, A0, FU, blk);
+template <int SC, int PARITY, int MODE, int ST>
+__device__ __forceinline__ void interp2_body(const IbmArgs& A, int m, unsigned blk) {
   extern __shared__ __align__(16) float smem_i[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int i = (int)blk * kIbmWarps + wib;
@@ -230,6 +229,22 @@ __global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A0,
   }
 }
 
+template <int SC, int PARITY, int MODE, int ST, bool FUSED>
+__global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A0, int m, Fuse FU) {
+  IBMLBM_BIND(FUSED, IbmArgs, A, A0, FU, blk);
+  if constexpr (FUSED) {  // members differ in box size: run the code compiled for this one
+    switch (A.box) {
+      case 14: interp2_body<14, PARITY, MODE, ST>(A, m, blk); return;
+      case 16: interp2_body<16, PARITY, MODE, ST>(A, m, blk); return;
+      case 18: interp2_body<18, PARITY, MODE, ST>(A, m, blk); return;
+      case 20: interp2_body<20, PARITY, MODE, ST>(A, m, blk); return;
+      case 22: interp2_body<22, PARITY, MODE, ST>(A, m, blk); return;
+      default: interp2_body<0, PARITY, MODE, ST>(A, m, blk); return;
+    }
+  }
+  interp2_body<SC, PARITY, MODE, ST>(A, m, blk);
+}
+
 // Spreading (Eq. 48) without shared-memory atomics.  The point's owner lane writes a
 // table row (the 16 products delta_x delta_y dV of its support, its force, the box
 // cell of its first support node).  Then the 16 lanes of each half-warp take one point
@@ -238,9 +253,8 @@ __global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A0,
 // node (anchors at most 3 apart on both axes) the halves take turns.  So no two lanes
 // of an instruction touch one cell and plain read-add-write is exact.  Finally the warp
 // adds the non-zero box cells to f_IB with one global vector atomic per cell.
-template <int SC, bool FUSED>
-__global__ void __launch_bounds__(kIbmWarps * 32) ibm_spread2_kernel(IbmArgs A0, Fuse FU) {
-  IBMLBM_BIND(FUSED, IbmArgs, A, A0, FU, blk);
+template <int SC>
+__device__ __forceinline__ void spread2_body(const IbmArgs& A, unsigned blk) {
   extern __shared__ __align__(16) float smem2[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int i = (int)blk * kIbmWarps + wib;
@@ -332,6 +346,22 @@ __global__ void __launch_bounds__(kIbmWarps * 32) ibm_spread2_kernel(IbmArgs A0,
     if (gy < 0 || gy >= A.g.ny) gy = ((gy % A.g.ny) + A.g.ny) % A.g.ny;  // axes reach here
     atomicAdd(fib2 + ((long long)gx + (long long)A.g.nx * gy), v);
   }
+}
+
+template <int SC, bool FUSED>
+__global__ void __launch_bounds__(kIbmWarps * 32) ibm_spread2_kernel(IbmArgs A0, Fuse FU) {
+  IBMLBM_BIND(FUSED, IbmArgs, A, A0, FU, blk);
+  if constexpr (FUSED) {  // members differ in box size: run the code compiled for this one
+    switch (A.box) {
+      case 14: spread2_body<14>(A, blk); return;
+      case 16: spread2_body<16>(A, blk); return;
+      case 18: spread2_body<18>(A, blk); return;
+      case 20: spread2_body<20>(A, blk); return;
+      case 22: spread2_body<22>(A, blk); return;
+      default: spread2_body<0>(A, blk); return;
+    }
+  }
+  spread2_body<SC>(A, blk);
 }
 
 // ------------------------------------------------------------------ 3D
@@ -700,9 +730,8 @@ __global__ void __launch_bounds__(256) ibm_forces_kernel(IbmArgs A) {
 // its candidate nodes kForceBatch at a time, so their loads are in flight together.
 constexpr int kForceBatch = 6;
 
-template <int SC, bool FUSED>
-__global__ void __launch_bounds__(256) ibm_forces2_kernel(IbmArgs A0, Fuse FU) {
-  IBMLBM_BIND(FUSED, IbmArgs, A, A0, FU, blk);
+template <int SC>
+__device__ __forceinline__ void forces2_body(const IbmArgs& A, unsigned blk) {
   const int i = (int)((blk * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= A.np) return;
@@ -760,6 +789,22 @@ __global__ void __launch_bounds__(256) ibm_forces2_kernel(IbmArgs A0, Fuse FU) {
     }
   }
   forces_finish<2>(A, i, lane, P, L);
+}
+
+template <int SC, bool FUSED>
+__global__ void __launch_bounds__(256) ibm_forces2_kernel(IbmArgs A0, Fuse FU) {
+  IBMLBM_BIND(FUSED, IbmArgs, A, A0, FU, blk);
+  if constexpr (FUSED) {  // members differ in box size: run the code compiled for this one
+    switch (A.box) {
+      case 14: forces2_body<14>(A, blk); return;
+      case 16: forces2_body<16>(A, blk); return;
+      case 18: forces2_body<18>(A, blk); return;
+      case 20: forces2_body<20>(A, blk); return;
+      case 22: forces2_body<22>(A, blk); return;
+      default: forces2_body<0>(A, blk); return;
+    }
+  }
+  forces2_body<SC>(A, blk);
 }
 
 // One warp per particle: regenerate its Lagrangian points for the next step,
