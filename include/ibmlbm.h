@@ -75,6 +75,9 @@ typedef struct ibm_lbm_config {
                              h_a = f_a / w_a (deviations from rest divided by the lattice
                              weight); collision, IBM and particle arithmetic stay FP32 /
                              FP64.  No counterpart in the paper, which stores doubles.    */
+  int32_t mlp_init;       /* 1: the first MDF iteration takes its force from the learned
+                             initializer (2D; parameters from ibm_lbm_set_mlp), the
+                             plain iterations 2..M follow.  No counterpart in the paper.  */
 } ibm_lbm_config;
 
 enum { IBMLBM_PDF_FP32 = 0, IBMLBM_PDF_FP16 = 1, IBMLBM_PDF_BF16 = 2 };
@@ -222,6 +225,46 @@ int ibm_lbm_pair_search_static(int32_t dim, const int32_t* n_nodes, const int32_
                                double diameter, double zeta, int32_t n, const double* d_X,
                                int32_t max_neighbors, int32_t* d_pairs, int64_t cap,
                                int64_t* h_count, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned MDF initializer (2D; no counterpart in the paper, which runs the plain
+ * iteration).  A perceptron 27 -> 64 -> 64 -> 3 (ReLU) maps the velocity-deficit
+ * stencil of a Lagrangian point, U_b - u_b* (u_b* = D_I u*, Eq. 12) at the point and at
+ * the 4 points on either side of it on the same circle, each as (normal, tangent, 0)
+ * components in the frame of the point, to the force of the first MDF iteration in
+ * that frame.  Parameters: ibm_lbm_mlp_param_count() floats, row-major
+ * W1[27][64] b1[64] W2[64][64] b2[64] W3[64][3] b3[3] in_scale out_scale (the network
+ * sees features * in_scale; its output is scaled by out_scale).
+ */
+int32_t ibm_lbm_mlp_param_count(void);
+
+/* Copy host parameters into the run (used by steps when cfg.mlp_init = 1). */
+int ibm_lbm_set_mlp(ibm_lbm_handle* h, const float* h_params);
+
+/* Training samples of the last step: d_X [npts][27] features, d_Y [npts][3] the step's
+ * total MDF force F_b in each point's frame (device arrays).  Synchronises the stream.
+ * Errors: INVALID_ARG before the first step or for a 3D run. */
+int ibm_lbm_mdf_samples(ibm_lbm_handle* h, float* d_X, float* d_Y);
+
+/* Record, in every later step, the boundary-velocity residual r_b = U_b - D_I u^(M)
+ * after the last MDF iteration (one extra interpolation launch; 2D). */
+int ibm_lbm_set_residual_tracking(ibm_lbm_handle* h, int32_t on);
+
+/* RMS and maximum over the points of |r_b| of the last tracked step (syncs). */
+int ibm_lbm_get_mdf_residual(ibm_lbm_handle* h, double* rms, double* maxabs);
+
+/* Training kernels (FP32; device pointers; loss = mean over the batch of the squared
+ * error summed over the 3 outputs).  Scratch: ibm_lbm_mlp_scratch_size bytes, 16-byte
+ * aligned.  mlp_grad writes d_grad (param_count floats; the two scales get none) and
+ * the loss to *h_loss (syncs when h_loss is set). */
+int ibm_lbm_mlp_scratch_size(int32_t batch, size_t* bytes);
+int ibm_lbm_mlp_grad(const float* d_params, const float* d_X, const float* d_T, int32_t batch,
+                     float* d_grad, double* h_loss, void* d_scratch, size_t scratch_bytes, void* stream);
+/* One Adam step (0.9, 0.999, 1e-8) at step t >= 1 with learning rate lr. */
+int ibm_lbm_mlp_adam(float* d_params, const float* d_grad, float* d_m, float* d_v, int64_t t, float lr,
+                     void* stream);
+/* Tensor-core inference (FP16 operands, FP32 accumulation) of n feature rows. */
+int ibm_lbm_mlp_infer(const float* d_params, const float* d_X, int64_t n, float* d_Y, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Batched ensemble: many independent 2D cavities stepped together.  Each member is an

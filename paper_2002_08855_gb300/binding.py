@@ -43,6 +43,7 @@ class Config(C.Structure):
         ("mdf_iters", C.c_int32), ("density_ratio", C.c_double), ("gravity", C.c_double * 3),
         ("zeta", C.c_double), ("eps_pp", C.c_double), ("E_pp", C.c_double),
         ("fixed_particles", C.c_int32), ("max_neighbors", C.c_int32), ("pdf_storage", C.c_int32),
+        ("mlp_init", C.c_int32),
     ]
 
 
@@ -74,6 +75,7 @@ def make_config(w, max_neighbors: int = 0) -> Config:
     c.fixed_particles = int(get("fixed_particles", 0))
     c.max_neighbors = int(max_neighbors)
     c.pdf_storage = int(get("pdf_storage", 0))
+    c.mlp_init = int(get("mlp_init", 0))
     return c
 
 
@@ -107,6 +109,15 @@ SIGNATURES = {
     "ibm_lbm_pair_search_static": (C.c_int, [C.c_int32, _ip, _ip, C.c_double, C.c_double,
                                              C.c_int32, _vp, C.c_int32, _vp, C.c_int64, _i64p,
                                              _vp]),
+    "ibm_lbm_mlp_param_count": (C.c_int32, []),
+    "ibm_lbm_set_mlp": (C.c_int, [_vp, _fp]),
+    "ibm_lbm_mdf_samples": (C.c_int, [_vp, _vp, _vp]),
+    "ibm_lbm_set_residual_tracking": (C.c_int, [_vp, C.c_int32]),
+    "ibm_lbm_get_mdf_residual": (C.c_int, [_vp, _dp, _dp]),
+    "ibm_lbm_mlp_scratch_size": (C.c_int, [C.c_int32, C.POINTER(C.c_size_t)]),
+    "ibm_lbm_mlp_grad": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp, _dp, _vp, C.c_size_t, _vp]),
+    "ibm_lbm_mlp_adam": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, C.c_float, _vp]),
+    "ibm_lbm_mlp_infer": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp]),
     "ibm_lbm_batch_workspace_size": (C.c_int, [C.POINTER(Config), C.c_int32, C.POINTER(C.c_size_t)]),
     "ibm_lbm_batch_init": (C.c_int, [C.POINTER(Config), C.c_int32, _vp, C.c_size_t, _vp,
                                      C.POINTER(_dp), C.POINTER(_vp)]),
@@ -281,6 +292,31 @@ class Simulation:
                 continue
             _check(rc, "get_pairs")
             return buf[: 2 * n.value].reshape(-1, 2)
+
+    # ------------------------------------------------------------ learned initializer
+    def set_mlp(self, params):
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+        if p.size != lib().ibm_lbm_mlp_param_count():
+            raise ValueError("wrong number of parameters")
+        _check(lib().ibm_lbm_set_mlp(self.h, _ptr(p, C.c_float)), "set_mlp")
+
+    def mdf_samples(self):
+        """(features [npts][27], targets [npts][3]) of the last step, as CUDA tensors."""
+        n = self.np * self.nl
+        X = self.torch.empty((n, 27), dtype=self.torch.float32, device=self.device)
+        Y = self.torch.empty((n, 3), dtype=self.torch.float32, device=self.device)
+        self._wait_torch()
+        _check(lib().ibm_lbm_mdf_samples(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(Y.data_ptr())),
+               "mdf_samples")
+        return X, Y
+
+    def set_residual_tracking(self, on: bool = True):
+        _check(lib().ibm_lbm_set_residual_tracking(self.h, int(bool(on))), "set_residual_tracking")
+
+    def mdf_residual(self):
+        rms, mx = C.c_double(0), C.c_double(0)
+        _check(lib().ibm_lbm_get_mdf_residual(self.h, C.byref(rms), C.byref(mx)), "get_mdf_residual")
+        return rms.value, mx.value
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:

@@ -17,6 +17,7 @@
 #include "ibmlbm.h"
 #include "common.cuh"
 #include "launch.h"
+#include "mlp.h"
 
 using namespace ibmlbm;
 
@@ -65,7 +66,7 @@ struct Derived {
 struct Layout {
   size_t f, ustar, fib, mask;
   size_t X0, X1, U, Om, Fh, Th, FhN, ThN, acc, alp, Pint, Lint, Pprev, Lprev, Fc;
-  size_t Uf, Omf, ref_fix, ref_f, Xcf, Xb0, Xb1, Ub0, Ub1, Fb, dFb, ubs, ubox;
+  size_t Uf, Omf, ref_fix, ref_f, Xcf, Xb0, Xb1, Ub0, Ub1, Fb, dFb, ubs, ubox, res, mlp, mlp_img;
   size_t cell_count, cell_ids, nbr, nbr_count, gt, pairs, status;
   size_t total;
 };
@@ -89,6 +90,10 @@ int check_config(const ibm_lbm_config* c) {
     return fail(IBMLBM_ERR_INVALID_ARG, "max_neighbors must be in 0..64");
   if (c->pdf_storage < IBMLBM_PDF_FP32 || c->pdf_storage > IBMLBM_PDF_BF16)
     return fail(IBMLBM_ERR_INVALID_ARG, "pdf_storage must be 0 (FP32), 1 (FP16) or 2 (BF16)");
+  if (c->mlp_init != 0 && c->mlp_init != 1) return fail(IBMLBM_ERR_INVALID_ARG, "mlp_init must be 0 or 1");
+  if (c->mlp_init && (c->dim != 2 || c->mdf_iters < 1 || c->n_lag > mlp_max_points()))
+    return fail(IBMLBM_ERR_UNSUPPORTED,
+                "the learned initializer needs a 2D run with mdf_iters >= 1 and n_lag <= 256");
   if (c->n_particles > 0) {
     if (c->n_lag < 1) return fail(IBMLBM_ERR_INVALID_ARG, "n_lag must be >= 1");
     if (!(c->diameter > 0.0)) return fail(IBMLBM_ERR_INVALID_ARG, "diameter must be > 0");
@@ -196,6 +201,9 @@ Layout carve(const ibm_lbm_config* c, const Derived& d) {
   l.Fb = cv.take(sizeof(float) * npts * D);
   l.dFb = cv.take(sizeof(float) * npts * D);
   l.ubs = cv.take(sizeof(float) * npts * D);
+  l.res = cv.take(D == 2 ? sizeof(float) * npts * D : 0);   // residual pass (2D)
+  l.mlp = cv.take(D == 2 ? sizeof(float) * kMlpParams : 0);  // learned initializer
+  l.mlp_img = cv.take(D == 2 ? mlp_image_bytes() : 0);
   // 2D: u* of each particle's node box (box rows of box_pitch(box) float2 cells)
   l.ubox = cv.take(D == 2 ? sizeof(float) * np * 2 * (size_t)d.box * box_pitch(d.box) : 0);
   const size_t ncells = (size_t)d.nc[0] * d.nc[1] * d.nc[2];
@@ -243,6 +251,9 @@ struct ibm_lbm_handle {
   // that fork it from and join it back into s
   cudaStream_t side;
   cudaEvent_t fork, join;
+  bool mlp_set;     // learned-initializer parameters copied in
+  bool track_res;   // residual pass after the last MDF iteration
+  long long res_step;  // step whose residual the buffer holds (-1: none)
   long long step;
   int have_prev;
   int64_t launches;
@@ -297,6 +308,7 @@ struct ibm_lbm_handle {
     a.Fb = at<float>(l.Fb);
     a.dFb = at<float>(l.dFb);
     a.ubs = at<float>(l.ubs);
+    a.res = at<float>(l.res);
     a.Xc = X(parity);
     a.Xcf = at<long long>(l.Xcf);
     a.ref_f = at<float>(l.ref_f);
@@ -416,10 +428,18 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
     for (int m = 1; m <= h->cfg.mdf_iters; ++m) {
       CUDA_TRY(launch_ibm_interp(ia, m, s));  // 3D: interpolation and spreading
       ++k;
+      if (m == 1 && h->cfg.mlp_init) {  // learned first force (2D)
+        CUDA_TRY(launch_mlp_step(ia, h->at<float>(h->l.mlp), h->at<void>(h->l.mlp_img), s));
+        ++k;
+      }
       if (h->d.D == 2) {
         CUDA_TRY(launch_ibm_spread(ia, s));
         ++k;
       }
+    }
+    if (h->track_res && h->d.D == 2 && h->cfg.mdf_iters > 0) {
+      CUDA_TRY(launch_ibm_interp(ia, -1, s));
+      ++k;
     }
     CUDA_TRY(launch_ibm_forces(ia, s));
     ++k;
@@ -560,6 +580,9 @@ int ibm_lbm_init(const ibm_lbm_config* cfg, void* d_workspace, size_t bytes, voi
   h->graph_tried[0] = h->graph_tried[1] = false;
   h->side = nullptr;
   h->fork = h->join = nullptr;
+  h->mlp_set = false;
+  h->track_res = false;
+  h->res_step = -1;
   auto bail = [&](int code) {
     if (h->side) cudaStreamDestroy(h->side);
     if (h->fork) cudaEventDestroy(h->fork);
@@ -606,6 +629,8 @@ int ibm_lbm_step(ibm_lbm_handle* h, int32_t n_steps) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (n_steps < 0) return fail(IBMLBM_ERR_INVALID_ARG, "n_steps < 0");
+  if (h->cfg.mlp_init && !h->mlp_set)
+    return fail(IBMLBM_ERR_INVALID_ARG, "mlp_init is set but ibm_lbm_set_mlp was not called");
   for (int32_t t = 0; t < n_steps; ++t) {
     const int parity = (int)(h->step & 1);
     if (h->have_prev && !h->graph_tried[parity]) {
@@ -621,6 +646,7 @@ int ibm_lbm_step(ibm_lbm_handle* h, int32_t n_steps) {
       if (rc) return rc;
       h->launches += nk;
     }
+    if (h->track_res) h->res_step = h->step;
     h->step += 1;
     h->have_prev = 1;
   }
@@ -843,6 +869,67 @@ int ibm_lbm_time_parts(ibm_lbm_handle* h, int32_t n_steps, double* ms) {
   return out;
 }
 
+
+int ibm_lbm_set_mlp(ibm_lbm_handle* h, const float* h_params) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!h_params) return fail(IBMLBM_ERR_INVALID_ARG, "h_params is NULL");
+  if (h->d.D != 2) return fail(IBMLBM_ERR_UNSUPPORTED, "the learned initializer is 2D");
+  CUDA_TRY(cudaMemcpyAsync(h->at<float>(h->l.mlp), h_params, sizeof(float) * kMlpParams,
+                           cudaMemcpyHostToDevice, h->s));
+  CUDA_TRY(launch_mlp_image(h->at<float>(h->l.mlp), h->at<void>(h->l.mlp_img), h->s));
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  h->mlp_set = true;
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_mdf_samples(ibm_lbm_handle* h, float* d_X, float* d_Y) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!d_X || !d_Y) return fail(IBMLBM_ERR_INVALID_ARG, "sample arrays are NULL");
+  if (h->d.D != 2 || h->step < 1)
+    return fail(IBMLBM_ERR_INVALID_ARG, "samples need a 2D run after its first step");
+  CUDA_TRY(launch_mlp_samples(h->ibm((int)((h->step - 1) & 1)), d_X, d_Y, h->s));
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_set_residual_tracking(ibm_lbm_handle* h, int32_t on) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (h->d.D != 2) return fail(IBMLBM_ERR_UNSUPPORTED, "residual tracking is 2D");
+  if ((bool)on == h->track_res) return IBMLBM_OK;
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  for (int p = 0; p < 2; ++p) {  // the captured steps change: capture again
+    if (h->graph_ok[p]) cudaGraphExecDestroy(h->graph[p]);
+    h->graph_ok[p] = h->graph_tried[p] = false;
+  }
+  h->track_res = on != 0;
+  h->res_step = -1;
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_get_mdf_residual(ibm_lbm_handle* h, double* rms, double* maxabs) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (h->res_step < 0) return fail(IBMLBM_ERR_INVALID_ARG, "no tracked step yet");
+  const size_t npts = (size_t)h->d.npts;
+  std::vector<float> r(npts * 2);
+  if (npts)
+    CUDA_TRY(cudaMemcpyAsync(r.data(), h->at<float>(h->l.res), sizeof(float) * r.size(),
+                             cudaMemcpyDeviceToHost, h->s));
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  double s2 = 0.0, mx = 0.0;
+  for (size_t b = 0; b < npts; ++b) {
+    const double v = (double)r[2 * b] * r[2 * b] + (double)r[2 * b + 1] * r[2 * b + 1];
+    s2 += v;
+    mx = std::max(mx, std::sqrt(v));
+  }
+  if (rms) *rms = npts ? std::sqrt(s2 / npts) : 0.0;
+  if (maxabs) *maxabs = mx;
+  return IBMLBM_OK;
+}
+
 void ibm_lbm_destroy(ibm_lbm_handle* h) {
   if (!h) return;
   for (int p = 0; p < 2; ++p)
@@ -1021,6 +1108,7 @@ int check_batch(const ibm_lbm_config* cfgs, int32_t n) {
     if (cfgs[i].dim != 2) return fail(IBMLBM_ERR_UNSUPPORTED, "batch members must be 2D");
     if (cfgs[i].pdf_storage == IBMLBM_PDF_BF16)
       return fail(IBMLBM_ERR_UNSUPPORTED, "batch members store PDFs as FP32 or FP16");
+    if (cfgs[i].mlp_init) return fail(IBMLBM_ERR_UNSUPPORTED, "batch members use the plain MDF");
     if (cfgs[i].pdf_storage != cfgs[0].pdf_storage || cfgs[i].mdf_iters != cfgs[0].mdf_iters)
       return fail(IBMLBM_ERR_INVALID_ARG, "batch members must share pdf_storage and mdf_iters");
   }
@@ -1060,6 +1148,9 @@ struct ibm_lbm_batch {
   cudaStream_t s;
   cudaStream_t side;
   cudaEvent_t fork, join;
+  bool mlp_set;     // learned-initializer parameters copied in
+  bool track_res;   // residual pass after the last MDF iteration
+  long long res_step;  // step whose residual the buffer holds (-1: none)
   int store, mdf;
   size_t smem;                   // 2D IBM shared memory for the largest box
   unsigned blocks[BK_COUNT];

@@ -178,6 +178,7 @@ struct IbmArgs {
   double* Lint;      // [np][3] interior angular momentum
   double* FhN;       // [np][D] -dV sum_b F_b of this step
   double* ThN;       // [np][3] -dV sum_b r_b x F_b of this step
+  float* res;        // [npts][D] U_b - D_I u^(M) (residual pass, 2D)
   uint32_t* status;
 };
 

@@ -105,7 +105,8 @@ __device__ __forceinline__ bool box_node(const Geo& g, int ox, int oy, int r, in
 //   MODE 0 (m = 1, or m = 0: box only, when no forcing iteration runs): u* (Eq. 5) of
 //     every node of the particle's box from the PDFs (AA-parity addressing), kept in
 //     the particle's box buffer for the later iterations and the interior sums;
-//   MODE 1 (m >= 2): the box buffer plus f_IB/2.
+//   MODE 1 (m >= 2): the box buffer plus f_IB/2; with m < 0 the same gather after the
+//     last iteration only records the residual U_b - D_I u^(M).
 // Lane k then interpolates point k from shared memory.  Box nodes beyond a wall hold
 // zero, which drops them from the sum.
 template <int SC, int PARITY, int MODE, int ST>
@@ -119,7 +120,7 @@ __device__ __forceinline__ void interp2_body(const IbmArgs& A, int m, unsigned b
   float2* aux = box + cells;
   float2* ub = reinterpret_cast<float2*>(A.ubox) + (size_t)i * cells;
   // the first point of this lane is loaded before the box, so both latencies overlap
-  const bool has0 = m > 0 && lane < A.nl;
+  const bool has0 = m != 0 && lane < A.nl;
   const long long b0 = (long long)i * A.nl + lane;
   long long X0x = 0, X0y = 0;
   float U0x = 0.0f, U0y = 0.0f;
@@ -213,6 +214,11 @@ __device__ __forceinline__ void interp2_body(const IbmArgs& A, int m, unsigned b
         acc0 += wy * a0;
         acc1 += wy * a1;
       }
+    }
+    if (m < 0) {  // residual pass after the last iteration: r_b = U_b - D_I u^(M)
+      A.res[b * 2] = Ux - acc0;
+      A.res[b * 2 + 1] = Uy - acc1;
+      continue;
     }
     const float d0 = 2.0f * (Ux - acc0), d1 = 2.0f * (Uy - acc1);
     A.dFb[b * 2] = d0;
@@ -902,7 +908,7 @@ cudaError_t launch_ibm_interp(const IbmArgs& A, int m, cudaStream_t s) {
   if (A.npts == 0) return cudaSuccess;
   if (A.D == 2) {
     const unsigned grid = (unsigned)((A.np + kIbmWarps - 1) / kIbmWarps);
-    const int mode = m <= 1 ? 0 : 1;
+    const int mode = (m == 0 || m == 1) ? 0 : 1;  // m < 0: residual pass (box + f_IB/2)
     const size_t sm = sizeof(float) * kIbmWarps * (size_t)interp2_warp_floats(mode, A.box);
 #define IBMLBM_INTERP2_ST(SC, P)                                                             \
   do {                                                                                        \

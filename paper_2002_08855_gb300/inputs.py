@@ -67,6 +67,7 @@ class Workload:
     E_pp: float = 1e-4
     fixed_particles: int = 0
     pdf_storage: int = 0  # 0 FP32, 1 FP16, 2 BF16 (GPU storage of the PDFs only)
+    mlp_init: int = 0     # 1: learned first MDF force (GPU, 2D)
     steps: int = 100
     seed: int = SEED_BASE
     centres: np.ndarray | None = field(default=None, repr=False)
@@ -82,7 +83,7 @@ class Workload:
         d = {k: getattr(self, k) for k in (
             "dim", "nx", "ny", "nz", "periodic", "tau", "body_force", "n_particles", "n_lag",
             "diameter", "delta_kind", "drs", "mdf_iters", "density_ratio", "gravity", "zeta",
-            "eps_pp", "E_pp", "fixed_particles", "pdf_storage")}
+            "eps_pp", "E_pp", "fixed_particles", "pdf_storage", "mlp_init")}
         if self.dim == 2:
             d["nz"] = 1
         return d
