@@ -12,8 +12,8 @@ form, FP16 storage of h = f / w with the learned first MDF force and 2 iteration
 its stated error and its boundary-velocity residual (against the plain form's).  Also reported: the roofline of
 the dominant kernel (lbm_step) against the measured HBM copy bandwidth, an
 end-to-end number through the C ABI with host buffers, the FP64 CPU oracle timed
-on a bounded sample on the host cores, and the batched ensemble of 256 independent
-cavities (aggregate MLUPS).
+on a bounded sample on the host cores, the batched ensemble of 256 independent
+cavities (aggregate MLUPS) and the 384 x 384 x 768 D3Q19 cavity with 20000 spheres.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 (N > 1: launch with torchrun; each rank runs an independent replica.)
@@ -360,6 +360,37 @@ def _ensemble(args, dev, local):
     return out
 
 
+def _cavity3d(args, dev, local):
+    """The D3Q19 cavity 384 x 384 x 768 with 20000 spheres (d = 12, 452 points), FP32
+    and FP16 storage: MLUPS over min(steps, 20) timed steps."""
+    import torch
+
+    from paper_2002_08855_gb300 import binding, inputs
+
+    w = inputs.cavity_3d(1)
+    X = inputs.place_particles(w)
+    steps = max(3, min(args.steps, 20))
+    out = {"workload": w.name, "lattice": "D3Q19 384x384x768", "particles": w.n_particles,
+           "points_per_particle": w.n_lag, "steps": steps}
+    for st, name in ((0, "fp32"), (1, "fp16")):
+        sim = binding.Simulation(w.with_(pdf_storage=st), X, device=str(dev))
+        sim.step(3)
+        sim.sync()
+        with ClockSampler(local) as clk:
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(sim.stream)
+            sim.step(steps)
+            ev1.record(sim.stream)
+            ev1.synchronize()
+            sim.sync()
+        ms = ev0.elapsed_time(ev1) / steps
+        parts = sim.time_parts(3)
+        sim.close()
+        out[name] = {"value": w.n_grid / (ms * 1e3), "unit": METRIC, "ms_per_step": ms,
+                     "parts_ms_per_step": {k: v / 3 for k, v in parts.items()}, "clocks": clk.summary()}
+    return out
+
+
 def run(args):
     import torch
 
@@ -426,8 +457,9 @@ def run(args):
 
     # the other forms of the method on the same workload and the chosen one
     chosen, forms = _forms(args, w, X, dev, peak, peak_kind, local)
-    # the batched ensemble of independent cavities
+    # the batched ensemble of independent cavities, and the 3D cavity
     ensemble = _ensemble(args, dev, local)
+    cavity3d = _cavity3d(args, dev, local)
 
     # end to end through the C ABI with host buffers: init from host centres, then per
     # step one ibm_lbm_step and a read of the particle state into pinned host memory
@@ -474,6 +506,7 @@ def run(args):
             "chosen_form": chosen,
             "forms": forms,
             "ensemble": ensemble,
+            "cavity3d": cavity3d,
         }
         print(json.dumps(line))
     if dist is not None:
