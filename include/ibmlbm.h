@@ -61,7 +61,8 @@ typedef struct ibm_lbm_config {
   int32_t n_particles;    /* N_p, rigid circles (2D) or spheres (3D), >= 0               */
   int32_t n_lag;          /* N_L Lagrangian points per particle (Sec. 2.2)               */
   double diameter;        /* D_p                                                         */
-  int32_t delta_kind;     /* regularised delta function of Fig. 2b: 4 (4-point)          */
+  int32_t delta_kind;     /* regularised delta function of Fig. 2b: 4 (Peskin's 4-point) or
+                             3 (3-point of Roma, Peskin and Berger; drs = 1.9 in Sec. 2.2) */
   double drs;             /* solid-shell thickness of Eq. 13 (2.6 for the 4-point delta) */
   int32_t mdf_iters;      /* M >= 0 multi-direct-forcing iterations; 1 is BTDF (Eq. 9-11)*/
   double density_ratio;   /* rho_p / rho_f                                               */
@@ -98,7 +99,7 @@ int ibm_lbm_workspace_size(const ibm_lbm_config* cfg, size_t* bytes);
  * p = 0 (every PDF zero, the deviation gauge of the incompressible model) and the
  * particles with U = Omega = 0.  Copies the centres to the device and waits for
  * the stream.  Errors: INVALID_ARG (configuration, pointers, a centre outside
- * the domain), WORKSPACE, UNSUPPORTED (delta_kind other than 4), CUDA. */
+ * the domain), WORKSPACE, UNSUPPORTED (delta_kind other than 3 or 4), CUDA. */
 int ibm_lbm_init(const ibm_lbm_config* cfg, void* d_workspace, size_t bytes, void* stream,
                  const double* h_centres, ibm_lbm_handle** out);
 

@@ -97,8 +97,8 @@ int check_config(const ibm_lbm_config* c) {
   if (c->n_particles > 0) {
     if (c->n_lag < 1) return fail(IBMLBM_ERR_INVALID_ARG, "n_lag must be >= 1");
     if (!(c->diameter > 0.0)) return fail(IBMLBM_ERR_INVALID_ARG, "diameter must be > 0");
-    if (c->delta_kind != 4)
-      return fail(IBMLBM_ERR_UNSUPPORTED, "only the 4-point delta function is built");
+    if (c->delta_kind != 4 && c->delta_kind != 3)
+      return fail(IBMLBM_ERR_UNSUPPORTED, "delta_kind must be 4 or 3");
     if (!(c->drs > 0.0)) return fail(IBMLBM_ERR_INVALID_ARG, "drs must be > 0");
     if (c->mdf_iters < 0) return fail(IBMLBM_ERR_INVALID_ARG, "mdf_iters must be >= 0");
     if (!(c->density_ratio > 0.0))
@@ -291,6 +291,7 @@ struct ibm_lbm_handle {
     a.np = cfg.n_particles;
     a.nl = cfg.n_lag;
     a.npts = d.npts;
+    a.delta_kind = cfg.delta_kind;
     a.radius = d.radius;
     a.radius_f = (float)d.radius;
     a.rcell = d.rcell;

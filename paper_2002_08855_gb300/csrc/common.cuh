@@ -154,6 +154,7 @@ struct IbmArgs {
   int D;             // dimension
   int np, nl;
   long long npts;
+  int delta_kind;    // 4: Peskin's 4-point delta, 3: the 3-point delta
   double radius;     // D_p / 2
   float radius_f;    // D_p / 2 as float
   int rcell;         // ceil(D_p / 2)

@@ -26,32 +26,29 @@ __device__ __forceinline__ float delta4(float r) {
   return 0.0f;
 }
 
-struct AxisSup {
-  int idx[4];
-  float w[4];
-  bool ok[4];
-};
+// 3-point regularised delta function (Fig. 2b; the form of Roma, Peskin and Berger,
+// used with drs = 1.9 in Sec. 2.2)
+__device__ __forceinline__ float delta3(float r) {
+  const float a = fabsf(r);
+  if (a <= 0.5f) return (1.0f + sqrtf(fmaxf(0.0f, 1.0f - 3.0f * a * a))) * (1.0f / 3.0f);
+  if (a <= 1.5f) return (5.0f - 3.0f * a - sqrtf(fmaxf(0.0f, -2.0f + 6.0f * a - 3.0f * a * a))) * (1.0f / 6.0f);
+  return 0.0f;
+}
 
-// support nodes floor(X)-1 .. floor(X)+2 along one axis of a fixed-point coordinate;
-// the offsets from X are (t - 1) - frac(X).  Nodes beyond a wall are dropped,
-// periodic axes wrap.
-__device__ __forceinline__ void axis_support(long long Xfix, int n, int per, AxisSup& s) {
-  const int i0 = fix_anchor(Xfix) - 1;
-  const float fr = fix_frac(Xfix);
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    int i = i0 + t;
-    s.w[t] = delta4((float)(t - 1) - fr);
-    bool ok = true;
-    if (i < 0 || i >= n) {
-      if (per)
-        i = ((i % n) + n) % n;
-      else
-        ok = false;
-    }
-    s.idx[t] = i;
-    s.ok[t] = ok;
+__device__ __forceinline__ float delta_w(int kind, float r) { return kind == 3 ? delta3(r) : delta4(r); }
+
+// First support node along one axis of a fixed-point coordinate X, and fr such that
+// the offset of support node t (t = 0..3) from X is (t - 1) - fr: 4-point nodes
+// floor(X)-1 .. floor(X)+2 (fr = frac X); 3-point nodes round(X)-1 .. round(X)+1
+// (fr = X - round X), whose fourth node then carries weight zero.
+__device__ __forceinline__ int support_first(int kind, long long X, float& fr) {
+  if (kind == 3) {
+    const long long r = X + (1LL << 31);  // X + 1/2
+    fr = fix_frac(r) - 0.5f;
+    return fix_anchor(r) - 1;
   }
+  fr = fix_frac(X);
+  return fix_anchor(X) - 1;
 }
 
 // 2D kernels with one warp per particle and the particle's node box in shared memory
@@ -186,18 +183,18 @@ __device__ __forceinline__ void interp2_body(const IbmArgs& A, int m, unsigned b
     const bool first = k == lane;
     const long long Xx = first ? X0x : A.Xb[b * 2], Xy = first ? X0y : A.Xb[b * 2 + 1];
     const float Ux = first ? U0x : A.Ub[b * 2], Uy = first ? U0y : A.Ub[b * 2 + 1];
-    const int lx0 = fix_anchor(Xx) - 1 - ox, ly0 = fix_anchor(Xy) - 1 - oy;
-    const float rx = fix_frac(Xx), ry = fix_frac(Xy);
+    float rx, ry;
+    const int lx0 = support_first(A.delta_kind, Xx, rx) - ox, ly0 = support_first(A.delta_kind, Xy, ry) - oy;
     float acc0 = 0.0f, acc1 = 0.0f;
     if (lx0 < 0 || ly0 < 0 || lx0 + 3 >= S || ly0 + 3 >= S) {
       atomicOr(A.status, ST_CAPACITY);
     } else {
       float wx[4];
 #pragma unroll
-      for (int sx = 0; sx < 4; ++sx) wx[sx] = delta4((float)(sx - 1) - rx);
+      for (int sx = 0; sx < 4; ++sx) wx[sx] = delta_w(A.delta_kind, (float)(sx - 1) - rx);
 #pragma unroll
       for (int sy = 0; sy < 4; ++sy) {
-        const float wy = delta4((float)(sy - 1) - ry);
+        const float wy = delta_w(A.delta_kind, (float)(sy - 1) - ry);
         const int o = (ly0 + sy) * P + lx0;
         float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
@@ -284,8 +281,8 @@ __device__ __forceinline__ void spread2_body(const IbmArgs& A, unsigned blk) {
       const long long b = (long long)i * A.nl + g0 + lane;
       const long long Xx = A.Xb[b * 2], Xy = A.Xb[b * 2 + 1];
       const float fx = A.dFb[b * 2] * A.dV, fy = A.dFb[b * 2 + 1] * A.dV;
-      const int bx = fix_anchor(Xx) - 1, by = fix_anchor(Xy) - 1;
-      const float rx = fix_frac(Xx), ry = fix_frac(Xy);
+      float rx, ry;
+      const int bx = support_first(A.delta_kind, Xx, rx), by = support_first(A.delta_kind, Xy, ry);
       lbx = bx - ox;
       lby = by - oy;
       valid = lbx >= 0 && lby >= 0 && lbx + 3 < S && lby + 3 < S;
@@ -294,8 +291,8 @@ __device__ __forceinline__ void spread2_body(const IbmArgs& A, unsigned blk) {
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const int gx = bx + t, gy = by + t;
-        wx[t] = (!A.g.per[0] && (gx < 0 || gx >= A.g.nx)) ? 0.0f : delta4((float)(t - 1) - rx);
-        wy[t] = (!A.g.per[1] && (gy < 0 || gy >= A.g.ny)) ? 0.0f : delta4((float)(t - 1) - ry);
+        wx[t] = (!A.g.per[0] && (gx < 0 || gx >= A.g.nx)) ? 0.0f : delta_w(A.delta_kind, (float)(t - 1) - rx);
+        wy[t] = (!A.g.per[1] && (gy < 0 || gy >= A.g.ny)) ? 0.0f : delta_w(A.delta_kind, (float)(t - 1) - ry);
       }
       float* row = tw + lane * kTw;
 #pragma unroll
@@ -432,7 +429,13 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_mdf3_kernel(IbmArgs A, int m
   }
   const float dx = (float)(org[0] + lane - an[0]) - fr[0];
 
-  // 1. stage the ball of the box, kRows3 rows per warp and round
+  // 1. stage the ball of the box, kRows3 rows per warp and round.  The 3-point delta's
+  //    fourth (zero-weight) node can lie outside the ball: the box starts from zero then.
+  if (A.delta_kind == 3) {
+    const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int q = tid; q < 3 * cells / 4; q += kMdf3Threads) reinterpret_cast<float4*>(box)[q] = z4;
+    __syncthreads();
+  }
   const int rows = S * S;
   for (int r0 = warp; r0 < rows; r0 += kMdf3Warps * kRows3) {
     float4 v[kRows3];
@@ -482,15 +485,15 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_mdf3_kernel(IbmArgs A, int m
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const long long X = A.Xb[b * 3 + a];
-      const int s0 = fix_anchor(X) - 1;
-      const float f = fix_frac(X);
+      float f;
+      const int s0 = support_first(A.delta_kind, X, f);
       const int l0 = s0 - org[a];
       if (l0 < 0 || l0 + 3 >= S) valid = false;
       base += l0 * (a == 0 ? 1 : a == 1 ? Py : Pz);
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const int gc = s0 + t;
-        row[4 * a + t] = (!A.g.per[a] && (gc < 0 || gc >= nn[a])) ? 0.0f : delta4((float)(t - 1) - f);
+        row[4 * a + t] = (!A.g.per[a] && (gc < 0 || gc >= nn[a])) ? 0.0f : delta_w(A.delta_kind, (float)(t - 1) - f);
       }
     }
     if (!valid) {

@@ -62,7 +62,7 @@ def test_half_precision_storage_halves_the_pdf_bytes(lib):
 
 @pytest.mark.parametrize("field,value,code", [
     ("dim", 4, "INVALID_ARG"), ("tau", 0.5, "INVALID_ARG"), ("nx", 0, "INVALID_ARG"),
-    ("delta_kind", 3, "UNSUPPORTED"), ("n_lag", 0, "INVALID_ARG"), ("drs", 0.0, "INVALID_ARG"),
+    ("delta_kind", 5, "UNSUPPORTED"), ("n_lag", 0, "INVALID_ARG"), ("drs", 0.0, "INVALID_ARG"),
     ("pdf_storage", 3, "INVALID_ARG"),
 ])
 def test_invalid_configurations_are_rejected(lib, field, value, code):

@@ -38,13 +38,26 @@ CASES = [
 ]
 
 
+# the 3-point delta function (drs = 1.9, Sec. 2.2) on a subset of the cases
+CASES3 = [CASES[1], CASES[2], CASES[3], CASES[4], CASES[5], CASES[6]]
+
+
 @pytest.mark.parametrize("dim,shape,per,xc,D,nl", CASES)
 def test_one_step_lagrangian_forces(dim, shape, per, xc, D, nl):
+    _one_step(dim, shape, per, xc, D, nl, 4, 2.6)
+
+
+@pytest.mark.parametrize("dim,shape,per,xc,D,nl", CASES3)
+def test_one_step_lagrangian_forces_3_point_delta(dim, shape, per, xc, D, nl):
+    _one_step(dim, shape, per, xc, D, nl, 3, 1.9)
+
+
+def _one_step(dim, shape, per, xc, D, nl, kind, drs):
     require_gpu()
     xc = np.array(xc)
     w = Workload(name="ibm", dim=dim, nx=shape[0], ny=shape[1], nz=shape[2] if dim == 3 else 1,
                  periodic=per, tau=0.7, n_particles=len(xc), n_lag=nl, diameter=D, mdf_iters=3,
-                 fixed_particles=1)
+                 fixed_particles=1, delta_kind=kind, drs=drs)
     rng = np.random.Generator(np.random.PCG64(3))
     U = rng.uniform(-2e-3, 2e-3, xc.shape)
     Om = rng.uniform(-1e-4, 1e-4, (len(xc), 1 if dim == 2 else 3))

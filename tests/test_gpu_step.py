@@ -58,3 +58,23 @@ def test_cavity_3d_small():
     pg, po = sim.get_particles(), ref.get_particles()
     assert rel_l2(pg["X"] - X0, po["X"] - X0) < 1e-5
     sim.close()
+
+
+def test_cavity_128x256_3_point_delta():
+    """The same cavity with the 3-point delta function and drs = 1.9 (the paper's
+    experiments, Sec. 2.2 and 6.2), 100 steps."""
+    require_gpu()
+    from paper_2002_08855_gb300.binding import Simulation
+
+    w = inputs.cavity_2d_small().with_(delta_kind=3, drs=1.9)
+    X0 = inputs.place_particles(w)
+    sim = Simulation(w, X0)
+    ref = oracle.Sim(w.as_dict(), X0)
+    sim.step(100)
+    ref.step(100)
+    _, ug = sim.get_fields()
+    _, uo = ref.get_fields()
+    assert rel_l2(ug.cpu().numpy(), uo) < 1e-5
+    pg, po = sim.get_particles(), ref.get_particles()
+    assert rel_l2(pg["X"] - X0, po["X"] - X0) < 1e-5
+    sim.close()
