@@ -24,6 +24,16 @@ CASES = [
     (3, (19, 13, 11), (0, 0, 0)),
     (3, (16, 12, 10), (1, 0, 1)),
     (3, (35, 9, 8), (1, 1, 1)),
+    # degenerate domains: one or two nodes across, walls and periodic axes mixed (the
+    # odd-step edge kernel covers rows that are faces on both sides, rows of one node)
+    (2, (1, 7, 1), (1, 0, 0)),
+    (2, (5, 1, 1), (0, 1, 0)),
+    (2, (2, 2, 1), (0, 0, 0)),
+    (2, (1, 1, 1), (1, 1, 0)),
+    (3, (3, 1, 4), (0, 1, 0)),
+    (3, (1, 3, 3), (1, 0, 0)),
+    (3, (4, 4, 1), (0, 0, 1)),
+    (3, (2, 2, 2), (0, 0, 0)),
 ]
 
 
