@@ -172,7 +172,8 @@ Layout carve(const ibm_lbm_config* c, const Derived& d) {
   const size_t npts = (size_t)d.npts;
   l.f = cv.take((c->pdf_storage == IBMLBM_PDF_FP32 ? 4 : 2) * ((size_t)d.Q * d.g.Np + 64));
   l.ustar = cv.take(D == 3 ? sizeof(float) * 4 * N : 0);  // 3D [N][4]; 2D keeps u* per particle box
-  l.fib = cv.take(sizeof(float) * (D == 3 ? 4 : 2) * N);     // 2D [N][2], 3D [N][4]
+  // 2D [N][2] (none in a run without particles), 3D [N][4]
+  l.fib = cv.take(D == 3 ? sizeof(float) * 4 * N : (np > 0 ? sizeof(float) * 2 * N : 0));
   l.mask = cv.take(D == 3 ? 2 * sizeof(uint32_t) * (size_t)d.g.rows * d.g.wpr : 0);  // 3D, one per parity
   l.X0 = cv.take(sizeof(double) * np * D);
   l.X1 = cv.take(sizeof(double) * np * D);
@@ -275,7 +276,7 @@ struct ibm_lbm_handle {
     a.f = at<void>(l.f);
     a.store = cfg.pdf_storage;
     a.ustar = at<float>(l.ustar);
-    a.fib = at<float>(l.fib);
+    a.fib = (d.D == 3 || cfg.n_particles > 0) ? at<float>(l.fib) : nullptr;  // 2D: null = no IB force
     a.mask = mask(parity);
     a.omega = (float)(1.0 / cfg.tau);
     a.kforce = (float)(1.0 - 0.5 / cfg.tau);
@@ -503,7 +504,7 @@ int capture_graph(ibm_lbm_handle* h, int parity) {
     return IBMLBM_ERR_CUDA;
   }
   cudaGraphExec_t exec = nullptr;
-  if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+  if (cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) {
     cudaGraphDestroy(graph);
     cudaGetLastError();
     return IBMLBM_ERR_CUDA;
@@ -598,7 +599,14 @@ int ibm_lbm_init(const ibm_lbm_config* cfg, void* d_workspace, size_t bytes, voi
       return bail(fail(IBMLBM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_))); \
   } while (0)
   INIT_TRY(cudaMemsetAsync(h->ws, 0, l.total, h->s));
-  INIT_TRY(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  {
+    // the side stream's short particle kernels at the highest priority: the block
+    // scheduler then places their blocks ahead of lbm_step's as SMs free up, so they
+    // finish inside lbm_step's time instead of after it
+    int lo_ = 0, hi_ = 0;
+    INIT_TRY(cudaDeviceGetStreamPriorityRange(&lo_, &hi_));
+    INIT_TRY(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi_));
+  }
   INIT_TRY(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
   INIT_TRY(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
   if (cfg->n_particles > 0) {
@@ -1227,7 +1235,7 @@ int capture_batch_graph(ibm_lbm_batch* b, int parity) {
     return IBMLBM_ERR_CUDA;
   }
   cudaGraphExec_t exec = nullptr;
-  if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+  if (cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) {
     cudaGraphDestroy(graph);
     cudaGetLastError();
     return IBMLBM_ERR_CUDA;
@@ -1299,7 +1307,14 @@ int ibm_lbm_batch_init(const ibm_lbm_config* cfgs, int32_t n, void* d_workspace,
     if (e_ != cudaSuccess)                                                               \
       return bail(fail(IBMLBM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_))); \
   } while (0)
-  BATCH_TRY(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+  {
+    // the side stream's short particle kernels at the highest priority: the block
+    // scheduler then places their blocks ahead of lbm_step's as SMs free up, so they
+    // finish inside lbm_step's time instead of after it
+    int lo_ = 0, hi_ = 0;
+    BATCH_TRY(cudaDeviceGetStreamPriorityRange(&lo_, &hi_));
+    BATCH_TRY(cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, hi_));
+  }
   BATCH_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
   BATCH_TRY(cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming));
   int maxbox = 0;

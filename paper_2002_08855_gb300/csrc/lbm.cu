@@ -136,13 +136,15 @@ __device__ __forceinline__ NodeCoord node_coord(const Geo& g, int cpr) {
 // ------------------------------------------------------------------ kernels
 
 // IB force of one node.  2D [N][2], read for every node together with the PDFs (one
-// memory latency; a read that first waits for the node mask was measured slower);
-// 3D [N][4], read only on nodes the particle update marked (where it can be non-zero)
+// memory latency; a read that first waits for the node mask was measured slower), and
+// not at all in a run without particles (A.fib null); 3D [N][4], read only on nodes the
+// particle update marked (where it can be non-zero)
 template <class L>
 __device__ __forceinline__ void ib_force(const LbmArgs& A, long long row, int x, long long n,
                                          float (&fv)[3]) {
   fv[0] = fv[1] = fv[2] = 0.0f;
   if (L::dim == 2) {
+    if (!A.fib) return;
     const float2 v = reinterpret_cast<const float2*>(A.fib)[n];
     fv[0] = v.x;
     fv[1] = v.y;

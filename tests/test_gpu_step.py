@@ -78,3 +78,34 @@ def test_cavity_128x256_3_point_delta():
     pg, po = sim.get_particles(), ref.get_particles()
     assert rel_l2(pg["X"] - X0, po["X"] - X0) < 1e-5
     sim.close()
+
+
+def test_periodic_box_particles_crossing_the_edges():
+    """A 64 x 72 box periodic on both axes, three circles (d = 10, 31 points) whose
+    node boxes wrap around the edges and that move across them within 120 steps: the
+    IB force the spreading of one step leaves on the grid, wrapped nodes included, must
+    be gone before the step after next spreads into the same buffer."""
+    require_gpu()
+    from paper_2002_08855_gb300.binding import Simulation
+
+    w = inputs.Workload(name="per", dim=2, nx=64, ny=72, periodic=(1, 1, 0), tau=0.7,
+                        n_particles=3, n_lag=31, diameter=10.0, density_ratio=1.5,
+                        gravity=(0.0, -1e-5, 0.0), mdf_iters=3)
+    X0 = np.array([[62.9, 20.4], [30.2, 0.6], [0.8, 71.0]])
+    U0 = np.array([[0.04, 0.01], [-0.01, -0.05], [-0.03, 0.035]])
+    Om0 = np.array([[1e-3], [-2e-3], [5e-4]])
+    sim = Simulation(w, X0)
+    sim.set_particles(X0, U=U0, Omega=Om0)
+    ref = oracle.Sim(w.as_dict(), X0)
+    ref.set_particles(X0, U=U0, Omega=Om0)
+    sim.step(120)
+    ref.step(120)
+    _, ug = sim.get_fields()
+    _, uo = ref.get_fields()
+    pg, po = sim.get_particles(), ref.get_particles()
+    # each circle crossed an edge (its centre wrapped)
+    assert pg["X"][0, 0] < 10.0 and pg["X"][2, 1] < 10.0 and pg["X"][1, 1] > 60.0
+    assert rel_l2(ug.cpu().numpy(), uo) < 1e-5
+    assert rel_l2(pg["X"], po["X"]) < 1e-6
+    assert rel_l2(pg["U"], po["U"]) < 1e-5
+    sim.close()
