@@ -303,6 +303,35 @@ ibm_lbm_handle* ibm_lbm_batch_member(ibm_lbm_batch* b, int32_t i);
 /* Kernels the batch has launched so far. */
 int64_t ibm_lbm_batch_launch_count(const ibm_lbm_batch* b);
 
+/* Tile shapes of a batch's fused collide-stream launch (Eq. 1, 4-8; the work items are
+ * (member, tile) pairs).  Shape 0: a block of 128 threads takes 128 K consecutive nodes
+ * of one row (K = 1 for FP32, 2 for FP16).  Shapes >= 1: the rows of each member are
+ * cut into segments of 32 K nodes, one per warp, and a block takes W consecutive
+ * segments (a tile can span several short rows); a persistent shape launches as many
+ * blocks as the GPU holds at once and walks the tiles with a grid stride, the others
+ * one block per tile.  Every shape updates every node with the same arithmetic, so the
+ * results do not depend on the shape.  ibm_lbm_tile_shape reports shape's K, W and
+ * whether it is persistent for the given storage (IBMLBM_PDF_FP32 or _FP16; shape 0
+ * reports W = 4).  Errors: INVALID_ARG for an unknown shape or storage. */
+int ibm_lbm_tile_shape_count(void);
+int ibm_lbm_tile_shape(int32_t shape, int32_t pdf_storage, int32_t* nodes_per_thread,
+                       int32_t* warps_per_block, int32_t* persistent);
+
+/* Use tile shape `shape` from the next step on (a new batch uses shape 0).  Errors:
+ * INVALID_ARG for an unknown shape. */
+int ibm_lbm_batch_set_tile_shape(ibm_lbm_batch* b, int32_t shape);
+int ibm_lbm_batch_get_tile_shape(const ibm_lbm_batch* b, int32_t* shape);
+
+/* Autotuner: run steps_per_shape real steps of the batch (even, >= 2, so both AA
+ * parities count alike) with each tile shape in turn, timing the collide-stream launches
+ * with CUDA events, and keep the shape with the least mean time per step.  The steps
+ * advance the simulation like ibm_lbm_batch_step (shapes do not change results), run
+ * as eager launches, and the next ibm_lbm_batch_step captures new graphs.  Blocks
+ * until the tuning steps are done.  h_ms_per_shape (host, ibm_lbm_tile_shape_count()
+ * floats, or NULL) receives each shape's mean milliseconds per step.  Errors:
+ * INVALID_ARG for a bad steps_per_shape; CUDA when a launch or an event fails. */
+int ibm_lbm_batch_autotune(ibm_lbm_batch* b, int32_t steps_per_shape, float* h_ms_per_shape);
+
 /* Destroy the batch and its member handles (never fails). */
 void ibm_lbm_batch_destroy(ibm_lbm_batch* b);
 

@@ -125,6 +125,11 @@ SIGNATURES = {
     "ibm_lbm_batch_sync": (C.c_int, [_vp]),
     "ibm_lbm_batch_member": (_vp, [_vp, C.c_int32]),
     "ibm_lbm_batch_launch_count": (C.c_int64, [_vp]),
+    "ibm_lbm_tile_shape_count": (C.c_int, []),
+    "ibm_lbm_tile_shape": (C.c_int, [C.c_int32, C.c_int32, _ip, _ip, _ip]),
+    "ibm_lbm_batch_set_tile_shape": (C.c_int, [_vp, C.c_int32]),
+    "ibm_lbm_batch_get_tile_shape": (C.c_int, [_vp, _ip]),
+    "ibm_lbm_batch_autotune": (C.c_int, [_vp, C.c_int32, _fp]),
     "ibm_lbm_batch_destroy": (None, [_vp]),
 }
 
@@ -357,6 +362,18 @@ class BatchMember(Simulation):
         self.h = C.c_void_p(None)  # owned by the batch
 
 
+def tile_shapes(pdf_storage: int = 0) -> list:
+    """(nodes per thread, warps per block, persistent) of each lbm_step tile shape of a
+    batch, by shape index."""
+    out = []
+    for sh in range(lib().ibm_lbm_tile_shape_count()):
+        k, w, p = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+        _check(lib().ibm_lbm_tile_shape(sh, int(pdf_storage), C.byref(k), C.byref(w), C.byref(p)),
+               "tile_shape")
+        out.append((k.value, w.value, p.value))
+    return out
+
+
 class Batch:
     """Many independent 2D cavities stepped together (fused launches, one CUDA graph
     per step parity).  members[i] gives the field and particle calls of member i."""
@@ -395,6 +412,22 @@ class Batch:
 
     def launch_count(self) -> int:
         return int(lib().ibm_lbm_batch_launch_count(self.h))
+
+    def set_tile_shape(self, shape: int):
+        _check(lib().ibm_lbm_batch_set_tile_shape(self.h, int(shape)), "batch_set_tile_shape")
+
+    def tile_shape(self) -> int:
+        v = C.c_int32(0)
+        _check(lib().ibm_lbm_batch_get_tile_shape(self.h, C.byref(v)), "batch_get_tile_shape")
+        return v.value
+
+    def autotune(self, steps_per_shape: int = 2) -> tuple:
+        """Time every tile shape on steps_per_shape real steps; keep the fastest.
+        Returns (chosen shape, mean ms per step of each shape's collide-stream launches)."""
+        ms = np.zeros(lib().ibm_lbm_tile_shape_count(), dtype=np.float32)
+        _check(lib().ibm_lbm_batch_autotune(self.h, int(steps_per_shape), _ptr(ms, C.c_float)),
+               "batch_autotune")
+        return self.tile_shape(), [float(v) for v in ms]
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -1130,10 +1131,12 @@ size_t batch_table_bytes(const ibm_lbm_config* cfgs, int32_t n) {
     const Derived d = derive(&cfgs[i]);
     for (int t = 0; t < BK_COUNT; ++t) blocks += member_blocks(t, d, cfgs[i]);
   }
-  // args: Lbm x2, Ibm x2, Regen x2, Pair x4 per member; maps: first[] per type, cav[] per block
+  // args: Lbm x2, Ibm x2, Regen x2, Pair x4 per member; maps: first[] per type, cav[] per
+  // block, and a tile prefix table [n + 1] per lbm_step tile shape (each table padded to 16 bytes)
   const size_t args = (size_t)n * (2 * sizeof(LbmArgs) + 2 * sizeof(IbmArgs) + 2 * sizeof(RegenArgs) +
                                    4 * sizeof(PairArgs));
-  return args + sizeof(int) * (blocks + (size_t)BK_COUNT * n) + 4096;
+  const size_t tiles = (size_t)tile_shape_count() * (sizeof(int) * (n + 1) + 16);
+  return args + sizeof(int) * (blocks + (size_t)BK_COUNT * n) + tiles + 4096;
 }
 
 BatchPlan plan_batch(const ibm_lbm_config* cfgs, int32_t n) {
@@ -1150,6 +1153,8 @@ BatchPlan plan_batch(const ibm_lbm_config* cfgs, int32_t n) {
 }
 
 }  // namespace
+
+constexpr int kMaxTileShapes = 16;
 
 struct ibm_lbm_batch {
   int n;
@@ -1170,6 +1175,11 @@ struct ibm_lbm_batch {
   PairArgs* pair_args[2][2];     // [parity][have_prev]
   int* first[BK_COUNT];
   int* cav[BK_COUNT];
+  // lbm_step tile shape (0: row tiles through the block map; >= 1: warp tiles through
+  // a per-shape prefix table of the members' tile counts)
+  int shape;
+  int* tile_first[kMaxTileShapes];
+  int tile_total[kMaxTileShapes];
   long long step;
   int have_prev;
   int64_t launches;
@@ -1182,7 +1192,8 @@ namespace {
 
 Fuse fuse(const ibm_lbm_batch* b, int type, const void* args) { return Fuse{args, b->cav[type], b->first[type]}; }
 
-int enqueue_batch_step(ibm_lbm_batch* b, int parity, int have_prev, int* nk) {
+// ev (or null): events recorded around the lbm_step launches (tile-shape tuning)
+int enqueue_batch_step(ibm_lbm_batch* b, int parity, int have_prev, int* nk, cudaEvent_t* ev = nullptr) {
   const cudaStream_t s = b->s;
   int k = 0;
   const unsigned* B = b->blocks;
@@ -1212,8 +1223,14 @@ int enqueue_batch_step(ibm_lbm_batch* b, int parity, int have_prev, int* nk) {
     CUDA_TRY(cudaEventRecord(b->join, b->side));
   }
   const void* la = b->lbm_args[parity];
-  CUDA_TRY(launch_lbm_step_fused(fuse(b, BK_LBM, la), B[BK_LBM], fuse(b, BK_EDGE, la), B[BK_EDGE], b->store,
-                                 parity, s));
+  if (ev) CUDA_TRY(cudaEventRecord(ev[0], s));
+  if (b->shape == 0)
+    CUDA_TRY(launch_lbm_step_fused(fuse(b, BK_LBM, la), B[BK_LBM], fuse(b, BK_EDGE, la), B[BK_EDGE], b->store,
+                                   parity, s));
+  else
+    CUDA_TRY(launch_lbm_step_tiles(b->shape, b->lbm_args[parity], b->tile_first[b->shape], b->n,
+                                   b->tile_total[b->shape], fuse(b, BK_EDGE, la), B[BK_EDGE], b->store, parity, s));
+  if (ev) CUDA_TRY(cudaEventRecord(ev[1], s));
   k += (parity == 1 && B[BK_EDGE]) ? 2 : 1;
   if (B[BK_WARP]) CUDA_TRY(cudaStreamWaitEvent(s, b->join, 0));
   *nk = k;
@@ -1368,6 +1385,20 @@ int ibm_lbm_batch_init(const ibm_lbm_config* cfgs, int32_t n, void* d_workspace,
     o_first[t] = put(first.data(), sizeof(int) * n);
     o_cav[t] = cav.empty() ? o : put(cav.data(), sizeof(int) * cav.size());
   }
+  size_t o_tile[kMaxTileShapes] = {};
+  b->shape = 0;
+  for (int sh = 1; sh < tile_shape_count(); ++sh) {
+    std::vector<int> first(n + 1, 0);
+    long long tot = 0;
+    for (int32_t i = 0; i < n; ++i) {
+      first[i] = (int)tot;
+      tot += tile_count(b->m[i]->d.g, sh);
+    }
+    if (tot > INT32_MAX) return bail(fail(IBMLBM_ERR_UNSUPPORTED, "batch too large for the tile tables"));
+    first[n] = (int)tot;
+    b->tile_total[sh] = (int)tot;
+    o_tile[sh] = put(first.data(), sizeof(int) * (n + 1));
+  }
   if (o > host.size()) return bail(fail(IBMLBM_ERR_WORKSPACE, "batch tables overflow"));
   char* dt = ws + plan.tables;
   BATCH_TRY(cudaMemcpyAsync(dt, host.data(), o, cudaMemcpyHostToDevice, b->s));
@@ -1382,10 +1413,35 @@ int ibm_lbm_batch_init(const ibm_lbm_config* cfgs, int32_t n, void* d_workspace,
     b->first[t] = reinterpret_cast<int*>(dt + o_first[t]);
     b->cav[t] = reinterpret_cast<int*>(dt + o_cav[t]);
   }
+  for (int sh = 1; sh < tile_shape_count(); ++sh) b->tile_first[sh] = reinterpret_cast<int*>(dt + o_tile[sh]);
 #undef BATCH_TRY
   *out = b;
   return IBMLBM_OK;
 }
+
+}  // extern "C"
+
+namespace {
+
+void advance_batch(ibm_lbm_batch* b) {
+  b->step += 1;
+  b->have_prev = 1;
+  for (ibm_lbm_handle* h : b->m) {  // the members' own clocks (their I/O reads by parity)
+    h->step += 1;
+    h->have_prev = 1;
+  }
+}
+
+void drop_batch_graphs(ibm_lbm_batch* b) {
+  for (int p = 0; p < 2; ++p) {
+    if (b->graph_ok[p]) cudaGraphExecDestroy(b->graph[p]);
+    b->graph_ok[p] = b->graph_tried[p] = false;
+  }
+}
+
+}  // namespace
+
+extern "C" {
 
 int ibm_lbm_batch_step(ibm_lbm_batch* b, int32_t n_steps) {
   if (!b) return fail(IBMLBM_ERR_INVALID_ARG, "batch is NULL");
@@ -1405,14 +1461,83 @@ int ibm_lbm_batch_step(ibm_lbm_batch* b, int32_t n_steps) {
       if (rc) return rc;
       b->launches += nk;
     }
-    b->step += 1;
-    b->have_prev = 1;
-    for (ibm_lbm_handle* h : b->m) {  // the members' own clocks (their I/O reads by parity)
-      h->step += 1;
-      h->have_prev = 1;
-    }
+    advance_batch(b);
   }
   return IBMLBM_OK;
+}
+
+int ibm_lbm_tile_shape_count(void) { return tile_shape_count(); }
+
+int ibm_lbm_tile_shape(int32_t shape, int32_t pdf_storage, int32_t* nodes_per_thread,
+                       int32_t* warps_per_block, int32_t* persistent) {
+  if (shape < 0 || shape >= tile_shape_count()) return fail(IBMLBM_ERR_INVALID_ARG, "no such tile shape");
+  if (pdf_storage != IBMLBM_PDF_FP32 && pdf_storage != IBMLBM_PDF_FP16)
+    return fail(IBMLBM_ERR_INVALID_ARG, "a batch stores FP32 or FP16");
+  int k = 0, w = 0, p = 0;
+  tile_shape(shape, pdf_storage, &k, &w, &p);
+  if (nodes_per_thread) *nodes_per_thread = k;
+  if (warps_per_block) *warps_per_block = w;
+  if (persistent) *persistent = p;
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_batch_set_tile_shape(ibm_lbm_batch* b, int32_t shape) {
+  if (!b) return fail(IBMLBM_ERR_INVALID_ARG, "batch is NULL");
+  if (shape < 0 || shape >= tile_shape_count()) return fail(IBMLBM_ERR_INVALID_ARG, "no such tile shape");
+  if (shape != b->shape) {
+    b->shape = shape;
+    drop_batch_graphs(b);  // captured with the old shape
+  }
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_batch_get_tile_shape(const ibm_lbm_batch* b, int32_t* shape) {
+  if (!b || !shape) return fail(IBMLBM_ERR_INVALID_ARG, "batch or shape is NULL");
+  *shape = b->shape;
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_batch_autotune(ibm_lbm_batch* b, int32_t steps_per_shape, float* h_ms_per_shape) {
+  if (!b) return fail(IBMLBM_ERR_INVALID_ARG, "batch is NULL");
+  if (steps_per_shape < 2 || steps_per_shape % 2 != 0)
+    return fail(IBMLBM_ERR_INVALID_ARG, "steps_per_shape must be even and >= 2");
+  const int S = tile_shape_count();
+  std::vector<cudaEvent_t> ev((size_t)2 * S * steps_per_shape, nullptr);
+  auto done = [&](int code) {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    return code;
+  };
+  for (cudaEvent_t& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return done(fail(IBMLBM_ERR_CUDA, "cudaEventCreate failed"));
+  drop_batch_graphs(b);
+  for (int sh = 0; sh < S; ++sh) {
+    b->shape = sh;
+    for (int j = 0; j < steps_per_shape; ++j) {
+      int nk = 0;
+      const int rc = enqueue_batch_step(b, (int)(b->step & 1), b->have_prev, &nk,
+                                        &ev[(size_t)2 * (sh * steps_per_shape + j)]);
+      if (rc) return done(rc);
+      b->launches += nk;
+      advance_batch(b);
+    }
+  }
+  if (cudaStreamSynchronize(b->s) != cudaSuccess) return done(fail(IBMLBM_ERR_CUDA, "tuning steps failed"));
+  int best = 0;
+  std::vector<float> ms(S, 0.0f);
+  for (int sh = 0; sh < S; ++sh) {
+    for (int j = 0; j < steps_per_shape; ++j) {
+      float t = 0.0f;
+      const size_t e = (size_t)2 * (sh * steps_per_shape + j);
+      if (cudaEventElapsedTime(&t, ev[e], ev[e + 1]) != cudaSuccess)
+        return done(fail(IBMLBM_ERR_CUDA, "cudaEventElapsedTime failed"));
+      ms[sh] += t / steps_per_shape;
+    }
+    if (ms[sh] < ms[best]) best = sh;
+  }
+  b->shape = best;
+  if (h_ms_per_shape) std::copy(ms.begin(), ms.end(), h_ms_per_shape);
+  return done(IBMLBM_OK);
 }
 
 int ibm_lbm_batch_sync(ibm_lbm_batch* b) {

@@ -36,6 +36,11 @@ cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t s);
 // launches; see Fuse in common.cuh)
 unsigned lbm_step_blocks(const Geo& g, int store);
 unsigned lbm_edge_blocks(const Geo& g, int D);
+int tile_shape_count();
+void tile_shape(int s, int store, int* k, int* w, int* persist);
+int tile_count(const Geo& g, int s);
+cudaError_t launch_lbm_step_tiles(int shape, const LbmArgs* args, const int* first, int n, int total,
+                                  const Fuse& FE, unsigned eblocks, int store, int parity, cudaStream_t s);
 cudaError_t launch_lbm_step_fused(const Fuse& F, unsigned blocks, const Fuse& FE, unsigned eblocks,
                                   int store, int parity, cudaStream_t s);
 size_t ibm_box2_smem(int box);

@@ -10,6 +10,8 @@
 //     writes f*_a to a[a][x + e_a], or to a[opp(a)][x] when x + e_a lies beyond a wall.
 // Each node reads and writes the same set of slots, so no two nodes race and one
 // copy of the PDFs suffices (the role the swap algorithm of Sec. 3.3 plays on a CPU).
+#include <algorithm>
+
 #include "common.cuh"
 #include "launch.h"
 #include "pdf_access.cuh"
@@ -187,25 +189,18 @@ __device__ __forceinline__ bool odd_edge_row(const Geo& g, int y, int z) {
   return y == 0 || y == g.ny - 1 || (L::dim == 3 && (z == 0 || z == g.nz - 1));
 }
 
-// One full time step (Eq. 1, 4-8, 17-18) of K adjacent nodes per thread: read the
-// nodes' PDFs (AA parity) and IB force, collide, store in place.  All K nodes' loads are
-// issued before any store, so a thread keeps K nodes' bytes in flight (K = 2 for the
-// 16-bit storages, whose requests are half as large).  In an odd step the nodes whose
-// neighbourhood crosses a domain face (rows on a y or z face, the first and last node
-// of a row) are left to lbm_step_edge_kernel, so every node here uses fixed neighbour
-// offsets; the AA pattern makes the nodes independent of each other.  The even step
-// is local everywhere.
-template <class L, int PARITY, int ST, int K, bool FUSED>
-__global__ void __launch_bounds__(kLbmBlock) lbm_step_kernel(LbmArgs A0, int spr0, Fuse FU) {
-  IBMLBM_BIND(FUSED, LbmArgs, A, A0, FU, blk);
+// One full time step (Eq. 1, 4-8, 17-18) of the K adjacent nodes x0 .. x0 + K - 1 of a
+// row: read the nodes' PDFs (AA parity) and IB force, collide, store in place.  All K
+// nodes' loads are issued before any store, so a thread keeps K nodes' bytes in flight
+// (K = 2 suits the 16-bit storages, whose requests are half as large).  In an odd step
+// the nodes whose neighbourhood crosses a domain face (rows on a y or z face, the first
+// and last node of a row) are left to lbm_step_edge_kernel, so every node here uses
+// fixed neighbour offsets; the AA pattern makes the nodes independent of each other.
+// The even step is local everywhere.
+template <class L, int PARITY, int ST, int K>
+__device__ __forceinline__ void step_row_nodes(const LbmArgs& A, long long row, int y, int z, int x0) {
   const Geo& g = A.g;
-  const int spr = FUSED ? (g.nx + K * kLbmBlock - 1) / (K * kLbmBlock) : spr0;
-  const unsigned b = blk, uspr = (unsigned)spr, uny = (unsigned)g.ny;
-  const unsigned row = b / uspr, seg = b - row * uspr;
-  const unsigned uz = row / uny;
-  const int y = (int)(row - uz * uny), z = (int)uz;
   if (PARITY == 1 && odd_edge_row<L>(g, y, z)) return;
-  const int x0 = K * ((int)seg * kLbmBlock + (int)threadIdx.x);
   float fa[K][L::Q], fv[K][3];
   bool act[K];
 #pragma unroll
@@ -228,6 +223,49 @@ __global__ void __launch_bounds__(kLbmBlock) lbm_step_kernel(LbmArgs A0, int spr
     collide<L>(fa[k], F, A.omega, A.kforce);
     store_post<L, PARITY, ST, PARITY == 1>(g, A.f, x, y, z, n, fa[k]);
     ib_force_clear<L>(A, n, fv[k]);
+  }
+}
+
+// Row tiles: a block of kLbmBlock threads takes K * kLbmBlock consecutive nodes of one
+// row (spr blocks per row).
+template <class L, int PARITY, int ST, int K, bool FUSED>
+__global__ void __launch_bounds__(kLbmBlock) lbm_step_kernel(LbmArgs A0, int spr0, Fuse FU) {
+  IBMLBM_BIND(FUSED, LbmArgs, A, A0, FU, blk);
+  const Geo& g = A.g;
+  const int spr = FUSED ? (g.nx + K * kLbmBlock - 1) / (K * kLbmBlock) : spr0;
+  const unsigned b = blk, uspr = (unsigned)spr, uny = (unsigned)g.ny;
+  const unsigned row = b / uspr, seg = b - row * uspr;
+  const unsigned uz = row / uny;
+  step_row_nodes<L, PARITY, ST, K>(A, row, (int)(row - uz * uny), (int)uz,
+                                   K * ((int)seg * kLbmBlock + (int)threadIdx.x));
+}
+
+// Warp tiles over the members of a 2D batch: the rows of a member are cut into
+// segments of 32 K nodes, one per warp, and a tile is W consecutive segments of the
+// member's row-major segment sequence (so a tile can span short rows).  Tile t of the
+// launch belongs to the member m with first[m] <= t < first[m + 1].  PERSIST: a grid
+// of as many blocks as fit on the GPU at once walks the tiles with a grid stride;
+// otherwise one block per tile.
+template <int PARITY, int ST, int K, int W, bool PERSIST>
+__global__ void __launch_bounds__(32 * W) lbm_step_tiles_kernel(const LbmArgs* __restrict__ args,
+                                                                const int* __restrict__ first, int n,
+                                                                int total) {
+  using L = Lat<2>;
+  const int lane = (int)(threadIdx.x & 31), warp = (int)(threadIdx.x >> 5);
+  for (int t = (int)blockIdx.x; t < total; t += PERSIST ? (int)gridDim.x : total) {
+    int lo = 0, hi = n - 1;  // the member: the last m with first[m] <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(first + mid) <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const LbmArgs A = args[lo];  // local copy: fields loaded once, not after every store
+    const int spr = (A.g.nx + 32 * K - 1) / (32 * K);
+    const long long item = (long long)(t - __ldg(first + lo)) * W + warp;
+    const long long row = item / spr;
+    if (row >= A.g.rows) continue;  // past the member's last row (its last tile)
+    const int seg = (int)(item - row * spr);
+    step_row_nodes<L, PARITY, ST, K>(A, row, (int)row, 0, K * (seg * 32 + lane));
   }
 }
 
@@ -456,6 +494,86 @@ cudaError_t launch_lbm_step_fused(const Fuse& F, unsigned blocks, const Fuse& FE
     if (parity == 0) IBMLBM_STEPF(0, STORE_F16); else IBMLBM_STEPF(1, STORE_F16);
   }
 #undef IBMLBM_STEPF
+  return cudaGetLastError();
+}
+
+// Tile shapes of a batch's fused lbm_step: shape 0 is the row-tile kernel above (K = 1
+// for FP32, 2 for FP16, kLbmBlock threads), shapes 1.. are warp tiles (K nodes per
+// thread, W warps per block, persistent grid or one block per tile).
+struct TileShape {
+  int k, w, persist;
+};
+constexpr TileShape kTileShapes[] = {{0, 0, 0}, {1, 4, 0}, {1, 8, 0}, {2, 4, 0},
+                                     {1, 4, 1}, {1, 8, 1}, {2, 4, 1}};
+constexpr int kTileShapeCount = (int)(sizeof(kTileShapes) / sizeof(kTileShapes[0]));
+
+int tile_shape_count() { return kTileShapeCount; }
+
+void tile_shape(int s, int store, int* k, int* w, int* persist) {
+  const TileShape& t = kTileShapes[s];
+  *k = s == 0 ? (store == STORE_F32 ? 1 : 2) : t.k;
+  *w = s == 0 ? kLbmBlock / 32 : t.w;
+  *persist = t.persist;
+}
+
+// warp tiles of one member for shape s >= 1
+int tile_count(const Geo& g, int s) {
+  const TileShape& t = kTileShapes[s];
+  const long long spr = (g.nx + 32 * t.k - 1) / (32 * t.k);
+  return (int)((spr * g.rows + t.w - 1) / t.w);
+}
+
+template <int PARITY, int ST, int K, int W, bool PERSIST>
+static cudaError_t launch_tiles(const LbmArgs* args, const int* first, int n, int total, cudaStream_t s) {
+  auto kern = lbm_step_tiles_kernel<PARITY, ST, K, W, PERSIST>;
+  unsigned grid = (unsigned)total;
+  if (PERSIST) {
+    static int resident = 0;  // blocks of this kernel the GPU holds at once
+    if (resident == 0) {
+      int dev = 0, sms = 0, per_sm = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * W, 0);
+      if (e != cudaSuccess) return e;
+      resident = std::max(1, sms * per_sm);
+    }
+    grid = (unsigned)std::min(total, resident);
+  }
+  kern<<<grid, 32 * W, 0, s>>>(args, first, n, total);
+  return cudaSuccess;
+}
+
+template <int PARITY, int ST>
+static cudaError_t launch_tiles_shape(int shape, const LbmArgs* args, const int* first, int n, int total,
+                                      cudaStream_t s) {
+  switch (shape) {
+    case 1: return launch_tiles<PARITY, ST, 1, 4, false>(args, first, n, total, s);
+    case 2: return launch_tiles<PARITY, ST, 1, 8, false>(args, first, n, total, s);
+    case 3: return launch_tiles<PARITY, ST, 2, 4, false>(args, first, n, total, s);
+    case 4: return launch_tiles<PARITY, ST, 1, 4, true>(args, first, n, total, s);
+    case 5: return launch_tiles<PARITY, ST, 1, 8, true>(args, first, n, total, s);
+    default: return launch_tiles<PARITY, ST, 2, 4, true>(args, first, n, total, s);
+  }
+}
+
+// fused lbm_step of a batch with warp-tile shape >= 1 (the edge kernel as for shape 0)
+cudaError_t launch_lbm_step_tiles(int shape, const LbmArgs* args, const int* first, int n, int total,
+                                  const Fuse& FE, unsigned eblocks, int store, int parity, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (total > 0) {
+    if (store == STORE_F32)
+      e = parity == 0 ? launch_tiles_shape<0, STORE_F32>(shape, args, first, n, total, s)
+                      : launch_tiles_shape<1, STORE_F32>(shape, args, first, n, total, s);
+    else
+      e = parity == 0 ? launch_tiles_shape<0, STORE_F16>(shape, args, first, n, total, s)
+                      : launch_tiles_shape<1, STORE_F16>(shape, args, first, n, total, s);
+  }
+  if (e != cudaSuccess) return e;
+  const LbmArgs none{};
+  if (parity == 1 && eblocks) {
+    if (store == STORE_F32) lbm_step_edge_kernel<Lat<2>, STORE_F32, true><<<eblocks, kLbmBlock, 0, s>>>(none, 0, 0, FE);
+    else lbm_step_edge_kernel<Lat<2>, STORE_F16, true><<<eblocks, kLbmBlock, 0, s>>>(none, 0, 0, FE);
+  }
   return cudaGetLastError();
 }
 

@@ -96,3 +96,68 @@ def test_ensemble_256_cavities_steps():
     p, u = batch.members[17].get_fields()
     assert np.isfinite(u.cpu().numpy()).all()
     batch.close()
+
+
+def _flow_members(storage):
+    """Particle-free members of assorted shapes (short rows, a single row, a one-node
+    cavity, periodic axes) with random PDFs and a body force: the collide-stream
+    launch alone decides their state, and it has no atomics, so it is deterministic."""
+    from paper_2002_08855_gb300.inputs import random_pdfs
+
+    shapes = [(64, 64, (0, 0, 0)), (65, 3, (1, 0, 0)), (1, 1, (0, 0, 0)), (2, 7, (0, 1, 0)),
+              (130, 90, (0, 0, 0)), (512, 33, (1, 1, 0)), (33, 1, (1, 0, 0)), (97, 101, (0, 0, 0))]
+    ws = [Workload(name=f"f{i}", dim=2, nx=nx, ny=ny, periodic=per, tau=0.55 + 0.05 * (i % 3),
+                   body_force=(1e-5, -2e-5, 0.0), pdf_storage=storage, seed=40 + i)
+          for i, (nx, ny, per) in enumerate(shapes)]
+    f0 = [random_pdfs(9, w.n_grid, seed=70 + i, scale=1e-2) for i, w in enumerate(ws)]
+    return ws, f0
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_tile_shapes_update_every_node_identically(storage):
+    """Every collide-stream tile shape (row tiles, warp tiles of 32 K nodes, W warps per
+    block, persistent or not) gives the same PDFs bit for bit, over both AA parities."""
+    require_gpu()
+    from paper_2002_08855_gb300.binding import Batch, tile_shapes
+
+    ws, f0 = _flow_members(storage)
+    out = []
+    for sh in range(len(tile_shapes(storage))):
+        batch = Batch(ws, [None] * len(ws))
+        for m, f in zip(batch.members, f0):
+            m.set_pdfs(f)
+        batch.set_tile_shape(sh)
+        batch.step(7)
+        batch.sync()
+        assert batch.tile_shape() == sh
+        out.append([m.get_pdfs().cpu().numpy() for m in batch.members])
+        batch.close()
+    for sh in range(1, len(out)):
+        for i, (a, b) in enumerate(zip(out[0], out[sh])):
+            assert np.array_equal(a, b), (sh, ws[i].name)
+
+
+def test_autotune_picks_the_fastest_shape_and_keeps_the_results():
+    """The autotuner's steps are real steps: after tuning and ten more steps every
+    member equals its run alone after the same number of steps."""
+    require_gpu()
+    from paper_2002_08855_gb300.binding import Batch, Simulation, tile_shapes
+
+    ws, Xs = _members()
+    batch = Batch(ws, Xs)
+    batch.step(2)
+    chosen, ms = batch.autotune(4)
+    assert len(ms) == len(tile_shapes(0)) and min(ms) > 0.0
+    assert chosen == int(np.argmin(ms))
+    batch.step(10)
+    batch.sync()
+    steps = 2 + 4 * len(ms) + 10
+    for w, X, m in zip(ws, Xs, batch.members):
+        alone = Simulation(w, X)
+        alone.step(steps)
+        alone.sync()
+        _, ub = m.get_fields()
+        _, ua = alone.get_fields()
+        assert rel_l2(ub.cpu().numpy(), ua.cpu().numpy()) < 1e-6, w.name
+        alone.close()
+    batch.close()
