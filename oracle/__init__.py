@@ -50,7 +50,7 @@ class Params(C.Structure):
         ("delta_kind", C.c_int32), ("drs", C.c_double), ("mdf_iters", C.c_int32),
         ("density_ratio", C.c_double), ("gravity", C.c_double * 3),
         ("zeta", C.c_double), ("eps_pp", C.c_double), ("E_pp", C.c_double),
-        ("fixed_particles", C.c_int32),
+        ("fixed_particles", C.c_int32), ("boundary", C.c_int32), ("u_inlet", C.c_double),
     ]
 
 
@@ -82,6 +82,8 @@ def make_params(cfg) -> Params:
     P.eps_pp = float(get("eps_pp", 1e-2))
     P.E_pp = float(get("E_pp", 1e-4))
     P.fixed_particles = int(get("fixed_particles", 0))
+    P.boundary = int(get("boundary", 0))
+    P.u_inlet = float(get("u_inlet", 0.0))
     return P
 
 

@@ -48,6 +48,17 @@
  *      with the squared distance summed in axis order without fused multiply-add.
  *   R12 step order: macro -> IBM (MDF) -> collide -> stream -> pair force ->
  *      particle update, explicit coupling (U_b uses U_c of the current step).
+ *   R13 non-equilibrium extrapolation (boundary 1, 2; Sec. 6.1-6.2 cite it as their
+ *      ref. [48] without formulas): the wall lies on the outermost node x_b of every
+ *      non-periodic axis.  After streaming, f_a(x_b) = f_a^eq(p_b, u_b) + f_a(x_f) -
+ *      f_a^eq(p_f, u_f), with x_f = x_b + (the sum of the inward normals of the faces
+ *      x_b lies on) and (p_f, u_f) the pressure and velocity of x_f (Eq. 5-7 with the
+ *      fluid body force: the next step's IB force is not known yet).  Walls: u_b = 0,
+ *      p_b = p_f.  Channel (boundary 2): inlet face y = 0 with u_b along y equal to
+ *      u_inlet times prod_k 4 c_k (L_k - c_k) / L_k^2 over the other non-periodic axes
+ *      (L_k = n_k - 1) and p_b = p_f; outlet face y = ny - 1 with p_b = 0, u_b = u_f.
+ *      A node on both a wall face and an inlet or outlet face is a wall node.  The
+ *      mirror images of R10 then reflect through the boundary nodes (0 and n - 1).
  */
 #include "ibmlbm_oracle.h"
 
@@ -525,8 +536,10 @@ void or_contact_forces(const or_params* P, int64_t n, const double* X, double* F
       int s, m;
       if (P->periodic[k]) continue;
       for (s = 0; s < 2; ++s) {
-        /* wall at -1/2 (s = 0) or n - 1/2 (s = 1): image mirrored through the wall */
-        double wall = (s == 0) ? -0.5 : axis_length(P, k) - 0.5;
+        /* wall at -1/2 (s = 0) or n - 1/2 (s = 1), on the nodes 0 and n - 1 with the
+         * extrapolation boundaries (R13): image mirrored through the wall */
+        double lo = P->boundary ? 0.0 : -0.5;
+        double wall = (s == 0) ? lo : axis_length(P, k) - 1.0 - lo;
         for (m = 0; m < 3; ++m) img[m] = X[3 * i + m];
         img[k] = 2.0 * wall - X[3 * i + k];
         or_pair_force(P, c, &X[3 * i], img, F);
@@ -841,6 +854,60 @@ static void move_particles(or_sim* S) {
   S->have_prev = 1;
 }
 
+/* R13: non-equilibrium extrapolation on the boundary nodes, after streaming. */
+static void extrapolation_boundaries(or_sim* S) {
+  const or_params* P = &S->P;
+  const int n[3] = {P->nx, P->ny, P->nz};
+  int x, y, z, k, a;
+  for (z = 0; z < n[2]; ++z)
+    for (y = 0; y < n[1]; ++y)
+      for (x = 0; x < n[0]; ++x) {
+        int c[3], cf[3], on = 0, wall = 0, inlet = 0;
+        double fn[19], eqf[19], eqb[19], us[3], uf[3], ub[3] = {0.0, 0.0, 0.0}, pf, pb;
+        long nb, nf;
+        c[0] = x; c[1] = y; c[2] = z;
+        for (k = 0; k < 3; ++k) {
+          int lo, hi;
+          cf[k] = c[k];
+          if (k >= P->dim || P->periodic[k]) continue;
+          lo = c[k] == 0;
+          hi = c[k] == n[k] - 1;
+          if (!lo && !hi) continue;
+          on = 1;
+          cf[k] = lo ? c[k] + 1 : c[k] - 1;
+          if (P->boundary == 2 && k == 1) {
+            if (lo) inlet = 1;
+          } else {
+            wall = 1;
+          }
+        }
+        if (!on) continue;
+        nb = node_index(n[0], n[1], c[0], c[1], c[2]);
+        nf = node_index(n[0], n[1], cf[0], cf[1], cf[2]);
+        for (a = 0; a < S->L.q; ++a) fn[a] = S->f[(long)a * S->N + nf];
+        macro_node(&S->L, fn, P->body_force, us, uf, &pf);
+        feq_node(&S->L, pf, uf, eqf);
+        if (wall) {
+          pb = pf;
+        } else if (inlet) {
+          double prof = P->u_inlet;
+          for (k = 0; k < P->dim; ++k) {
+            double L;
+            if (k == 1 || P->periodic[k]) continue;
+            L = n[k] - 1.0;
+            prof *= 4.0 * c[k] * (L - c[k]) / (L * L);
+          }
+          ub[1] = prof;
+          pb = pf;
+        } else { /* outlet */
+          for (k = 0; k < 3; ++k) ub[k] = uf[k];
+          pb = 0.0;
+        }
+        feq_node(&S->L, pb, ub, eqb);
+        for (a = 0; a < S->L.q; ++a) S->f[(long)a * S->N + nb] = eqb[a] + fn[a] - eqf[a];
+      }
+}
+
 /* One time step in the order of R12 (the step list after Eq. 18 and Sec. 6 part list). */
 void or_step(or_sim* S, int32_t nsteps) {
   int32_t s;
@@ -850,6 +917,7 @@ void or_step(or_sim* S, int32_t nsteps) {
     ibm_mdf(S);
     collide(S);
     or_stream_push(S->P.dim, S->P.nx, S->P.ny, S->P.nz, S->P.periodic, S->fp, S->f);
+    if (S->P.boundary) extrapolation_boundaries(S);
     move_particles(S);
   }
 }

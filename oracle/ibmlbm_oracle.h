@@ -48,6 +48,12 @@ typedef struct or_params {
   double gravity[3];        /* g acting on particles                             */
   double zeta, eps_pp, E_pp;/* Eq. 16 range and stiffness parameters             */
   int32_t fixed_particles;  /* 1: particles keep their state (static bodies)     */
+  int32_t boundary;         /* 0: halfway bounce-back walls at -1/2, n - 1/2;
+                               1: non-equilibrium extrapolation walls on the outermost
+                                  nodes of every non-periodic axis;
+                               2: as 1, with a velocity inlet on y = 0 and a pressure
+                                  outlet on y = ny - 1 (a channel along y)           */
+  double u_inlet;           /* peak inlet velocity (boundary 2)                   */
 } or_params;
 
 typedef struct or_sim or_sim;
