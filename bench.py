@@ -397,6 +397,43 @@ def _cavity3d(args, dev, local):
     return out
 
 
+def _poiseuille(args, dev, local):
+    """The particle-free flows of Sec. 6.1 at the paper's largest sizes: Poiseuille
+    channels with a parabolic velocity inlet on y = 0, a pressure outlet on y = ny - 1
+    and walls on the other faces, all by non-equilibrium extrapolation; D2Q9 4000 x 4000
+    and D3Q19 210^3, FP32 and FP16 storage, MLUPS (Eq. 52) over min(steps, 50) steps."""
+    import torch
+
+    from paper_2002_08855_gb300 import binding
+    from paper_2002_08855_gb300.inputs import Workload
+
+    steps = max(3, min(args.steps, 50))
+    out = {"steps": steps, "boundary": "non-equilibrium extrapolation, inlet u = 0.05 peak"}
+    for name, w in (("2d_4000x4000", Workload(name="chan2", dim=2, nx=4000, ny=4000, tau=0.6,
+                                                boundary=2, u_inlet=0.05)),
+                    ("3d_210x210x210", Workload(name="chan3", dim=3, nx=210, ny=210, nz=210, tau=0.6,
+                                                  boundary=2, u_inlet=0.05))):
+        out[name] = {}
+        for st, sname in ((0, "fp32"), (1, "fp16")):
+            sim = binding.Simulation(w.with_(pdf_storage=st), np.zeros((0, w.dim)), device=str(dev))
+            sim.step(3)
+            sim.sync()
+            with ClockSampler(local) as clk:
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(sim.stream)
+                sim.step(steps)
+                ev1.record(sim.stream)
+                ev1.synchronize()
+                sim.sync()
+            ms = ev0.elapsed_time(ev1) / steps
+            _, u = sim.get_fields()
+            finite = bool(torch.isfinite(u).all().item())
+            sim.close()
+            out[name][sname] = {"value": w.n_grid / (ms * 1e3), "unit": METRIC, "ms_per_step": ms,
+                                "finite": finite, "clocks": clk.summary()}
+    return out
+
+
 def run(args):
     import torch
 
@@ -466,6 +503,7 @@ def run(args):
     # the batched ensemble of independent cavities, and the 3D cavity
     ensemble = _ensemble(args, dev, local)
     cavity3d = _cavity3d(args, dev, local)
+    poiseuille = _poiseuille(args, dev, local)
 
     # end to end through the C ABI with host buffers: init from host centres, then per
     # step one ibm_lbm_step and a read of the particle state into pinned host memory
@@ -513,6 +551,7 @@ def run(args):
             "forms": forms,
             "ensemble": ensemble,
             "cavity3d": cavity3d,
+            "poiseuille_sec61": poiseuille,
         }
         print(json.dumps(line))
     if dist is not None:

@@ -55,7 +55,7 @@ typedef struct ibm_lbm_config {
   uint32_t struct_size;   /* must equal sizeof(ibm_lbm_config)                           */
   int32_t dim;            /* 2: D2Q9, 3: D3Q19                                           */
   int32_t nx, ny, nz;     /* fluid nodes per axis (nz = 1 when dim = 2)                  */
-  int32_t periodic[3];    /* per axis: 1 periodic, 0 halfway bounce-back walls           */
+  int32_t periodic[3];    /* per axis: 1 periodic, 0 walls (see boundary)                */
   double tau;             /* relaxation time of Eq. 1, tau > 1/2                         */
   double body_force[3];   /* uniform fluid body force, added to the IB force (Eq. 7-8)  */
   int32_t n_particles;    /* N_p, rigid circles (2D) or spheres (3D), >= 0               */
@@ -79,6 +79,20 @@ typedef struct ibm_lbm_config {
   int32_t mlp_init;       /* 1: the first MDF iteration takes its force from the learned
                              initializer (2D; parameters from ibm_lbm_set_mlp), the
                              plain iterations 2..M follow.  No counterpart in the paper.  */
+  int32_t boundary;       /* fluid boundaries of the non-periodic axes:
+                             0: halfway bounce-back walls at -1/2 and n - 1/2;
+                             1: walls on the outermost nodes, by non-equilibrium
+                                extrapolation (Sec. 6.1-6.2: after streaming a boundary
+                                node takes the equilibrium of its prescribed state plus
+                                the non-equilibrium part of its inward neighbour);
+                             2: as 1, with the y axis a channel: a velocity inlet on
+                                y = 0 (the parabola u_inlet prod 4 c (L - c) / L^2 over the
+                                other non-periodic axes, L = n - 1) and a pressure outlet
+                                (p = 0) on y = ny - 1 (the Poiseuille flows of Sec. 6.1).
+                             1 and 2 need n >= 3 on every non-periodic axis; 2 needs a
+                             non-periodic y axis.  Particle contacts with a wall mirror
+                             through the wall's position.                                */
+  double u_inlet;         /* peak inlet velocity of boundary 2                           */
 } ibm_lbm_config;
 
 enum { IBMLBM_PDF_FP32 = 0, IBMLBM_PDF_FP16 = 1, IBMLBM_PDF_BF16 = 2 };

@@ -43,7 +43,7 @@ class Config(C.Structure):
         ("mdf_iters", C.c_int32), ("density_ratio", C.c_double), ("gravity", C.c_double * 3),
         ("zeta", C.c_double), ("eps_pp", C.c_double), ("E_pp", C.c_double),
         ("fixed_particles", C.c_int32), ("max_neighbors", C.c_int32), ("pdf_storage", C.c_int32),
-        ("mlp_init", C.c_int32),
+        ("mlp_init", C.c_int32), ("boundary", C.c_int32), ("u_inlet", C.c_double),
     ]
 
 
@@ -76,6 +76,8 @@ def make_config(w, max_neighbors: int = 0) -> Config:
     c.max_neighbors = int(max_neighbors)
     c.pdf_storage = int(get("pdf_storage", 0))
     c.mlp_init = int(get("mlp_init", 0))
+    c.boundary = int(get("boundary", 0))
+    c.u_inlet = float(get("u_inlet", 0.0))
     return c
 
 

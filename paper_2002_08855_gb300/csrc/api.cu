@@ -95,6 +95,16 @@ int check_config(const ibm_lbm_config* c) {
   if (c->mlp_init && (c->dim != 2 || c->mdf_iters < 1 || c->n_lag > mlp_max_points()))
     return fail(IBMLBM_ERR_UNSUPPORTED,
                 "the learned initializer needs a 2D run with mdf_iters >= 1 and n_lag <= 256");
+  if (c->boundary < 0 || c->boundary > 2) return fail(IBMLBM_ERR_INVALID_ARG, "boundary must be 0, 1 or 2");
+  if (c->boundary) {
+    const int32_t nn[3] = {c->nx, c->ny, c->nz};
+    for (int k = 0; k < c->dim; ++k)
+      if (!c->periodic[k] && nn[k] < 3)
+        return fail(IBMLBM_ERR_INVALID_ARG, "extrapolation boundaries need n >= 3 on every wall axis");
+    if (c->boundary == 2 && c->periodic[1])
+      return fail(IBMLBM_ERR_INVALID_ARG, "a channel (boundary 2) needs a non-periodic y axis");
+    if (!std::isfinite(c->u_inlet)) return fail(IBMLBM_ERR_INVALID_ARG, "u_inlet must be finite");
+  }
   if (c->n_particles > 0) {
     if (c->n_lag < 1) return fail(IBMLBM_ERR_INVALID_ARG, "n_lag must be >= 1");
     if (!(c->diameter > 0.0)) return fail(IBMLBM_ERR_INVALID_ARG, "diameter must be > 0");
@@ -280,6 +290,8 @@ struct ibm_lbm_handle {
     a.fib = (d.D == 3 || cfg.n_particles > 0) ? at<float>(l.fib) : nullptr;  // 2D: null = no IB force
     a.mask = mask(parity);
     a.omega = (float)(1.0 / cfg.tau);
+    a.boundary = cfg.boundary;
+    a.u_inlet = (float)cfg.u_inlet;
     a.kforce = (float)(1.0 - 0.5 / cfg.tau);
     for (int k = 0; k < 3; ++k) a.body[k] = (k < d.D) ? (float)cfg.body_force[k] : 0.0f;
     return a;
@@ -360,6 +372,7 @@ struct ibm_lbm_handle {
     a.c_ij = d.c_ij;
     a.eps_pp = cfg.eps_pp;
     a.E_pp = cfg.E_pp;
+    a.wall_lo = cfg.boundary ? 0.0 : -0.5;
     a.kmax = d.kmax;
     a.X = X(parity);
     a.cell_count = at<int>(l.cell_count);
@@ -465,6 +478,8 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
     CUDA_TRY(cudaEventRecord(h->join, h->side));
     CUDA_TRY(launch_lbm_step(la, h->d.D, parity, s));
     k += lbm_step_launches(h->d.g, h->d.D, parity);
+    CUDA_TRY(launch_lbm_nee(la, h->d.D, parity, s));
+    k += h->cfg.boundary ? 1 : 0;
     CUDA_TRY(cudaStreamWaitEvent(s, h->join, 0));
     *nk = k;
     return IBMLBM_OK;
@@ -472,6 +487,8 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
   // one part after the other (no particles, or timed parts)
   CUDA_TRY(launch_lbm_step(la, h->d.D, parity, s));
   k += lbm_step_launches(h->d.g, h->d.D, parity);
+  CUDA_TRY(launch_lbm_nee(la, h->d.D, parity, s));
+  k += h->cfg.boundary ? 1 : 0;
   if (ev) CUDA_TRY(cudaEventRecord(ev[3], s));
   if (particles) {
     const PairArgs pa = h->pairs(parity, have_prev);
@@ -1034,6 +1051,7 @@ int ibm_lbm_pair_search(int32_t dim, const int32_t* n_nodes, const int32_t* peri
   char* sc = static_cast<char*>(d_scratch);
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   PairArgs a{};
+  a.wall_lo = -0.5;
   a.g.nx = (int)L[0];
   a.g.ny = (int)L[1];
   a.g.nz = (int)L[2];
@@ -1119,6 +1137,7 @@ int check_batch(const ibm_lbm_config* cfgs, int32_t n) {
     if (cfgs[i].pdf_storage == IBMLBM_PDF_BF16)
       return fail(IBMLBM_ERR_UNSUPPORTED, "batch members store PDFs as FP32 or FP16");
     if (cfgs[i].mlp_init) return fail(IBMLBM_ERR_UNSUPPORTED, "batch members use the plain MDF");
+    if (cfgs[i].boundary) return fail(IBMLBM_ERR_UNSUPPORTED, "batch members use halfway bounce-back walls");
     if (cfgs[i].pdf_storage != cfgs[0].pdf_storage || cfgs[i].mdf_iters != cfgs[0].mdf_iters)
       return fail(IBMLBM_ERR_INVALID_ARG, "batch members must share pdf_storage and mdf_iters");
   }

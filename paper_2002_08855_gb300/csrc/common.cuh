@@ -147,6 +147,8 @@ struct LbmArgs {
   float omega;       // 1 / tau
   float kforce;      // 1 - omega / 2 (Eq. 8 prefactor)
   float body[3];     // uniform body force
+  int boundary;      // 0 halfway bounce-back, 1 extrapolation walls, 2 extrapolation channel
+  float u_inlet;     // peak inlet velocity (boundary 2)
 };
 
 struct IbmArgs {
@@ -265,6 +267,7 @@ struct PairArgs {
   double L[3];
   double diam, zeta, thr2;
   double c_ij, eps_pp, E_pp;
+  double wall_lo;       // wall positions on a non-periodic axis: wall_lo and L - 1 - wall_lo
   int kmax;
   const double* X;      // [n][D]
   int* cell_count;      // [ncells], zero before the insertion

@@ -36,6 +36,7 @@ cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t s);
 // launches; see Fuse in common.cuh)
 unsigned lbm_step_blocks(const Geo& g, int store);
 unsigned lbm_edge_blocks(const Geo& g, int D);
+cudaError_t launch_lbm_nee(const LbmArgs& A, int D, int parity, cudaStream_t s);
 int tile_shape_count();
 void tile_shape(int s, int store, int* k, int* w, int* persist);
 int tile_count(const Geo& g, int s);

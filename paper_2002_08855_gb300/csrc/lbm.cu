@@ -113,6 +113,27 @@ __device__ __forceinline__ void collide(float (&f)[L::Q], const float (&F)[3], f
   }
 }
 
+// Eq. 4 equilibrium of every direction at (p, u)
+template <class L>
+__device__ __forceinline__ void equilibrium(float p, const float (&u)[3], float (&feq)[L::Q]) {
+  const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  constexpr float w0 = L::w(0);
+  feq[0] = 3.0f * (w0 - 1.0f) * p - 1.5f * w0 * uu;
+#pragma unroll
+  for (int a = 1; a <= L::H; ++a) {
+    const float w = L::w(a);
+    float eu = 0.0f;
+#pragma unroll
+    for (int k = 0; k < L::dim; ++k) {
+      if (L::e(a, k) == 1) eu += u[k];
+      if (L::e(a, k) == -1) eu -= u[k];
+    }
+    const float even = w * (3.0f * p + 4.5f * eu * eu - 1.5f * uu), odd = 3.0f * w * eu;
+    feq[a] = even + odd;
+    feq[a + L::H] = even - odd;
+  }
+}
+
 struct NodeCoord {
   int x, y, z;
   long long row, n;
@@ -326,6 +347,102 @@ __global__ void __launch_bounds__(kLbmBlock) lbm_step_edge_kernel(LbmArgs A0, lo
   }
   const long long row = (long long)y + (long long)g.ny * z;
   step_node<L, 1, ST>(A, row, x, y, z, (long long)x + (long long)g.nx * row);
+}
+
+// Boundary nodes of the extrapolation boundaries: the nodes on a face of a
+// non-periodic axis, enumerated as the two z faces (3D), then the two y faces of the
+// inner z range, then the two x faces of the inner y and z ranges.
+__host__ __device__ inline void shell_groups(const Geo& g, int dim, long long& gz, long long& gy,
+                                             long long& gx) {
+  const bool fz = dim == 3 && !g.per[2], fy = !g.per[1], fx = !g.per[0];
+  const long long iz = dim == 3 ? (fz ? g.nz - 2 : g.nz) : 1, iy = fy ? g.ny - 2 : g.ny;
+  gz = fz ? 2LL * g.nx * g.ny : 0;
+  gy = fy ? 2LL * g.nx * iz : 0;
+  gx = fx ? 2LL * iy * iz : 0;
+}
+
+__device__ __forceinline__ bool shell_node(const Geo& g, int dim, long long t, int (&c)[3]) {
+  long long gz, gy, gx;
+  shell_groups(g, dim, gz, gy, gx);
+  const int oz = (dim == 3 && !g.per[2]) ? 1 : 0, oy = g.per[1] ? 0 : 1;
+  if (t < gz) {
+    const long long plane = (long long)g.nx * g.ny, r = t % plane;
+    c[0] = (int)(r % g.nx);
+    c[1] = (int)(r / g.nx);
+    c[2] = t < plane ? 0 : g.nz - 1;
+    return true;
+  }
+  t -= gz;
+  if (t < gy) {
+    const long long r = t >> 1;
+    c[0] = (int)(r % g.nx);
+    c[1] = (t & 1) ? g.ny - 1 : 0;
+    c[2] = oz + (int)(r / g.nx);
+    return true;
+  }
+  t -= gy;
+  if (t < gx) {
+    const long long r = t >> 1;
+    const long long iy = g.per[1] ? g.ny : g.ny - 2;
+    c[0] = (t & 1) ? g.nx - 1 : 0;
+    c[1] = oy + (int)(r % iy);
+    c[2] = oz + (int)(r / iy);
+    return true;
+  }
+  return false;
+}
+
+// Non-equilibrium extrapolation (the method Sec. 6.1-6.2 apply; boundary 1, 2), after
+// the collide-stream step, in the layout PARITY the next step reads: a boundary node
+// x_b takes f_a = f_a^eq(p_b, u_b) + f_a(x_f) - f_a^eq(p_f, u_f), x_f = x_b + the sum of
+// the inward normals of the faces x_b lies on, (p_f, u_f) = Eq. 6-7 at x_f with the
+// body force.  Walls: u_b = 0, p_b = p_f; channel inlet (y = 0): u_b along y = the
+// parabola, p_b = p_f; outlet (y = ny - 1): p_b = 0, u_b = u_f; a node on a wall face
+// is a wall node.  x_f is never a boundary node (n >= 3 on those axes), and each thread
+// reads only x_f's slots and writes only x_b's, so the threads are independent.
+template <class L, int PARITY, int ST>
+__global__ void __launch_bounds__(kLbmBlock) lbm_nee_kernel(LbmArgs A) {
+  const Geo& g = A.g;
+  int c[3] = {0, 0, 0};
+  if (!shell_node(g, L::dim, blockIdx.x * (long long)kLbmBlock + threadIdx.x, c)) return;
+  const int n3[3] = {g.nx, g.ny, g.nz};
+  int cf[3] = {c[0], c[1], c[2]};
+  bool wall = false, inlet = false;
+#pragma unroll
+  for (int k = 0; k < L::dim; ++k) {
+    if (g.per[k]) continue;
+    const bool lo = c[k] == 0, hi = c[k] == n3[k] - 1;
+    if (!lo && !hi) continue;
+    cf[k] = lo ? c[k] + 1 : c[k] - 1;
+    if (A.boundary == 2 && k == 1) inlet = inlet || lo;
+    else wall = true;
+  }
+  float fa[L::Q], eqf[L::Q], eqb[L::Q], us[3], s1, uf[3], ub[3] = {0.0f, 0.0f, 0.0f};
+  load_pdfs<L, PARITY, ST>(g, A.f, cf[0], cf[1], cf[2], node_of(g, cf[0], cf[1], cf[2]), fa);
+  moments<L>(fa, us, s1);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) uf[k] = (k < L::dim) ? us[k] + 0.5f * A.body[k] : 0.0f;  // Eq. 7
+  const float pf = pressure<L>(s1, uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2]);
+  float pb = pf;
+  if (!wall && inlet) {
+    float prof = A.u_inlet;
+#pragma unroll
+    for (int k = 0; k < L::dim; ++k) {
+      if (k == 1 || g.per[k]) continue;
+      const float Lk = (float)(n3[k] - 1), ck = (float)c[k];
+      prof *= 4.0f * ck * (Lk - ck) / (Lk * Lk);
+    }
+    ub[1] = prof;
+  } else if (!wall) {  // outlet
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ub[k] = uf[k];
+    pb = 0.0f;
+  }
+  equilibrium<L>(pf, uf, eqf);
+  equilibrium<L>(pb, ub, eqb);
+#pragma unroll
+  for (int a = 0; a < L::Q; ++a) fa[a] = eqb[a] + (fa[a] - eqf[a]);
+  put_pdfs<L, PARITY, ST>(g, A.f, c[0], c[1], c[2], node_of(g, c[0], c[1], c[2]), fa);
 }
 
 // u* = sum_a e_a f_a (Eq. 5) on the flagged nodes only: one thread per node in large
@@ -574,6 +691,19 @@ cudaError_t launch_lbm_step_tiles(int shape, const LbmArgs* args, const int* fir
     if (store == STORE_F32) lbm_step_edge_kernel<Lat<2>, STORE_F32, true><<<eblocks, kLbmBlock, 0, s>>>(none, 0, 0, FE);
     else lbm_step_edge_kernel<Lat<2>, STORE_F16, true><<<eblocks, kLbmBlock, 0, s>>>(none, 0, 0, FE);
   }
+  return cudaGetLastError();
+}
+
+// extrapolation boundaries after a step of the given parity (no-op for boundary 0)
+cudaError_t launch_lbm_nee(const LbmArgs& A, int D, int parity, cudaStream_t s) {
+  if (A.boundary == 0) return cudaSuccess;
+  long long gz, gy, gx;
+  shell_groups(A.g, D, gz, gy, gx);
+  const long long total = gz + gy + gx;
+  if (total == 0) return cudaSuccess;
+  const dim3 grid((unsigned)((total + kLbmBlock - 1) / kLbmBlock));
+  const int next = 1 - parity;  // the layout the next step reads
+  IBMLBM_DISPATCH_G(D, next, lbm_nee_kernel, grid, kLbmBlock, A);
   return cudaGetLastError();
 }
 

@@ -264,11 +264,12 @@ __global__ void __launch_bounds__(128) pair_force_kernel(PairArgs A0, Fuse FU) {
     if (d > 0.0 && mag != 0.0)
       for (int k = 0; k < D; ++k) F[k] += mag * dx[k] / d;
   }
-  // walls: a mirror image through each wall at -1/2 and L - 1/2
+  // walls: a mirror image through each wall (at -1/2 and L - 1/2 for halfway
+  // bounce-back, on the nodes 0 and L - 1 for the extrapolation boundaries)
   for (int k = 0; k < D; ++k) {
     if (A.g.per[k]) continue;
     for (int s = 0; s < 2; ++s) {
-      const double wall = (s == 0) ? -0.5 : A.L[k] - 0.5;
+      const double wall = (s == 0) ? A.wall_lo : A.L[k] - 1.0 - A.wall_lo;
       const double dk = 2.0 * (Xi[k] - wall);
       const double d = fabs(dk);
       const double mag = eq16_magnitude(A, d);

@@ -83,6 +83,7 @@ extern "C" int ibm_lbm_pair_search_static(int32_t dim, const int32_t* n_nodes, c
     return static_fail(IBMLBM_ERR_INVALID_ARG, "max_neighbors must be in 0..64");
   *h_count = 0;
   PairArgs a{};
+  a.wall_lo = -0.5;
   const double reach = diameter + zeta;
   for (int k = 0; k < 3; ++k) {
     if (k < dim && n_nodes[k] < 1) return static_fail(IBMLBM_ERR_INVALID_ARG, "n_nodes must be >= 1");

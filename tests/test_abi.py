@@ -111,3 +111,17 @@ def test_batch_rejects_mixed_or_unsupported_members(lib, change, code):
     rc, _ = _batch_sizes(ws)
     assert rc == code
     assert lib.ibm_lbm_last_error().decode()
+
+
+@pytest.mark.parametrize("changes", [
+    dict(boundary=3),                                    # unknown kind
+    dict(boundary=1, nx=2),                              # a wall axis needs 3 nodes
+    dict(boundary=2, periodic=(0, 1, 0)),                # a channel needs walls on y
+    dict(boundary=2, u_inlet=float("inf")),
+])
+def test_extrapolation_boundary_configurations_are_checked(lib, changes):
+    w = inputs.cavity_2d_small().as_dict()
+    w.update(changes)
+    with pytest.raises(binding.IbmLbmError) as e:
+        binding.workspace_size(w)
+    assert "INVALID_ARG" in str(e.value)
