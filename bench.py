@@ -397,6 +397,28 @@ def _cavity3d(args, dev, local):
     return out
 
 
+def _pair_search_modes(dev, w2, X2):
+    """Pair search and contact part (cell lists against the grid search of Table 5) of
+    the headline workload and of the 3D cavity, as the part timer measures it (the
+    contact search, Eq. 16 forces and the particle update, run on their own)."""
+    from paper_2002_08855_gb300 import binding, inputs
+
+    w3 = inputs.cavity_3d(1)
+    X3 = inputs.place_particles(w3)
+    out = {}
+    for name, w, X, reps in (("2d_headline", w2, X2, 20), ("3d_cavity", w3, X3, 3)):
+        out[name] = {}
+        for mode, mname in ((0, "cell_lists"), (1, "grid_search")):
+            sim = binding.Simulation(w.with_(pair_search=mode), X, device=str(dev))
+            sim.step(3)
+            sim.sync()
+            parts = sim.time_parts(reps)
+            n_pairs = len(sim.get_pairs())
+            sim.close()
+            out[name][mname] = {"pairs_ms_per_step": parts["pairs"] / reps, "pairs": n_pairs}
+    return out
+
+
 def _poiseuille(args, dev, local):
     """The particle-free flows of Sec. 6.1 at the paper's largest sizes: Poiseuille
     channels with a parabolic velocity inlet on y = 0, a pressure outlet on y = ny - 1
@@ -504,6 +526,7 @@ def run(args):
     ensemble = _ensemble(args, dev, local)
     cavity3d = _cavity3d(args, dev, local)
     poiseuille = _poiseuille(args, dev, local)
+    pair_modes = _pair_search_modes(dev, w, X)
 
     # end to end through the C ABI with host buffers: init from host centres, then per
     # step one ibm_lbm_step and a read of the particle state into pinned host memory
@@ -552,6 +575,7 @@ def run(args):
             "ensemble": ensemble,
             "cavity3d": cavity3d,
             "poiseuille_sec61": poiseuille,
+            "pair_search": pair_modes,
         }
         print(json.dumps(line))
     if dist is not None:

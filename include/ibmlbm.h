@@ -93,6 +93,12 @@ typedef struct ibm_lbm_config {
                              non-periodic y axis.  Particle contacts with a wall mirror
                              through the wall's position.                                */
   double u_inlet;         /* peak inlet velocity of boundary 2                           */
+  int32_t pair_search;    /* particle-pair search: 0 cell lists (cells of side >= D_p +
+                             zeta, buckets of particle indices); 1 the grid search of
+                             Sec. 5 (Table 5, Eq. 49-51: cells of side < D_p / sqrt(dim)
+                             holding one particle index each, scanned within
+                             ceil((D_p + zeta) / side) cells).  Both give the same
+                             sorted pair lists and forces.  Batches use 0.              */
 } ibm_lbm_config;
 
 enum { IBMLBM_PDF_FP32 = 0, IBMLBM_PDF_FP16 = 1, IBMLBM_PDF_BF16 = 2 };

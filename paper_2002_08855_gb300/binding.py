@@ -44,6 +44,7 @@ class Config(C.Structure):
         ("zeta", C.c_double), ("eps_pp", C.c_double), ("E_pp", C.c_double),
         ("fixed_particles", C.c_int32), ("max_neighbors", C.c_int32), ("pdf_storage", C.c_int32),
         ("mlp_init", C.c_int32), ("boundary", C.c_int32), ("u_inlet", C.c_double),
+        ("pair_search", C.c_int32),
     ]
 
 
@@ -78,6 +79,7 @@ def make_config(w, max_neighbors: int = 0) -> Config:
     c.mlp_init = int(get("mlp_init", 0))
     c.boundary = int(get("boundary", 0))
     c.u_inlet = float(get("u_inlet", 0.0))
+    c.pair_search = int(get("pair_search", 0))
     return c
 
 

@@ -59,6 +59,10 @@ struct Derived {
   int kmax;
   int nc[3];
   double H[3], L[3];
+  int gnc[3], greach[3];  // grid search (pair_search 1): cells per axis, cells scanned per side
+  double gH[3];
+  long long gcells;
+  int over_cap;
   int box, rcell;
   double radius, dV, Mp, meff, Ip, Kt, Kr, c_ij, thr2;
   float mark_radius;
@@ -69,6 +73,7 @@ struct Layout {
   size_t X0, X1, U, Om, Fh, Th, FhN, ThN, acc, alp, Pint, Lint, Pprev, Lprev, Fc;
   size_t Uf, Omf, ref_fix, ref_f, Xcf, Xb0, Xb1, Ub0, Ub1, Fb, dFb, ubs, ubox, res, mlp, mlp_img;
   size_t cell_count, cell_ids, nbr, nbr_count, gt, pairs, status;
+  size_t grid, over, over_count;
   size_t total;
 };
 
@@ -104,6 +109,14 @@ int check_config(const ibm_lbm_config* c) {
     if (c->boundary == 2 && c->periodic[1])
       return fail(IBMLBM_ERR_INVALID_ARG, "a channel (boundary 2) needs a non-periodic y axis");
     if (!std::isfinite(c->u_inlet)) return fail(IBMLBM_ERR_INVALID_ARG, "u_inlet must be finite");
+  }
+  if (c->pair_search != 0 && c->pair_search != 1)
+    return fail(IBMLBM_ERR_INVALID_ARG, "pair_search must be 0 or 1");
+  if (c->pair_search == 1 && c->n_particles > 0 && c->diameter > 0.0) {
+    double cells = 1.0;
+    const double L3[3] = {(double)c->nx, (double)c->ny, (double)c->nz};
+    for (int k = 0; k < c->dim; ++k) cells *= std::ceil(L3[k] / (c->diameter / std::sqrt((double)c->dim)));
+    if (cells > 1.0e9) return fail(IBMLBM_ERR_UNSUPPORTED, "grid search needs more than 1e9 cells");
   }
   if (c->n_particles > 0) {
     if (c->n_lag < 1) return fail(IBMLBM_ERR_INVALID_ARG, "n_lag must be >= 1");
@@ -159,6 +172,23 @@ Derived derive(const ibm_lbm_config* c) {
   d.rcell = (int)std::ceil(d.radius);
   d.box = 2 * d.rcell + 6;
   cell_grid(d.D, d.L, d.g.per, Dp + c->zeta, d.nc, d.H);
+  // grid search (Eq. 49): the largest side below D_p / sqrt(D) that tiles each axis
+  d.gcells = 0;
+  if (c->pair_search == 1 && c->n_particles > 0) {
+    const double hmax = Dp / std::sqrt((double)d.D) * (1.0 - 1e-12);
+    d.gcells = 1;
+    for (int k = 0; k < 3; ++k) {
+      d.gnc[k] = 1;
+      d.gH[k] = k < d.D ? d.L[k] : 1.0;
+      d.greach[k] = 0;
+      if (k >= d.D) continue;
+      d.gnc[k] = std::max(1, (int)std::ceil(d.L[k] / hmax));
+      d.gH[k] = d.L[k] / d.gnc[k];
+      d.greach[k] = (int)std::ceil((Dp + c->zeta) / d.gH[k]);
+      d.gcells *= d.gnc[k];
+    }
+    d.over_cap = std::min(c->n_particles, std::max(256, c->n_particles / 16));
+  }
   // Eq. 13 point volume: 2D ds * drs with ds = pi D / N_L; 3D (pi D^2 / N_L) * drs
   if (c->n_lag > 0)
     d.dV = (d.D == 2 ? kPi * Dp / c->n_lag : kPi * Dp * Dp / c->n_lag) * c->drs;
@@ -226,6 +256,9 @@ Layout carve(const ibm_lbm_config* c, const Derived& d) {
   l.gt = cv.take(sizeof(int) * 2 * (np + 1));
   l.pairs = cv.take(sizeof(int) * np * d.kmax);
   l.status = cv.take(sizeof(uint32_t));
+  l.grid = cv.take(sizeof(int) * (size_t)d.gcells);
+  l.over = cv.take(d.gcells ? sizeof(int) * (size_t)d.over_cap : 0);
+  l.over_count = cv.take(d.gcells ? sizeof(int) : 0);
   l.total = cv.off;
   return l;
 }
@@ -374,6 +407,16 @@ struct ibm_lbm_handle {
     a.E_pp = cfg.E_pp;
     a.wall_lo = cfg.boundary ? 0.0 : -0.5;
     a.kmax = d.kmax;
+    a.grid_mode = d.gcells > 0 ? 1 : 0;
+    a.grid = at<int>(l.grid);
+    for (int k = 0; k < 3; ++k) {
+      a.gnc[k] = d.gnc[k];
+      a.gH[k] = d.gH[k];
+      a.greach[k] = d.greach[k];
+    }
+    a.over = at<int>(l.over);
+    a.over_count = at<int>(l.over_count);
+    a.over_cap = d.over_cap;
     a.X = X(parity);
     a.cell_count = at<int>(l.cell_count);
     a.cell_ids = at<int>(l.cell_ids);
@@ -1138,6 +1181,7 @@ int check_batch(const ibm_lbm_config* cfgs, int32_t n) {
       return fail(IBMLBM_ERR_UNSUPPORTED, "batch members store PDFs as FP32 or FP16");
     if (cfgs[i].mlp_init) return fail(IBMLBM_ERR_UNSUPPORTED, "batch members use the plain MDF");
     if (cfgs[i].boundary) return fail(IBMLBM_ERR_UNSUPPORTED, "batch members use halfway bounce-back walls");
+    if (cfgs[i].pair_search) return fail(IBMLBM_ERR_UNSUPPORTED, "batch members use the cell-list search");
     if (cfgs[i].pdf_storage != cfgs[0].pdf_storage || cfgs[i].mdf_iters != cfgs[0].mdf_iters)
       return fail(IBMLBM_ERR_INVALID_ARG, "batch members must share pdf_storage and mdf_iters");
   }

@@ -278,6 +278,14 @@ struct PairArgs {
   double* Fc;           // [n][D] (null: pair list only)
   int* gt_count;        // [2 (n + 1)] partners j > i, then their offsets
   uint32_t* status;
+  int grid_mode;        // 1: grid search (one particle per cell) instead of cell buckets
+  int* grid;            // [gnc cells] particle index or -1
+  int gnc[3];           // grid cells per axis (side gH < D_p / sqrt(D))
+  double gH[3];
+  int greach[3];        // cells scanned on each side of the own cell
+  int* over;            // [over_cap] particles whose grid cell was taken
+  int* over_count;
+  int over_cap;
   int integrate;        // 1: advance the particles (PartState) after the contact force
   int have_prev;        // a previous step exists (history terms of the update)
   PartState ps;

@@ -144,6 +144,42 @@ __device__ void advance_particle(const PairArgs& A, int i, const double* X, cons
   if (bad) atomicOr(A.status, ST_NONFINITE);
 }
 
+// The cnt partners a warp collected for particle i (list holds the first kmax, in
+// any order): sort by index, store the list, its length and the number of partners
+// j > i; more than kmax partners is reported.
+__device__ __forceinline__ void store_partners(const PairArgs& A, int i, int lane, int* list, int cnt) {
+  __syncwarp();
+  const int n_ok = min(cnt, A.kmax);
+  if (lane == 0) {
+    if (cnt > A.kmax) atomicOr(A.status, ST_CAPACITY);
+    int gt = 0;
+    for (int a = 1; a < n_ok; ++a) {  // insertion sort by partner index
+      const int v = list[a];
+      int b = a - 1;
+      while (b >= 0 && list[b] > v) {
+        list[b + 1] = list[b];
+        --b;
+      }
+      list[b + 1] = v;
+    }
+    for (int a = 0; a < n_ok; ++a) gt += list[a] > i;
+    A.nbr_count[i] = n_ok;
+    A.gt_count[i] = gt;
+  }
+  __syncwarp();
+  for (int a = lane; a < n_ok; a += 32) A.nbr[(long long)i * A.kmax + a] = list[a];
+}
+
+// partner test of the pair rule: j != i and |X_i - X_j|^2 < (D_p + zeta)^2
+template <int D>
+__device__ __forceinline__ bool is_partner(const PairArgs& A, const double (&Xi)[3], int i, int j) {
+  if (j < 0 || j == i) return false;
+  double Xj[3] = {0.0, 0.0, 0.0}, dx[3];
+  for (int k = 0; k < D; ++k) Xj[k] = A.X[(long long)j * D + k];
+  separation<D>(A, Xi, Xj, dx);
+  return dist2_nofma(dx) < A.thr2;
+}
+
 // Neighbour search, one warp per particle.  Lane c < 3^D reads the count of
 // neighbouring cell c; a warp scan turns the counts into offsets, and lane l then
 // tests occupied slots l, l+32, ... of the concatenated buckets.  Accepted partners
@@ -221,26 +257,103 @@ __global__ void __launch_bounds__(256) pair_search_kernel(PairArgs A0, Fuse FU) 
     if (hit && pos < A.kmax) list[pos] = j;
     cnt += __popc(m);
   }
-  __syncwarp();
-  const int n_ok = min(cnt, A.kmax);
-  if (lane == 0) {
-    if (cnt > A.kmax) atomicOr(A.status, ST_CAPACITY);
-    int gt = 0;
-    for (int a = 1; a < n_ok; ++a) {  // insertion sort by partner index
-      const int v = list[a];
-      int b = a - 1;
-      while (b >= 0 && list[b] > v) {
-        list[b + 1] = list[b];
-        --b;
-      }
-      list[b + 1] = v;
-    }
-    for (int a = 0; a < n_ok; ++a) gt += list[a] > i;
-    A.nbr_count[i] = n_ok;
-    A.gt_count[i] = gt;
+  store_partners(A, i, lane, list, cnt);
+}
+
+// ---------------------------------------------------------------- grid search
+// The grid search of Sec. 5 (Table 5, Eq. 49-51): cells of side H_k < D_p / sqrt(D), so
+// a cell can hold the centre of at most one particle when no two centres are closer
+// than D_p, and the grid stores one particle index per cell (-1: empty).  Scatter: one
+// thread per particle claims its cell with a compare-and-swap.  Eq. 16's contact lets
+// two centres come closer than D_p, so a second centre in a claimed cell goes to an
+// overflow list that every particle also scans (nothing is dropped; overflow of that
+// list is reported).  Search: a warp per particle scans the cells within
+// reach_k = ceil((D_p + zeta) / H_k) of its own along each axis -- 5 per axis when
+// Eq. 50 holds (25 cells in 2D, 125 in 3D), wider where D_p + zeta >= 2 H_k (in 3D
+// Eq. 49 and 50 only meet for zeta < 0.155 D_p) -- and keeps the partners by the same
+// rule and in the same sorted order as the cell-list search, so the contact forces
+// are the same.  Each particle collects its own partners (no Newton's-third-law
+// pairing), so no two threads write one force.
+template <int D>
+__device__ __forceinline__ int grid_cell_of(const PairArgs& A, const double* X, int (&cc)[3]) {
+  int c = 0, stride = 1;
+  cc[0] = cc[1] = cc[2] = 0;
+  for (int k = 0; k < D; ++k) {
+    cc[k] = cell_coord(X[k], A.gH[k], A.gnc[k]);
+    c += stride * cc[k];
+    stride *= A.gnc[k];
   }
-  __syncwarp();
-  for (int a = lane; a < n_ok; a += 32) A.nbr[(long long)i * A.kmax + a] = list[a];
+  return c;
+}
+
+template <int D>
+__global__ void grid_scatter_kernel(PairArgs A) {
+  const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= A.n) return;
+  int cc[3];
+  const int c = grid_cell_of<D>(A, A.X + (long long)i * D, cc);
+  if (atomicCAS(&A.grid[c], -1, i) == -1) return;
+  const int slot = atomicAdd(A.over_count, 1);
+  if (slot < A.over_cap)
+    A.over[slot] = i;
+  else
+    atomicOr(A.status, ST_CAPACITY);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) grid_search_kernel(PairArgs A) {
+  __shared__ int s_list[8][kMaxNeighbors];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  if (i >= A.n) return;  // whole warp
+  int* list = s_list[w];
+  double Xi[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < D; ++k) Xi[k] = A.X[(long long)i * D + k];
+  int cc[3];
+  grid_cell_of<D>(A, Xi, cc);
+  // window per axis: 2 reach + 1 cells around the own cell, or the whole axis once
+  int wk[3] = {1, 1, 1}, lo[3] = {0, 0, 0};
+  for (int k = 0; k < D; ++k) {
+    const int span = 2 * A.greach[k] + 1;
+    if (span >= A.gnc[k]) {
+      wk[k] = A.gnc[k];
+    } else {
+      wk[k] = span;
+      lo[k] = cc[k] - A.greach[k];
+    }
+  }
+  const int T = wk[0] * wk[1] * wk[2];
+  const int n_over = min(*A.over_count, A.over_cap);
+  int cnt = 0;
+  for (int base = 0; base < T + n_over; base += 32) {
+    const int t = base + lane;
+    int j = -1;
+    if (t < T) {
+      int r = t, cell = 0, stride = 1;
+      bool ok = true;
+      for (int k = 0; k < D; ++k) {
+        int c = lo[k] + r % wk[k];
+        r /= wk[k];
+        if (c < 0 || c >= A.gnc[k]) {
+          if (A.g.per[k])
+            c = (c % A.gnc[k] + A.gnc[k]) % A.gnc[k];
+          else
+            ok = false;
+        }
+        cell += stride * c;
+        stride *= A.gnc[k];
+      }
+      if (ok) j = A.grid[cell];
+    } else if (t < T + n_over) {
+      j = A.over[t - T];
+    }
+    const bool hit = is_partner<D>(A, Xi, i, j);
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+    if (hit && pos < A.kmax) list[pos] = j;
+    cnt += __popc(m);
+  }
+  store_partners(A, i, lane, list, cnt);
 }
 
 // Eq. 16 contact force on particle i from its sorted partner list (summed in index
@@ -350,6 +463,18 @@ cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t s) {
 
 cudaError_t launch_pair_cells(const PairArgs& A, cudaStream_t s) {
   if (A.n == 0) return cudaSuccess;
+  if (A.grid_mode) {  // grid search: empty grid and overflow list, then the scatter
+    const size_t gcells = (size_t)A.gnc[0] * A.gnc[1] * A.gnc[2];
+    cudaError_t e = cudaMemsetAsync(A.grid, 0xff, sizeof(int) * gcells, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(A.over_count, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    const unsigned g = blocks_for(A.n, 256);
+    if (A.D == 2)
+      grid_scatter_kernel<2><<<g, 256, 0, s>>>(A);
+    else
+      grid_scatter_kernel<3><<<g, 256, 0, s>>>(A);
+    return cudaGetLastError();
+  }
   const size_t ncells = (size_t)A.nc[0] * A.nc[1] * A.nc[2];
   cudaError_t e = cudaMemsetAsync(A.cell_count, 0, sizeof(int) * ncells, s);
   if (e != cudaSuccess) return e;
@@ -366,10 +491,16 @@ cudaError_t launch_pair_cells(const PairArgs& A, cudaStream_t s) {
 cudaError_t launch_pair_contacts(const PairArgs& A, cudaStream_t s) {
   if (A.n == 0) return cudaSuccess;
   const unsigned gw = blocks_for((long long)A.n * 32, 256);
-  if (A.D == 2)
+  if (A.grid_mode) {
+    if (A.D == 2)
+      grid_search_kernel<2><<<gw, 256, 0, s>>>(A);
+    else
+      grid_search_kernel<3><<<gw, 256, 0, s>>>(A);
+  } else if (A.D == 2) {
     pair_search_kernel<2, false><<<gw, 256, 0, s>>>(A, Fuse{});
-  else
+  } else {
     pair_search_kernel<3, false><<<gw, 256, 0, s>>>(A, Fuse{});
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !A.Fc) return e;
   const unsigned g = blocks_for(A.n, 128);

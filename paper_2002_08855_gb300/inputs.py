@@ -68,6 +68,7 @@ class Workload:
     fixed_particles: int = 0
     boundary: int = 0     # 0 halfway bounce-back, 1 extrapolation walls, 2 extrapolation channel
     u_inlet: float = 0.0  # peak inlet velocity of the channel (boundary 2)
+    pair_search: int = 0  # 0 cell lists, 1 grid search (Table 5) (GPU; same pairs)
     pdf_storage: int = 0  # 0 FP32, 1 FP16, 2 BF16 (GPU storage of the PDFs only)
     mlp_init: int = 0     # 1: learned first MDF force (GPU, 2D)
     steps: int = 100
@@ -85,7 +86,7 @@ class Workload:
         d = {k: getattr(self, k) for k in (
             "dim", "nx", "ny", "nz", "periodic", "tau", "body_force", "n_particles", "n_lag",
             "diameter", "delta_kind", "drs", "mdf_iters", "density_ratio", "gravity", "zeta",
-            "eps_pp", "E_pp", "fixed_particles", "boundary", "u_inlet", "pdf_storage", "mlp_init")}
+            "eps_pp", "E_pp", "fixed_particles", "boundary", "u_inlet", "pair_search", "pdf_storage", "mlp_init")}
         if self.dim == 2:
             d["nz"] = 1
         return d

@@ -96,3 +96,65 @@ def test_handle_pairs_and_contact_forces():
     Fo = oracle.contact_forces(w.as_dict(), X)
     assert np.abs(Fc - Fo).max() <= 1e-12 * max(np.abs(Fo).max(), 1e-30)
     sim.close()
+
+
+@pytest.mark.parametrize("dim,shape,per", [
+    (2, (120, 100, 1), (0, 0, 0)),
+    (2, (90, 70, 1), (1, 1, 0)),
+    (3, (40, 36, 34), (0, 0, 0)),
+    (3, (34, 30, 32), (1, 0, 1)),
+])
+def test_grid_search_pairs_and_forces(dim, shape, per):
+    """The grid search of Table 5 (one particle per cell of side < D_p / sqrt(dim)) on
+    held particles, some pairs overlapping so that two centres share a grid cell (the
+    overflow list): the pair list equals the brute-force half search and the Eq. 16
+    forces equal the oracle's."""
+    require_gpu()
+    from paper_2002_08855_gb300.binding import Simulation
+
+    D = 8.0
+    n0 = 30 if dim == 2 else 20
+    X = inputs.place_rsa(dim, shape[:dim], n0, D, seed=31 + dim, gap=0.2, wall_gap=0.5)
+    # overlapping partners: 1.5 lattice units from a placed centre (same or next cell)
+    extra = X[:3] + np.array([1.5] + [0.3] * (dim - 1))
+    X = np.vstack([X, extra])
+    w = inputs.Workload(name="g", dim=dim, nx=shape[0], ny=shape[1], nz=shape[2] if dim == 3 else 1,
+                        periodic=per, n_particles=len(X), n_lag=25 if dim == 2 else 100, diameter=D,
+                        zeta=2.0, gravity=(0, -1e-5, 0), density_ratio=1.5, fixed_particles=1,
+                        mdf_iters=0, pair_search=1)
+    sim = Simulation(w, X, max_neighbors=64)
+    sim.step(1)
+    ref = oracle.pairs_bruteforce(w.as_dict(), X)
+    assert len(ref) > 3
+    assert np.array_equal(sim.get_pairs(), ref)
+    Fc = sim.get_particles()["F_c"]
+    Fo = oracle.contact_forces(w.as_dict(), X)
+    assert np.abs(Fc - Fo).max() <= 1e-12 * max(np.abs(Fo).max(), 1e-30)
+    sim.close()
+
+
+def test_grid_search_whole_steps_match_oracle():
+    """The 128 x 256 cavity (12 circles, 200 steps) with the grid search: the same
+    trajectory as the oracle, and the in-run pair list of step 200 equals the
+    brute-force list of the centres it was built from."""
+    require_gpu()
+    from paper_2002_08855_gb300.binding import Simulation
+
+    from gpu_util import rel_l2
+
+    w = inputs.cavity_2d_small().with_(pair_search=1)
+    X0 = inputs.place_particles(w)
+    sim = Simulation(w, X0)
+    ref = oracle.Sim(w.as_dict(), X0)
+    sim.step(199)
+    X199 = sim.get_particles()["X"]
+    sim.step(1)
+    sim.sync()
+    ref.step(200)
+    _, ug = sim.get_fields()
+    _, uo = ref.get_fields()
+    assert rel_l2(ug.cpu().numpy(), uo) < 1e-5
+    pg, po = sim.get_particles(), ref.get_particles()
+    assert rel_l2(pg["X"] - X0, po["X"] - X0) < 1e-5
+    assert np.array_equal(sim.get_pairs(), oracle.pairs_bruteforce(w.as_dict(), X199))
+    sim.close()
