@@ -485,8 +485,8 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
       ++k;
     }
     for (int m = 1; m <= h->cfg.mdf_iters; ++m) {
-      CUDA_TRY(launch_ibm_interp(ia, m, s));  // 3D: interpolation and spreading
-      ++k;
+      CUDA_TRY(launch_ibm_interp(ia, m, s));  // 3D: interpolation, then spreading
+      k += h->d.D == 3 ? 2 : 1;
       if (m == 1 && h->cfg.mlp_init) {  // learned first force (2D)
         CUDA_TRY(launch_mlp_step(ia, h->at<float>(h->l.mlp), h->at<void>(h->l.mlp_img), s));
         ++k;

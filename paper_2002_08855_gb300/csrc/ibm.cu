@@ -385,7 +385,8 @@ __global__ void __launch_bounds__(kIbmWarps * 32) ibm_spread2_kernel(IbmArgs A0,
 // box cell and dF_b dV.
 constexpr int kMdf3Threads = 512;
 constexpr int kMdf3Warps = kMdf3Threads / 32;
-constexpr int kTab3 = 16;  // table floats per point
+constexpr int kTab3 = 17;  // table floats per point: 16 used; an odd stride keeps the rows
+                            // a thread-per-point loop touches on distinct banks
 constexpr int kRows3 = 2;  // box rows each warp stages per round
 
 __host__ __device__ inline int box3_pitch(int S) {
@@ -398,20 +399,10 @@ size_t ibm_mdf3_smem(int nl, int box) {
   return sizeof(float) * (3 * plane * box + (size_t)kTab3 * nl + 32);
 }
 
-template <int SC, int MODE>
-__global__ void __launch_bounds__(kMdf3Threads) ibm_mdf3_kernel(IbmArgs A, int m) {
-  extern __shared__ __align__(16) float sm3[];
-  const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int S = SC ? SC : A.box, Py = box3_pitch(S), Pz = Py * S, cells = Pz * S;
-  float* box = sm3;                          // [3][cells]
-  int* boxi = reinterpret_cast<int*>(sm3);   // the same memory as fixed point (step 3)
-  float* tab = sm3 + 3 * cells;              // [nl][kTab3]
-  float* red = tab + (size_t)kTab3 * A.nl;   // [32] reduction scratch
-  const float4* us4 = reinterpret_cast<const float4*>(A.ustar);
-  float4* fib4 = reinterpret_cast<float4*>(A.fib);
-  const int nn[3] = {A.g.nx, A.g.ny, A.g.nz};
-  int an[3], org[3];
-  float fr[3];
+// box origin of sphere i (two nodes before its support reach) and the fixed-point
+// anchor and fraction of its centre
+__device__ __forceinline__ void mdf3_origin(const IbmArgs& A, int i, int (&an)[3], float (&fr)[3],
+                                            int (&org)[3]) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const long long v = A.Xcf[(long long)i * 3 + k];
@@ -419,6 +410,64 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_mdf3_kernel(IbmArgs A, int m
     fr[k] = fix_frac(v);
     org[k] = an[k] - A.rcell - 2;
   }
+}
+
+// table row of every point of sphere i: its 12 weights and first box cell (zero
+// weights, and CAPACITY, for a support outside the box)
+__device__ __forceinline__ void mdf3_table(const IbmArgs& A, int i, const int (&org)[3], int S, int Py,
+                                           int Pz, float* tab) {
+  const int nn[3] = {A.g.nx, A.g.ny, A.g.nz};
+  for (int k = threadIdx.x; k < A.nl; k += kMdf3Threads) {
+    const long long b = (long long)i * A.nl + k;
+    float* row = tab + (size_t)k * kTab3;
+    int base = 0;
+    bool valid = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const long long X = A.Xb[b * 3 + a];
+      float f;
+      const int s0 = support_first(A.delta_kind, X, f);
+      const int l0 = s0 - org[a];
+      if (l0 < 0 || l0 + 3 >= S) valid = false;
+      base += l0 * (a == 0 ? 1 : a == 1 ? Py : Pz);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int gc = s0 + t;
+        row[4 * a + t] = (!A.g.per[a] && (gc < 0 || gc >= nn[a])) ? 0.0f : delta_w(A.delta_kind, (float)(t - 1) - f);
+      }
+    }
+    if (!valid) {
+      atomicOr(A.status, ST_CAPACITY);
+      base = 0;
+#pragma unroll
+      for (int t = 0; t < 12; ++t) row[t] = 0.0f;
+    }
+    row[12] = __int_as_float(base);
+  }
+}
+
+// Interpolation of MDF iteration m, one block per sphere (Eq. 47, 10):
+//   1. stage u^(m-1) = u* + f_IB/2 (m = 1: u*) of the nodes of the sphere's box that
+//      lie in the marked ball (every support node does) into shared memory, one box
+//      row per warp and round, one node per lane (u* and f_IB are [N][4]);
+//   2. interpolate every point, one point per half-warp, lane (sx, sy) of the 4 x 4
+//      support columns, the 4 z levels in a loop; dF_b = 2 (U_b - u_b), F_b += dF_b.
+// The spreading of the iteration is a separate launch, so every sphere reads f_IB
+// with the increments of iterations 1 .. m-1 of all spheres and none of iteration m
+// (the iteration of the FP64 oracle).
+template <int SC, int MODE>
+__global__ void __launch_bounds__(kMdf3Threads) ibm_interp3_kernel(IbmArgs A, int m) {
+  extern __shared__ __align__(16) float sm3[];
+  const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int S = SC ? SC : A.box, Py = box3_pitch(S), Pz = Py * S, cells = Pz * S;
+  float* box = sm3;                          // [3][cells]
+  float* tab = sm3 + 3 * cells;              // [nl][kTab3]
+  const float4* us4 = reinterpret_cast<const float4*>(A.ustar);
+  const float4* fib4 = reinterpret_cast<const float4*>(A.fib);
+  const int nn[3] = {A.g.nx, A.g.ny, A.g.nz};
+  int an[3], org[3];
+  float fr[3];
+  mdf3_origin(A, i, an, fr, org);
   const float Rm2 = A.mark_radius * A.mark_radius;
   // this lane's column of every box row: grid x, and whether it is inside the domain
   // (S <= 26 here: a larger box does not fit in shared memory and is rejected at init)
@@ -476,40 +525,12 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_mdf3_kernel(IbmArgs A, int m
         box[2 * cells + cell[u]] = v[u].z;
       }
   }
-  // table: weights and first box cell of every point
-  for (int k = tid; k < A.nl; k += kMdf3Threads) {
-    const long long b = (long long)i * A.nl + k;
-    float* row = tab + (size_t)k * kTab3;
-    int base = 0;
-    bool valid = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const long long X = A.Xb[b * 3 + a];
-      float f;
-      const int s0 = support_first(A.delta_kind, X, f);
-      const int l0 = s0 - org[a];
-      if (l0 < 0 || l0 + 3 >= S) valid = false;
-      base += l0 * (a == 0 ? 1 : a == 1 ? Py : Pz);
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int gc = s0 + t;
-        row[4 * a + t] = (!A.g.per[a] && (gc < 0 || gc >= nn[a])) ? 0.0f : delta_w(A.delta_kind, (float)(t - 1) - f);
-      }
-    }
-    if (!valid) {
-      atomicOr(A.status, ST_CAPACITY);
-      base = 0;
-#pragma unroll
-      for (int t = 0; t < 12; ++t) row[t] = 0.0f;
-    }
-    row[12] = __int_as_float(base);
-  }
+  mdf3_table(A, i, org, S, Py, Pz, tab);
   __syncthreads();
 
   // 2. interpolation: warp w takes points 2 (w + kMdf3Warps j) + h, half h
   const int h = lane >> 4, sx = lane & 3, sy = (lane >> 2) & 3;
   const int colo = sx + Py * sy;
-  float mx = 0.0f;
   for (int p0 = 2 * warp; p0 < A.nl; p0 += 2 * kMdf3Warps) {
     const int p = p0 + h;
     const bool act = p < A.nl;
@@ -541,10 +562,10 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_mdf3_kernel(IbmArgs A, int m
     }
   }
   __syncthreads();
-  // dF_b = 2 (U_b - u_b), F_b, one thread per point; the table keeps dF_b dV
+  // dF_b = 2 (U_b - u_b) and F_b, one thread per point (coalesced)
   for (int k = tid; k < A.nl; k += kMdf3Threads) {
     const long long b = (long long)i * A.nl + k;
-    float* row = tab + (size_t)k * kTab3;
+    const float* row = tab + (size_t)k * kTab3;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float u = row[13 + c];
@@ -552,15 +573,52 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_mdf3_kernel(IbmArgs A, int m
       A.dFb[b * 3 + c] = d;
       A.Fb[b * 3 + c] = (m == 1) ? d : A.Fb[b * 3 + c] + d;
       if (m == 1) A.ubs[b * 3 + c] = u;
-      row[13 + c] = d * A.dV;
-      mx = fmaxf(mx, fabsf(d * A.dV));
+    }
+  }
+}
+
+// Spreading of an MDF iteration, one block per sphere (Eq. 48, 11):
+//   1. the table of weights (as in the interpolation) and dF_b dV of every point;
+//   2. spread into the sphere's box, accumulated as 32-bit fixed point with integer
+//      shared-memory atomics.  The scale of the sphere is 2^30 over (max |dF_b dV|
+//      times N_L times 1/8), a bound on any node's sum (every weight is at most 1/8),
+//      so no sum overflows and the rounding is that of single precision;
+//   3. add the non-zero box cells to f_IB with one vector atomic per cell.
+template <int SC>
+__global__ void __launch_bounds__(kMdf3Threads) ibm_spread3_kernel(IbmArgs A) {
+  extern __shared__ __align__(16) float sm3[];
+  const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int S = SC ? SC : A.box, Py = box3_pitch(S), Pz = Py * S, cells = Pz * S;
+  int* boxi = reinterpret_cast<int*>(sm3);   // [3][cells]
+  float* tab = sm3 + 3 * cells;              // [nl][kTab3]
+  float* red = tab + (size_t)kTab3 * A.nl;   // [32] reduction scratch
+  float4* fib4 = reinterpret_cast<float4*>(A.fib);
+  const int nn[3] = {A.g.nx, A.g.ny, A.g.nz};
+  int an[3], org[3];
+  float fr[3];
+  mdf3_origin(A, i, an, fr, org);
+  {
+    int4* b4 = reinterpret_cast<int4*>(boxi);
+    const int4 z = make_int4(0, 0, 0, 0);
+    for (int q = tid; q < 3 * cells / 4; q += kMdf3Threads) b4[q] = z;
+  }
+  mdf3_table(A, i, org, S, Py, Pz, tab);
+  float mx = 0.0f;
+  for (int k = tid; k < A.nl; k += kMdf3Threads) {
+    const long long b = (long long)i * A.nl + k;
+    float* row = tab + (size_t)k * kTab3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float d = A.dFb[b * 3 + c] * A.dV;
+      row[13 + c] = d;
+      mx = fmaxf(mx, fabsf(d));
     }
   }
   // largest |dF dV| of the sphere
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (lane == 0) red[warp] = mx;
-  __syncthreads();  // the box is free
+  __syncthreads();
   float gmax = 0.0f;
 #pragma unroll
   for (int w = 0; w < kMdf3Warps; ++w) gmax = fmaxf(gmax, red[w]);
@@ -570,14 +628,10 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_mdf3_kernel(IbmArgs A, int m
   }
   const float scale = 1073741824.0f / (gmax * 0.125f * (float)A.nl);  // 2^30 / bound
   const float inv = 1.0f / scale;
-  {
-    int4* b4 = reinterpret_cast<int4*>(boxi);
-    const int4 z = make_int4(0, 0, 0, 0);
-    for (int q = tid; q < 3 * cells / 4; q += kMdf3Threads) b4[q] = z;
-  }
-  __syncthreads();
 
-  // 3. spreading, same assignment of points to half-warps
+  // 2. spreading, one point per half-warp as in the interpolation
+  const int h = lane >> 4, sx = lane & 3, sy = (lane >> 2) & 3;
+  const int colo = sx + Py * sy;
   for (int p0 = 2 * warp; p0 < A.nl; p0 += 2 * kMdf3Warps) {
     const int p = p0 + h;
     if (p >= A.nl) continue;
@@ -597,7 +651,10 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_mdf3_kernel(IbmArgs A, int m
   }
   __syncthreads();
 
-  // 4. flush the non-zero cells to f_IB, one box row per warp and round
+  // 3. flush the non-zero cells to f_IB, one box row per warp and round
+  const int rows = S * S;
+  int gx = org[0] + lane;
+  if (gx < 0 || gx >= nn[0]) gx = ((gx % nn[0]) + nn[0]) % nn[0];  // only periodic x reaches the add
   for (int r = warp; r < rows; r += kMdf3Warps) {
     if (lane >= S) continue;
     const int ly = r % S, lz = r / S;
@@ -613,13 +670,15 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_mdf3_kernel(IbmArgs A, int m
   }
 }
 
+// one MDF iteration m >= 1 in 3D: the interpolation launch, then the spreading launch
 cudaError_t launch_ibm_mdf3(const IbmArgs& A, int m, cudaStream_t s) {
   if (A.np == 0 || m < 1) return cudaSuccess;
   const size_t sm = ibm_mdf3_smem(A.nl, A.box);
-#define IBMLBM_MDF3(SC)                                                 \
-  do {                                                                   \
-    if (m == 1) ibm_mdf3_kernel<SC, 0><<<A.np, kMdf3Threads, sm, s>>>(A, m); \
-    else ibm_mdf3_kernel<SC, 1><<<A.np, kMdf3Threads, sm, s>>>(A, m);        \
+#define IBMLBM_MDF3(SC)                                                    \
+  do {                                                                      \
+    if (m == 1) ibm_interp3_kernel<SC, 0><<<A.np, kMdf3Threads, sm, s>>>(A, m); \
+    else ibm_interp3_kernel<SC, 1><<<A.np, kMdf3Threads, sm, s>>>(A, m);        \
+    ibm_spread3_kernel<SC><<<A.np, kMdf3Threads, sm, s>>>(A);                    \
   } while (0)
   if (A.box == 18) IBMLBM_MDF3(18);
   else if (A.box == 14) IBMLBM_MDF3(14);
@@ -934,7 +993,7 @@ cudaError_t launch_ibm_interp(const IbmArgs& A, int m, cudaStream_t s) {
 #undef IBMLBM_INTERP2
 #undef IBMLBM_INTERP2_ST
   } else {
-    return launch_ibm_mdf3(A, m, s);  // interpolation and spreading in one launch
+    return launch_ibm_mdf3(A, m, s);  // the interpolation launch, then the spreading launch
   }
   return cudaGetLastError();
 }
@@ -977,9 +1036,11 @@ cudaError_t prepare_ibm_spread(int D, size_t smem) {
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   } else {
-    const void* fns[] = {(const void*)ibm_mdf3_kernel<18, 0>, (const void*)ibm_mdf3_kernel<18, 1>,
-                         (const void*)ibm_mdf3_kernel<14, 0>, (const void*)ibm_mdf3_kernel<14, 1>,
-                         (const void*)ibm_mdf3_kernel<0, 0>,  (const void*)ibm_mdf3_kernel<0, 1>};
+    const void* fns[] = {(const void*)ibm_interp3_kernel<18, 0>, (const void*)ibm_interp3_kernel<18, 1>,
+                         (const void*)ibm_interp3_kernel<14, 0>, (const void*)ibm_interp3_kernel<14, 1>,
+                         (const void*)ibm_interp3_kernel<0, 0>,  (const void*)ibm_interp3_kernel<0, 1>,
+                         (const void*)ibm_spread3_kernel<18>,   (const void*)ibm_spread3_kernel<14>,
+                         (const void*)ibm_spread3_kernel<0>};
     e = cudaSuccess;
     for (const void* fn : fns)
       if (e == cudaSuccess)
@@ -1000,7 +1061,7 @@ cudaError_t launch_ibm_spread(const IbmArgs& A, cudaStream_t s) {
       ibm_spread2_kernel<22, false><<<grid, kIbmWarps * 32, sm, s>>>(A, Fuse{});
     else
       ibm_spread2_kernel<0, false><<<grid, kIbmWarps * 32, sm, s>>>(A, Fuse{});
-  }  // 3D spreads inside launch_ibm_interp
+  }  // 3D: the spreading launch follows the interpolation inside launch_ibm_interp
   return cudaGetLastError();
 }
 
