@@ -397,6 +397,73 @@ def _cavity3d(args, dev, local):
     return out
 
 
+def _sec62_point(dev, w, steps=20, reps=5):
+    """One point of the Sec. 6.2 sweeps: MLUPS over `steps` graph-replayed steps, the
+    part times per step, mesh ratio eta = N_p N_L / N_grid and solid fraction."""
+    import torch
+
+    from paper_2002_08855_gb300 import binding, inputs
+
+    X = inputs.place_particles(w)
+    sim = binding.Simulation(w, X, device=str(dev))
+    sim.step(3)
+    sim.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(sim.stream)
+    sim.step(steps)
+    ev1.record(sim.stream)
+    ev1.synchronize()
+    sim.sync()
+    ms = ev0.elapsed_time(ev1) / steps
+    parts = sim.time_parts(reps)
+    sim.close()
+    vp = math.pi * w.diameter ** 2 / 4.0 if w.dim == 2 else math.pi * w.diameter ** 3 / 6.0
+    return {"n_grid": w.n_grid, "n_particles": w.n_particles, "diameter": w.diameter, "n_lag": w.n_lag,
+            "eta": w.n_particles * w.n_lag / w.n_grid, "solid_fraction": w.n_particles * vp / w.n_grid,
+            "mlups": w.n_grid / (ms * 1e3), "ms_per_step": ms,
+            "parts_ms_per_step": {k: v / reps for k, v in parts.items()}}
+
+
+SEED_SWEEP = 2002085500 + 7000  # seeds of the sweep workloads (input-generator base + 7000)
+
+
+def sweep(args):
+    """The two series of Sec. 6.2 (settling particles, density ratio 1.01, 3-point
+    delta with drs = 1.9, walls by non-equilibrium extrapolation): particle count at a
+    fixed lattice (6.2.1, Table 7: 2048^2 with d = 16, 150^3 with d = 12) and particle
+    resolution at fixed solid fraction (6.2.2: 40 d x 40 d with d = 12..48, (5 d)^3 with
+    d = 12..30); N_L = round(pi d) in 2D and round(pi d^2) in 3D (point spacing about
+    one lattice unit).  Prints one JSON line."""
+    import torch
+
+    from paper_2002_08855_gb300 import build
+    from paper_2002_08855_gb300.inputs import Workload
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    base = dict(tau=0.6, delta_kind=3, drs=1.9, density_ratio=1.01, boundary=1, mdf_iters=3)
+    out = {"settings": "Sec. 6.2: density ratio 1.01, 3-point delta, drs 1.9, extrapolation walls, M = 3, tau 0.6",
+           "count_2d": [], "count_3d": [], "resolution_2d": [], "resolution_3d": []}
+    for n in (1, 10, 100, 1000, 4000, 10000):
+        w = Workload(name=f"c2_{n}", dim=2, nx=2048, ny=2048, n_particles=n, n_lag=50, diameter=16.0,
+                     gravity=(0.0, -1e-4, 0.0), seed=SEED_SWEEP + n, **base)
+        out["count_2d"].append(_sec62_point(dev, w))
+    for n in (1, 10, 100, 300, 500):
+        w = Workload(name=f"c3_{n}", dim=3, nx=150, ny=150, nz=150, n_particles=n, n_lag=452, diameter=12.0,
+                     gravity=(0.0, -1e-4, 0.0), seed=SEED_SWEEP + 100 + n, **base)
+        out["count_3d"].append(_sec62_point(dev, w))
+    for d in (12, 18, 24, 36, 48):
+        w = Workload(name=f"r2_{d}", dim=2, nx=40 * d, ny=40 * d, n_particles=400, n_lag=int(round(math.pi * d)),
+                     diameter=float(d), gravity=(0.0, -1e-4, 0.0), seed=SEED_SWEEP + 200 + d, **base)
+        out["resolution_2d"].append(_sec62_point(dev, w))
+    for d in (12, 18, 24, 30):
+        w = Workload(name=f"r3_{d}", dim=3, nx=5 * d, ny=5 * d, nz=5 * d, n_particles=20,
+                     n_lag=int(round(math.pi * d * d)), diameter=float(d), gravity=(0.0, -1e-4, 0.0),
+                     seed=SEED_SWEEP + 300 + d, **base)
+        out["resolution_3d"].append(_sec62_point(dev, w, steps=10, reps=3))
+    print(json.dumps({"sweep": out}))
+
+
 def _pair_search_modes(dev, w2, X2):
     """Pair search and contact part (cell lists against the grid search of Table 5) of
     the headline workload and of the 3D cavity, as the part timer measures it (the
@@ -589,10 +656,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="run the Sec. 6.2 particle-count and resolution sweeps instead")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.sweep:
+        sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run(args)

@@ -625,11 +625,10 @@ int ibm_lbm_init(const ibm_lbm_config* cfg, void* d_workspace, size_t bytes, voi
       if (!std::isfinite(x) || x < -0.5 || x >= d.L[k] - 0.5)
         return fail(IBMLBM_ERR_INVALID_ARG, "particle centre outside the domain");
     }
-  if (cfg->n_particles > 0) {
-    const size_t smem = spread_smem(d.D, cfg->n_lag, d.box);
-    if (smem > 227 * 1024)
-      return fail(IBMLBM_ERR_UNSUPPORTED, "particle too large for the spreading box");
-  }
+  // 2D: one particle's box per warp must fit (fewer warps per block for large ones);
+  // 3D spheres whose box does not fit run the IBM from global memory
+  if (cfg->n_particles > 0 && d.D == 2 && spread_smem(2, cfg->n_lag, d.box) > 227 * 1024)
+    return fail(IBMLBM_ERR_UNSUPPORTED, "particle too large for the spreading box");
   ibm_lbm_handle* h = new ibm_lbm_handle();
   h->cfg = *cfg;
   h->d = d;
@@ -686,7 +685,8 @@ int ibm_lbm_init(const ibm_lbm_config* cfg, void* d_workspace, size_t bytes, voi
     INIT_TRY(cudaMemcpyAsync(h->at<float>(l.ref_f), ref_f.data(), sizeof(float) * ref_f.size(),
                              cudaMemcpyHostToDevice, h->s));
     INIT_TRY(cudaStreamSynchronize(h->s));  // host vectors go out of scope
-    INIT_TRY(prepare_ibm_spread(d.D, spread_smem(d.D, cfg->n_lag, d.box)));
+    if (spread_smem(d.D, cfg->n_lag, d.box) <= 227 * 1024)
+      INIT_TRY(prepare_ibm_spread(d.D, spread_smem(d.D, cfg->n_lag, d.box)));
     if (regenerate_points(h) != IBMLBM_OK) return bail(IBMLBM_ERR_CUDA);
   }
   INIT_TRY(cudaStreamSynchronize(h->s));

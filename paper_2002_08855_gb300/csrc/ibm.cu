@@ -84,6 +84,20 @@ size_t ibm_box2_smem(int box) {
   return sizeof(float) * (size_t)kIbmWarps * (size_t)max(a, c);
 }
 
+// Warps per block of a single run's 2D interpolation and spreading: kIbmWarps, fewer
+// for particles whose boxes would not fit 227 KB of shared memory per block (one warp
+// per particle either way; the kernels take the count from blockDim).
+int ibm2_warps(int box) {
+  const size_t per = sizeof(float) * (size_t)max(interp2_warp_floats(1, box), spread2_warp_floats(box));
+  int w = kIbmWarps;
+  while (w > 1 && per * w > 227 * 1024) --w;
+  return w;
+}
+size_t ibm2_smem(int box) {
+  const int a = interp2_warp_floats(1, box), c = spread2_warp_floats(box);
+  return sizeof(float) * (size_t)ibm2_warps(box) * (size_t)max(a, c);
+}
+
 // box node (row r, column c) -> grid node; false beyond a wall
 __device__ __forceinline__ bool box_node(const Geo& g, int ox, int oy, int r, int c, int& gx, int& gy) {
   gx = ox + c;
@@ -110,7 +124,7 @@ template <int SC, int PARITY, int MODE, int ST>
 __device__ __forceinline__ void interp2_body(const IbmArgs& A, int m, unsigned blk) {
   extern __shared__ __align__(16) float smem_i[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int i = (int)blk * kIbmWarps + wib;
+  const int i = (int)blk * (int)(blockDim.x >> 5) + wib;  // warps per block: blockDim
   if (i >= A.np) return;  // whole warp
   const int S = SC ? SC : A.box, P = box_pitch(S), cells = S * P;
   float2* box = reinterpret_cast<float2*>(smem_i + (size_t)wib * interp2_warp_floats(MODE, S));
@@ -260,7 +274,7 @@ template <int SC>
 __device__ __forceinline__ void spread2_body(const IbmArgs& A, unsigned blk) {
   extern __shared__ __align__(16) float smem2[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int i = (int)blk * kIbmWarps + wib;
+  const int i = (int)blk * (int)(blockDim.x >> 5) + wib;  // warps per block: blockDim
   if (i >= A.np) return;  // whole warp
   const int S = SC ? SC : A.box, P = box_pitch(S), cells = S * P;
   float* base = smem2 + (size_t)wib * spread2_warp_floats(S);
@@ -470,7 +484,7 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_interp3_kernel(IbmArgs A, in
   mdf3_origin(A, i, an, fr, org);
   const float Rm2 = A.mark_radius * A.mark_radius;
   // this lane's column of every box row: grid x, and whether it is inside the domain
-  // (S <= 26 here: a larger box does not fit in shared memory and is rejected at init)
+  // (S <= 22 here: a larger box does not fit in shared memory and takes the global path)
   int gx = org[0] + lane;
   bool xok = lane < S;
   if (gx < 0 || gx >= nn[0]) {
@@ -670,10 +684,132 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_spread3_kernel(IbmArgs A) {
   }
 }
 
+// 3D spheres whose box does not fit in shared memory: the same interpolation and
+// spreading, a half-warp per point (lane (sx, sy) of the 4 x 4 support columns, the
+// 4 z levels in a loop), reading u* + f_IB/2 through the caches and adding each
+// support node's share of dF_b dV to f_IB with a vector atomic.  Two launches per
+// iteration as for the staged kernels, so the iterations stay Jacobi.
+struct Support3 {
+  int s0[3];     // first support node per axis
+  float w[3];    // this lane's weights along x (sx) and y (sy); w[2] unused
+  float wz[4];   // the 4 z weights
+};
+
+__device__ __forceinline__ Support3 support3(const IbmArgs& A, long long b, int sx, int sy) {
+  Support3 S;
+  const int nn[3] = {A.g.nx, A.g.ny, A.g.nz};
+  const int lane_t[2] = {sx, sy};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float f;
+    S.s0[a] = support_first(A.delta_kind, A.Xb[b * 3 + a], f);
+    if (a < 2) {
+      const int gc = S.s0[a] + lane_t[a];
+      S.w[a] = (!A.g.per[a] && (gc < 0 || gc >= nn[a])) ? 0.0f : delta_w(A.delta_kind, (float)(lane_t[a] - 1) - f);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int gc = S.s0[2] + t;
+        S.wz[t] = (!A.g.per[2] && (gc < 0 || gc >= nn[2])) ? 0.0f : delta_w(A.delta_kind, (float)(t - 1) - f);
+      }
+    }
+  }
+  S.w[2] = 0.0f;
+  return S;
+}
+
+// wrapped node coordinate along an axis, or -1 beyond a wall
+__device__ __forceinline__ int wrap_axis(int c, int n, int per) {
+  if (c >= 0 && c < n) return c;
+  return per ? ((c % n) + n) % n : -1;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) ibm_interp3g_kernel(IbmArgs A, int m) {
+  const int lane = threadIdx.x & 31, sx = lane & 3, sy = (lane >> 2) & 3;
+  const long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 4;  // point
+  const bool act = b < A.npts;
+  float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+  if (act) {
+    const Support3 S = support3(A, b, sx, sy);
+    const int gx = wrap_axis(S.s0[0] + sx, A.g.nx, A.g.per[0]);
+    const int gy = wrap_axis(S.s0[1] + sy, A.g.ny, A.g.per[1]);
+    const float wxy = S.w[0] * S.w[1];
+    if (gx >= 0 && gy >= 0 && wxy != 0.0f) {
+      const float4* us4 = reinterpret_cast<const float4*>(A.ustar);
+      const float4* fib4 = reinterpret_cast<const float4*>(A.fib);
+#pragma unroll
+      for (int sz = 0; sz < 4; ++sz) {
+        const int gz = wrap_axis(S.s0[2] + sz, A.g.nz, A.g.per[2]);
+        const float w = wxy * S.wz[sz];
+        if (gz < 0 || w == 0.0f) continue;
+        const long long n = (long long)gx + (long long)A.g.nx * ((long long)gy + (long long)A.g.ny * gz);
+        float4 v = us4[n];
+        if (MODE == 1) {
+          const float4 f = fib4[n];
+          v.x += 0.5f * f.x;
+          v.y += 0.5f * f.y;
+          v.z += 0.5f * f.z;
+        }
+        a0 += w * v.x;
+        a1 += w * v.y;
+        a2 += w * v.z;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+  }
+  if (act && (lane & 15) == 0) {  // dF_b = 2 (U_b - u_b), F_b
+    const float u[3] = {a0, a1, a2};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float d = 2.0f * (A.Ub[b * 3 + c] - u[c]);
+      A.dFb[b * 3 + c] = d;
+      A.Fb[b * 3 + c] = (m == 1) ? d : A.Fb[b * 3 + c] + d;
+      if (m == 1) A.ubs[b * 3 + c] = u[c];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) ibm_spread3g_kernel(IbmArgs A) {
+  const int lane = threadIdx.x & 31, sx = lane & 3, sy = (lane >> 2) & 3;
+  const long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 4;  // point
+  if (b >= A.npts) return;
+  const Support3 S = support3(A, b, sx, sy);
+  const int gx = wrap_axis(S.s0[0] + sx, A.g.nx, A.g.per[0]);
+  const int gy = wrap_axis(S.s0[1] + sy, A.g.ny, A.g.per[1]);
+  const float wxy = S.w[0] * S.w[1];
+  if (gx < 0 || gy < 0 || wxy == 0.0f) return;
+  const float f0 = A.dFb[b * 3] * A.dV, f1 = A.dFb[b * 3 + 1] * A.dV, f2 = A.dFb[b * 3 + 2] * A.dV;
+  float4* fib4 = reinterpret_cast<float4*>(A.fib);
+#pragma unroll
+  for (int sz = 0; sz < 4; ++sz) {
+    const int gz = wrap_axis(S.s0[2] + sz, A.g.nz, A.g.per[2]);
+    const float w = wxy * S.wz[sz];
+    if (gz < 0 || w == 0.0f) continue;
+    const long long n = (long long)gx + (long long)A.g.nx * ((long long)gy + (long long)A.g.ny * gz);
+    atomicAdd(fib4 + n, make_float4(w * f0, w * f1, w * f2, 0.0f));
+  }
+}
+
+// shared memory of the staged 3D kernels; above this a sphere takes the global path
+constexpr size_t kMdf3SmemMax = 227 * 1024;
+
 // one MDF iteration m >= 1 in 3D: the interpolation launch, then the spreading launch
 cudaError_t launch_ibm_mdf3(const IbmArgs& A, int m, cudaStream_t s) {
   if (A.np == 0 || m < 1) return cudaSuccess;
   const size_t sm = ibm_mdf3_smem(A.nl, A.box);
+  if (sm > kMdf3SmemMax) {
+    const unsigned grid = (unsigned)((A.npts * 16 + 255) / 256);
+    if (m == 1) ibm_interp3g_kernel<0><<<grid, 256, 0, s>>>(A, m);
+    else ibm_interp3g_kernel<1><<<grid, 256, 0, s>>>(A, m);
+    ibm_spread3g_kernel<<<grid, 256, 0, s>>>(A);
+    return cudaGetLastError();
+  }
 #define IBMLBM_MDF3(SC)                                                    \
   do {                                                                      \
     if (m == 1) ibm_interp3_kernel<SC, 0><<<A.np, kMdf3Threads, sm, s>>>(A, m); \
@@ -969,14 +1105,15 @@ __global__ void __launch_bounds__(256) regen_kernel(RegenArgs A0, int init, Fuse
 cudaError_t launch_ibm_interp(const IbmArgs& A, int m, cudaStream_t s) {
   if (A.npts == 0) return cudaSuccess;
   if (A.D == 2) {
-    const unsigned grid = (unsigned)((A.np + kIbmWarps - 1) / kIbmWarps);
+    const int W = ibm2_warps(A.box);
+    const unsigned grid = (unsigned)((A.np + W - 1) / W);
     const int mode = (m == 0 || m == 1) ? 0 : 1;  // m < 0: residual pass (box + f_IB/2)
-    const size_t sm = sizeof(float) * kIbmWarps * (size_t)interp2_warp_floats(mode, A.box);
+    const size_t sm = sizeof(float) * W * (size_t)interp2_warp_floats(mode, A.box);
 #define IBMLBM_INTERP2_ST(SC, P)                                                             \
   do {                                                                                        \
-    if (A.store == STORE_F32) ibm_interp2_kernel<SC, P, 0, STORE_F32, false><<<grid, kIbmWarps * 32, sm, s>>>(A, m, Fuse{}); \
-    else if (A.store == STORE_F16) ibm_interp2_kernel<SC, P, 0, STORE_F16, false><<<grid, kIbmWarps * 32, sm, s>>>(A, m, Fuse{}); \
-    else ibm_interp2_kernel<SC, P, 0, STORE_BF16, false><<<grid, kIbmWarps * 32, sm, s>>>(A, m, Fuse{});      \
+    if (A.store == STORE_F32) ibm_interp2_kernel<SC, P, 0, STORE_F32, false><<<grid, W * 32, sm, s>>>(A, m, Fuse{}); \
+    else if (A.store == STORE_F16) ibm_interp2_kernel<SC, P, 0, STORE_F16, false><<<grid, W * 32, sm, s>>>(A, m, Fuse{}); \
+    else ibm_interp2_kernel<SC, P, 0, STORE_BF16, false><<<grid, W * 32, sm, s>>>(A, m, Fuse{});      \
   } while (0)
 #define IBMLBM_INTERP2(SC)                                                                   \
   do {                                                                                        \
@@ -984,7 +1121,7 @@ cudaError_t launch_ibm_interp(const IbmArgs& A, int m, cudaStream_t s) {
       if (A.parity == 0) IBMLBM_INTERP2_ST(SC, 0);                                            \
       else IBMLBM_INTERP2_ST(SC, 1);                                                          \
     } else {                                                                                  \
-      ibm_interp2_kernel<SC, 0, 1, STORE_F32, false><<<grid, kIbmWarps * 32, sm, s>>>(A, m, Fuse{});         \
+      ibm_interp2_kernel<SC, 0, 1, STORE_F32, false><<<grid, W * 32, sm, s>>>(A, m, Fuse{});         \
     }                                                                                         \
   } while (0)
     if (A.box == 16) IBMLBM_INTERP2(16);
@@ -1003,7 +1140,7 @@ cudaError_t launch_ibm_interp(const IbmArgs& A, int m, cudaStream_t s) {
 // shared memory of the spreading kernel used for this dimension (the 2D
 // interpolation kernel uses the same amount)
 size_t spread_smem(int D, int nl, int box) {
-  return D == 2 ? ibm_box2_smem(box) : ibm_mdf3_smem(nl, box);
+  return D == 2 ? ibm2_smem(box) : ibm_mdf3_smem(nl, box);
 }
 
 cudaError_t prepare_ibm_spread(int D, size_t smem) {
@@ -1053,14 +1190,15 @@ cudaError_t prepare_ibm_spread(int D, size_t smem) {
 cudaError_t launch_ibm_spread(const IbmArgs& A, cudaStream_t s) {
   if (A.np == 0) return cudaSuccess;
   if (A.D == 2) {
-    const unsigned grid = (unsigned)((A.np + kIbmWarps - 1) / kIbmWarps);
-    const size_t sm = sizeof(float) * kIbmWarps * (size_t)spread2_warp_floats(A.box);
+    const int W = ibm2_warps(A.box);
+    const unsigned grid = (unsigned)((A.np + W - 1) / W);
+    const size_t sm = sizeof(float) * W * (size_t)spread2_warp_floats(A.box);
     if (A.box == 16)
-      ibm_spread2_kernel<16, false><<<grid, kIbmWarps * 32, sm, s>>>(A, Fuse{});
+      ibm_spread2_kernel<16, false><<<grid, W * 32, sm, s>>>(A, Fuse{});
     else if (A.box == 22)
-      ibm_spread2_kernel<22, false><<<grid, kIbmWarps * 32, sm, s>>>(A, Fuse{});
+      ibm_spread2_kernel<22, false><<<grid, W * 32, sm, s>>>(A, Fuse{});
     else
-      ibm_spread2_kernel<0, false><<<grid, kIbmWarps * 32, sm, s>>>(A, Fuse{});
+      ibm_spread2_kernel<0, false><<<grid, W * 32, sm, s>>>(A, Fuse{});
   }  // 3D: the spreading launch follows the interpolation inside launch_ibm_interp
   return cudaGetLastError();
 }

@@ -35,11 +35,16 @@ CASES = [
     # near contact: the supports of neighbouring particles share nodes
     (2, (64, 48, 1), (0, 0, 0), [[20.2, 23.9], [31.1, 25.3]], 10.0, 31),
     (3, (40, 36, 34), (0, 0, 0), [[12.5, 17.2, 16.9], [25.3, 17.9, 17.4], [18.9, 28.1, 16.2]], 12.0, 452),
+    # large particles: 3D spheres whose box does not fit in shared memory (the IBM runs
+    # from global memory), a 2D pair whose boxes take fewer warps per block
+    (3, (48, 44, 46), (0, 0, 0), [[23.2, 21.7, 22.9]], 20.0, 1257),
+    (3, (40, 40, 40), (1, 1, 1), [[2.5, 38.1, 20.3]], 18.0, 1018),
+    (2, (120, 110, 1), (0, 0, 0), [[50.3, 55.6], [93.0, 54.2]], 40.0, 126),
 ]
 
 
 # the 3-point delta function (drs = 1.9, Sec. 2.2) on a subset of the cases
-CASES3 = [CASES[1], CASES[2], CASES[3], CASES[4], CASES[5], CASES[6]]
+CASES3 = [CASES[1], CASES[2], CASES[3], CASES[4], CASES[5], CASES[6], CASES[7], CASES[9]]
 
 
 @pytest.mark.parametrize("dim,shape,per,xc,D,nl", CASES)
@@ -122,4 +127,23 @@ def test_mdf_iterations_are_jacobi_across_many_spheres():
     pg, po = sim.get_particles(), ref.get_particles()
     assert rel_l2(pg["F_h"], po["F_h"]) < 1e-5
     assert rel_l2(sim.get_pdfs().cpu().numpy(), ref.get_pdfs()) < 1e-5
+    sim.close()
+
+
+def test_large_spheres_several_steps():
+    """Four spheres of d = 18 (box beyond shared memory: the global-memory IBM) moving
+    near contact for 30 steps, against the oracle."""
+    require_gpu()
+    w = Workload(name="big3", dim=3, nx=64, ny=60, nz=62, tau=0.7, n_particles=4, n_lag=1018,
+                 diameter=18.0, density_ratio=1.5, gravity=(0.0, -1e-5, 0.0))
+    xc = np.array([[18.5, 20.2, 30.1], [38.9, 21.0, 30.6], [28.4, 39.8, 29.5], [29.0, 30.1, 49.0]])
+    U = np.array([[1e-3, 0.0, 0.0], [-1e-3, 5e-4, 0.0], [0.0, -1e-3, 2e-4], [0.0, 0.0, -1e-3]])
+    sim, ref = _pair(w, xc, U)
+    sim.step(30)
+    ref.step(30)
+    pg, po = sim.get_particles(), ref.get_particles()
+    assert rel_l2(pg["X"] - xc, po["X"] - xc) < 1e-5
+    _, ug = sim.get_fields()
+    _, uo = ref.get_fields()
+    assert rel_l2(ug.cpu().numpy(), uo) < 1e-5
     sim.close()
