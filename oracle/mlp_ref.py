@@ -84,3 +84,59 @@ def features_2d(U_b, u_b_star, n_lag):
         X[:, 3 * j] = dj[:, 0] * nx + dj[:, 1] * ny
         X[:, 3 * j + 1] = -dj[:, 0] * ny + dj[:, 1] * nx
     return X
+
+
+def sphere_stencil(ref):
+    """Frame and neighbour order of every point of a sphere (3D reading of the learned
+    initializer's stencil), from the point offsets ref [N_L][3] of the reference sphere:
+      n = r_k / |r_k|;  t1 = (a x n) / |a x n| with a = e_z, or e_x where |n_z| >= 0.9;
+      t2 = n x t1;
+      neighbours: the 8 other points nearest to point k (distance |r_j - r_k|, ties by
+      index), ordered by their azimuth atan2((r_j - r_k).t2, (r_j - r_k).t1) in [0, 2 pi)
+      (ties by index).
+    Distances and azimuths are compared after rounding to 1e-9, so ties resolve by index
+    alike on any machine.  Returns (frames [N_L][3][3] rows n, t1, t2; nbr [N_L][8])."""
+    r = np.asarray(ref, dtype=np.float64)
+    nl = r.shape[0]
+    n = r / np.linalg.norm(r, axis=1, keepdims=True)
+    a = np.where(np.abs(n[:, 2:3]) < 0.9, np.array([[0.0, 0.0, 1.0]]), np.array([[1.0, 0.0, 0.0]]))
+    t1 = np.cross(a, n)
+    t1 /= np.linalg.norm(t1, axis=1, keepdims=True)
+    t2 = np.cross(n, t1)
+    frames = np.stack([n, t1, t2], axis=1)
+    nbr = np.zeros((nl, 8), dtype=np.int64)
+    idx = np.arange(nl)
+    for k in range(nl):
+        dist = np.round(np.linalg.norm(r - r[k], axis=1), 9)
+        cand = [j for j in np.lexsort((idx, dist)) if j != k][:8]
+        rel = r[cand] - r[k]
+        az = np.mod(np.arctan2(rel @ t2[k], rel @ t1[k]), 2.0 * np.pi)
+        order = np.lexsort((np.asarray(cand), np.round(az, 9)))
+        nbr[k] = np.asarray(cand)[order]
+    return frames, nbr
+
+
+def features_3d(U_b, u_b_star, ref):
+    """[npts][27] deficit stencils of spheres: for point k, U_b - u_b* at point k and at
+    its 8 stencil neighbours (sphere_stencil order), each as (normal, t1, t2) components
+    in the frame of point k."""
+    d = np.asarray(U_b, dtype=np.float64) - np.asarray(u_b_star, dtype=np.float64)
+    frames, nbr = sphere_stencil(ref)
+    nl = frames.shape[0]
+    npts = d.shape[0]
+    k = np.arange(npts) % nl
+    base = np.arange(npts) - k
+    X = np.zeros((npts, N_IN))
+    pts = np.concatenate([k[:, None], nbr[k]], axis=1)  # [npts][9]
+    for j in range(9):
+        dj = d[base + pts[:, j]]
+        X[:, 3 * j:3 * j + 3] = np.einsum("pc,pac->pa", dj, frames[k])
+    return X
+
+
+def to_frame_3d(F, ref):
+    """Per-point vectors F [npts][3] in the frame of their point (normal, t1, t2)."""
+    frames, _ = sphere_stencil(ref)
+    nl = frames.shape[0]
+    k = np.arange(F.shape[0]) % nl
+    return np.einsum("pc,pac->pa", np.asarray(F, dtype=np.float64), frames[k])

@@ -58,3 +58,60 @@ def test_features_are_frame_components_of_the_stencil():
         a = (j - 4) * 2 * np.pi / nl
         assert np.allclose(X[:, 3 * j], np.cos(a)) and np.allclose(X[:, 3 * j + 1], np.sin(a))
     assert np.all(X[:, 2::3] == 0.0)
+
+
+def _sphere_ref(nl=452, d=12.0):
+    """Point offsets of the oracle's reference sphere (Fibonacci lattice, Sec. 2.2)."""
+    import oracle
+
+    w = dict(dim=3, nx=24, ny=24, nz=24, n_particles=1, n_lag=nl, diameter=d, mdf_iters=1)
+    S = oracle.Sim(w, np.array([[11.5, 11.5, 11.5]]))
+    S.step(1)
+    return S.get_lagrangian()["X_b"] - np.array([11.5, 11.5, 11.5])
+
+
+def test_sphere_stencil_frames_and_neighbours():
+    from scipy.spatial import cKDTree
+
+    ref = _sphere_ref()
+    frames, nbr = mlp_ref.sphere_stencil(ref)
+    n, t1, t2 = frames[:, 0], frames[:, 1], frames[:, 2]
+    assert np.allclose(np.einsum("kij,klj->kil", frames, frames), np.eye(3)[None], atol=1e-12)
+    assert np.allclose(np.linalg.det(frames), 1.0)  # right-handed (n, t1, t2)
+    assert np.allclose(n, ref / np.linalg.norm(ref, axis=1, keepdims=True))  # outward normal
+    dist, idx = cKDTree(ref).query(ref, k=9)  # the point itself and its 8 nearest
+    for k in range(len(ref)):
+        assert set(nbr[k]) == set(idx[k, 1:]) or np.isclose(dist[k, 8], np.sort(
+            np.linalg.norm(ref[nbr[k]] - ref[k], axis=1))[-1])
+        rel = ref[nbr[k]] - ref[k]
+        az = np.mod(np.arctan2(rel @ t2[k], rel @ t1[k]), 2 * np.pi)
+        assert np.all(np.diff(az) >= -1e-9)  # azimuth order
+
+
+def test_sphere_features_are_frame_components_of_the_stencil():
+    ref = _sphere_ref()
+    frames, nbr = mlp_ref.sphere_stencil(ref)
+    nl = len(ref)
+    unit = ref / np.linalg.norm(ref, axis=1, keepdims=True)
+    # purely radial unit deficits: the point's own triple is (1, 0, 0)
+    X = mlp_ref.features_3d(unit, np.zeros_like(unit), ref)
+    assert np.allclose(X[:, 0:3], [1.0, 0.0, 0.0])
+    # one uniform deficit e everywhere: the nine triples of point k all equal e in k's frame
+    e = np.array([0.3, -1.2, 0.7])
+    X = mlp_ref.features_3d(np.tile(e, (2 * nl, 1)), np.zeros((2 * nl, 3)), ref)  # two spheres
+    want = np.einsum("c,kac->ka", e, frames)
+    for j in range(9):
+        assert np.allclose(X[:nl, 3 * j:3 * j + 3], want) and np.allclose(X[nl:, 3 * j:3 * j + 3], want)
+    # neighbour triples come from the neighbour's deficit: a field that is zero except at
+    # point 5 shows up at (k, j) exactly where nbr[k][j - 1] == 5
+    d = np.zeros((nl, 3))
+    d[5] = e
+    X = mlp_ref.features_3d(d, np.zeros_like(d), ref)
+    for k in range(nl):
+        for j in range(1, 9):
+            hit = nbr[k][j - 1] == 5
+            assert np.allclose(X[k, 3 * j:3 * j + 3], frames[k] @ e if hit else 0.0)
+    # the output frame is orthonormal: back-transforming recovers the vectors
+    F = np.random.default_rng(1).normal(size=(nl, 3))
+    Fl = mlp_ref.to_frame_3d(F, ref)
+    assert np.allclose(np.einsum("ka,kac->kc", Fl, frames), F)
