@@ -248,12 +248,18 @@ int ibm_lbm_pair_search_static(int32_t dim, const int32_t* n_nodes, const int32_
                                int64_t* h_count, void* stream);
 
 /* ---------------------------------------------------------------------------
- * Learned MDF initializer (2D; no counterpart in the paper, which runs the plain
+ * Learned MDF initializer (no counterpart in the paper, which runs the plain
  * iteration).  A perceptron 27 -> 64 -> 64 -> 3 (ReLU) maps the velocity-deficit
- * stencil of a Lagrangian point, U_b - u_b* (u_b* = D_I u*, Eq. 12) at the point and at
- * the 4 points on either side of it on the same circle, each as (normal, tangent, 0)
- * components in the frame of the point, to the force of the first MDF iteration in
- * that frame.  Parameters: ibm_lbm_mlp_param_count() floats, row-major
+ * stencil of a Lagrangian point, U_b - u_b* (u_b* = D_I u*, Eq. 12), to the force of
+ * the first MDF iteration, both in a frame of the point:
+ *   2D: the deficits at the point and at the 4 points on either side of it on the same
+ *       circle, as (normal, tangent, 0) components;
+ *   3D: the deficits at the point and at its 8 nearest other points on the reference
+ *       sphere, ordered by azimuth about the normal, as (n, t1, t2) components with
+ *       n = r / |r|, t1 = (a x n) / |a x n| (a = e_z, or e_x where |n_z| >= 0.9),
+ *       t2 = n x t1 (distances and azimuths compared after rounding to 1e-9, ties by
+ *       index).
+ * Parameters: ibm_lbm_mlp_param_count() floats, row-major
  * W1[27][64] b1[64] W2[64][64] b2[64] W3[64][3] b3[3] in_scale out_scale (the network
  * sees features * in_scale; its output is scaled by out_scale).
  */
@@ -264,14 +270,15 @@ int ibm_lbm_set_mlp(ibm_lbm_handle* h, const float* h_params);
 
 /* Training samples of the last step: d_X [npts][27] features, d_Y [npts][3] the step's
  * total MDF force F_b in each point's frame (device arrays).  Synchronises the stream.
- * Errors: INVALID_ARG before the first step or for a 3D run. */
+ * Errors: INVALID_ARG before the first step. */
 int ibm_lbm_mdf_samples(ibm_lbm_handle* h, float* d_X, float* d_Y);
 
 /* Record, in every later step, the boundary-velocity residual r_b = U_b - D_I u^(M)
- * after the last MDF iteration (one extra interpolation launch; 2D). */
+ * after the last MDF iteration (one extra interpolation launch). */
 int ibm_lbm_set_residual_tracking(ibm_lbm_handle* h, int32_t on);
 
-/* RMS and maximum over the points of |r_b| of the last tracked step (syncs). */
+/* RMS over the points and components of r_b, sqrt(sum_b sum_c r_bc^2 / (N_p N_L dim)),
+ * and the largest |r_bc|, of the last tracked step (syncs). */
 int ibm_lbm_get_mdf_residual(ibm_lbm_handle* h, double* rms, double* maxabs);
 
 /* Training kernels (FP32; device pointers; loss = mean over the batch of the squared

@@ -72,6 +72,7 @@ struct Layout {
   size_t f, ustar, fib, mask;
   size_t X0, X1, U, Om, Fh, Th, FhN, ThN, acc, alp, Pint, Lint, Pprev, Lprev, Fc;
   size_t Uf, Omf, ref_fix, ref_f, Xcf, Xb0, Xb1, Ub0, Ub1, Fb, dFb, ubs, ubox, res, mlp, mlp_img;
+  size_t frame3, nbr3;
   size_t cell_count, cell_ids, nbr, nbr_count, gt, pairs, status;
   size_t grid, over, over_count;
   size_t total;
@@ -97,9 +98,9 @@ int check_config(const ibm_lbm_config* c) {
   if (c->pdf_storage < IBMLBM_PDF_FP32 || c->pdf_storage > IBMLBM_PDF_BF16)
     return fail(IBMLBM_ERR_INVALID_ARG, "pdf_storage must be 0 (FP32), 1 (FP16) or 2 (BF16)");
   if (c->mlp_init != 0 && c->mlp_init != 1) return fail(IBMLBM_ERR_INVALID_ARG, "mlp_init must be 0 or 1");
-  if (c->mlp_init && (c->dim != 2 || c->mdf_iters < 1 || c->n_lag > mlp_max_points()))
+  if (c->mlp_init && (c->mdf_iters < 1 || (c->dim == 2 && c->n_lag > mlp_max_points())))
     return fail(IBMLBM_ERR_UNSUPPORTED,
-                "the learned initializer needs a 2D run with mdf_iters >= 1 and n_lag <= 256");
+                "the learned initializer needs mdf_iters >= 1 (and n_lag <= 256 in 2D)");
   if (c->boundary < 0 || c->boundary > 2) return fail(IBMLBM_ERR_INVALID_ARG, "boundary must be 0, 1 or 2");
   if (c->boundary) {
     const int32_t nn[3] = {c->nx, c->ny, c->nz};
@@ -243,9 +244,12 @@ Layout carve(const ibm_lbm_config* c, const Derived& d) {
   l.Fb = cv.take(sizeof(float) * npts * D);
   l.dFb = cv.take(sizeof(float) * npts * D);
   l.ubs = cv.take(sizeof(float) * npts * D);
-  l.res = cv.take(D == 2 ? sizeof(float) * npts * D : 0);   // residual pass (2D)
-  l.mlp = cv.take(D == 2 ? sizeof(float) * kMlpParams : 0);  // learned initializer
-  l.mlp_img = cv.take(D == 2 ? mlp_image_bytes() : 0);
+  l.res = cv.take(sizeof(float) * npts * D);                 // residual pass
+  l.mlp = cv.take(sizeof(float) * kMlpParams);               // learned initializer
+  l.mlp_img = cv.take(mlp_image_bytes());
+  // 3D stencil of the learned initializer: frames [nl][9] and neighbours [nl][8]
+  l.frame3 = cv.take(D == 3 ? sizeof(float) * 9 * (size_t)c->n_lag : 0);
+  l.nbr3 = cv.take(D == 3 ? sizeof(int) * 8 * (size_t)c->n_lag : 0);
   // 2D: u* of each particle's node box (box rows of box_pitch(box) float2 cells)
   l.ubox = cv.take(D == 2 ? sizeof(float) * np * 2 * (size_t)d.box * box_pitch(d.box) : 0);
   const size_t ncells = (size_t)d.nc[0] * d.nc[1] * d.nc[2];
@@ -282,6 +286,60 @@ std::vector<double> reference_points(int D, int nl, double R) {
     }
   }
   return r;
+}
+
+// Stencil of the 3D learned initializer on the reference sphere (offsets ref [nl][3]).
+// Per point k: the frame rows n = r_k / |r_k|, t1 = (a x n) / |a x n| (a = e_z, or e_x
+// where |n_z| >= 0.9), t2 = n x t1; and its 8 nearest other points (distance |r_j - r_k|,
+// ties by index) ordered by azimuth atan2((r_j - r_k).t2, (r_j - r_k).t1) in [0, 2 pi)
+// (ties by index).  Distances and azimuths are compared after rounding to 1e-9, so
+// the order is the same on any machine.
+void sphere_stencil(const std::vector<double>& ref, int nl, std::vector<float>& frames, std::vector<int>& nbrs) {
+  frames.assign((size_t)9 * nl, 0.0f);
+  nbrs.assign((size_t)8 * nl, 0);
+  auto rnd = [](double v) { return std::nearbyint(v * 1e9) / 1e9; };
+  auto cross = [](const double* a, const double* b, double* c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+  };
+  std::vector<std::pair<double, int>> cand((size_t)nl);
+  for (int k = 0; k < nl; ++k) {
+    const double* rk = &ref[3 * (size_t)k];
+    const double len = std::sqrt(rk[0] * rk[0] + rk[1] * rk[1] + rk[2] * rk[2]);
+    const double n[3] = {rk[0] / len, rk[1] / len, rk[2] / len};
+    const double a[3] = {std::fabs(n[2]) < 0.9 ? 0.0 : 1.0, 0.0, std::fabs(n[2]) < 0.9 ? 1.0 : 0.0};
+    double t1[3], t2[3];
+    cross(a, n, t1);
+    const double l1 = std::sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+    for (int c = 0; c < 3; ++c) t1[c] /= l1;
+    cross(n, t1, t2);
+    for (int c = 0; c < 3; ++c) {
+      frames[9 * (size_t)k + c] = (float)n[c];
+      frames[9 * (size_t)k + 3 + c] = (float)t1[c];
+      frames[9 * (size_t)k + 6 + c] = (float)t2[c];
+    }
+    cand.clear();
+    for (int j = 0; j < nl; ++j) {
+      if (j == k) continue;
+      const double* rj = &ref[3 * (size_t)j];
+      const double dx = rj[0] - rk[0], dy = rj[1] - rk[1], dz = rj[2] - rk[2];
+      cand.push_back({rnd(std::sqrt(dx * dx + dy * dy + dz * dz)), j});
+    }
+    const size_t m = std::min<size_t>(8, cand.size());
+    std::partial_sort(cand.begin(), cand.begin() + m, cand.end());
+    std::vector<std::pair<double, int>> az(m);
+    for (size_t q = 0; q < m; ++q) {
+      const int j = cand[q].second;
+      const double* rj = &ref[3 * (size_t)j];
+      const double d[3] = {rj[0] - rk[0], rj[1] - rk[1], rj[2] - rk[2]};
+      double phi = std::atan2(d[0] * t2[0] + d[1] * t2[1] + d[2] * t2[2], d[0] * t1[0] + d[1] * t1[1] + d[2] * t1[2]);
+      if (phi < 0.0) phi += 2.0 * kPi;
+      az[q] = {rnd(phi), j};
+    }
+    std::sort(az.begin(), az.end());
+    for (size_t q = 0; q < 8; ++q) nbrs[8 * (size_t)k + q] = q < m ? az[q].second : k;
+  }
 }
 
 }  // namespace
@@ -357,6 +415,8 @@ struct ibm_lbm_handle {
     a.dFb = at<float>(l.dFb);
     a.ubs = at<float>(l.ubs);
     a.res = at<float>(l.res);
+    a.frame3 = at<float>(l.frame3);
+    a.nbr3 = at<int>(l.nbr3);
     a.Xc = X(parity);
     a.Xcf = at<long long>(l.Xcf);
     a.ref_f = at<float>(l.ref_f);
@@ -485,18 +545,16 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
       ++k;
     }
     for (int m = 1; m <= h->cfg.mdf_iters; ++m) {
-      CUDA_TRY(launch_ibm_interp(ia, m, s));  // 3D: interpolation, then spreading
-      k += h->d.D == 3 ? 2 : 1;
-      if (m == 1 && h->cfg.mlp_init) {  // learned first force (2D)
+      CUDA_TRY(launch_ibm_interp(ia, m, s));
+      ++k;
+      if (m == 1 && h->cfg.mlp_init) {  // learned first force
         CUDA_TRY(launch_mlp_step(ia, h->at<float>(h->l.mlp), h->at<void>(h->l.mlp_img), s));
         ++k;
       }
-      if (h->d.D == 2) {
-        CUDA_TRY(launch_ibm_spread(ia, s));
-        ++k;
-      }
+      CUDA_TRY(launch_ibm_spread(ia, s));
+      ++k;
     }
-    if (h->track_res && h->d.D == 2 && h->cfg.mdf_iters > 0) {
+    if (h->track_res && h->cfg.mdf_iters > 0) {
       CUDA_TRY(launch_ibm_interp(ia, -1, s));
       ++k;
     }
@@ -684,6 +742,15 @@ int ibm_lbm_init(const ibm_lbm_config* cfg, void* d_workspace, size_t bytes, voi
                              sizeof(long long) * ref_fix.size(), cudaMemcpyHostToDevice, h->s));
     INIT_TRY(cudaMemcpyAsync(h->at<float>(l.ref_f), ref_f.data(), sizeof(float) * ref_f.size(),
                              cudaMemcpyHostToDevice, h->s));
+    std::vector<float> frames;
+    std::vector<int> nbrs;
+    if (d.D == 3) {
+      sphere_stencil(ref, cfg->n_lag, frames, nbrs);
+      INIT_TRY(cudaMemcpyAsync(h->at<float>(l.frame3), frames.data(), sizeof(float) * frames.size(),
+                               cudaMemcpyHostToDevice, h->s));
+      INIT_TRY(cudaMemcpyAsync(h->at<int>(l.nbr3), nbrs.data(), sizeof(int) * nbrs.size(),
+                               cudaMemcpyHostToDevice, h->s));
+    }
     INIT_TRY(cudaStreamSynchronize(h->s));  // host vectors go out of scope
     if (spread_smem(d.D, cfg->n_lag, d.box) <= 227 * 1024)
       INIT_TRY(prepare_ibm_spread(d.D, spread_smem(d.D, cfg->n_lag, d.box)));
@@ -944,7 +1011,6 @@ int ibm_lbm_set_mlp(ibm_lbm_handle* h, const float* h_params) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (!h_params) return fail(IBMLBM_ERR_INVALID_ARG, "h_params is NULL");
-  if (h->d.D != 2) return fail(IBMLBM_ERR_UNSUPPORTED, "the learned initializer is 2D");
   CUDA_TRY(cudaMemcpyAsync(h->at<float>(h->l.mlp), h_params, sizeof(float) * kMlpParams,
                            cudaMemcpyHostToDevice, h->s));
   CUDA_TRY(launch_mlp_image(h->at<float>(h->l.mlp), h->at<void>(h->l.mlp_img), h->s));
@@ -957,8 +1023,7 @@ int ibm_lbm_mdf_samples(ibm_lbm_handle* h, float* d_X, float* d_Y) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (!d_X || !d_Y) return fail(IBMLBM_ERR_INVALID_ARG, "sample arrays are NULL");
-  if (h->d.D != 2 || h->step < 1)
-    return fail(IBMLBM_ERR_INVALID_ARG, "samples need a 2D run after its first step");
+  if (h->step < 1) return fail(IBMLBM_ERR_INVALID_ARG, "samples need a run after its first step");
   CUDA_TRY(launch_mlp_samples(h->ibm((int)((h->step - 1) & 1)), d_X, d_Y, h->s));
   CUDA_TRY(cudaStreamSynchronize(h->s));
   return IBMLBM_OK;
@@ -967,7 +1032,6 @@ int ibm_lbm_mdf_samples(ibm_lbm_handle* h, float* d_X, float* d_Y) {
 int ibm_lbm_set_residual_tracking(ibm_lbm_handle* h, int32_t on) {
   int rc = check_handle(h);
   if (rc) return rc;
-  if (h->d.D != 2) return fail(IBMLBM_ERR_UNSUPPORTED, "residual tracking is 2D");
   if ((bool)on == h->track_res) return IBMLBM_OK;
   CUDA_TRY(cudaStreamSynchronize(h->s));
   for (int p = 0; p < 2; ++p) {  // the captured steps change: capture again
@@ -983,19 +1047,18 @@ int ibm_lbm_get_mdf_residual(ibm_lbm_handle* h, double* rms, double* maxabs) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (h->res_step < 0) return fail(IBMLBM_ERR_INVALID_ARG, "no tracked step yet");
-  const size_t npts = (size_t)h->d.npts;
-  std::vector<float> r(npts * 2);
+  const size_t npts = (size_t)h->d.npts, D = (size_t)h->d.D;
+  std::vector<float> r(npts * D);
   if (npts)
     CUDA_TRY(cudaMemcpyAsync(r.data(), h->at<float>(h->l.res), sizeof(float) * r.size(),
                              cudaMemcpyDeviceToHost, h->s));
   CUDA_TRY(cudaStreamSynchronize(h->s));
   double s2 = 0.0, mx = 0.0;
-  for (size_t b = 0; b < npts; ++b) {
-    const double v = (double)r[2 * b] * r[2 * b] + (double)r[2 * b + 1] * r[2 * b + 1];
-    s2 += v;
-    mx = std::max(mx, std::sqrt(v));
+  for (size_t q = 0; q < npts * D; ++q) {
+    s2 += (double)r[q] * r[q];
+    mx = std::max(mx, std::fabs((double)r[q]));
   }
-  if (rms) *rms = npts ? std::sqrt(s2 / npts) : 0.0;
+  if (rms) *rms = npts ? std::sqrt(s2 / (double)(npts * D)) : 0.0;
   if (maxabs) *maxabs = mx;
   return IBMLBM_OK;
 }

@@ -181,7 +181,9 @@ struct IbmArgs {
   double* Lint;      // [np][3] interior angular momentum
   double* FhN;       // [np][D] -dV sum_b F_b of this step
   double* ThN;       // [np][3] -dV sum_b r_b x F_b of this step
-  float* res;        // [npts][D] U_b - D_I u^(M) (residual pass, 2D)
+  float* res;        // [npts][D] U_b - D_I u^(M) (residual pass)
+  const float* frame3;  // 3D learned initializer: [nl][3][3] rows n, t1, t2 of each point
+  const int* nbr3;      // 3D learned initializer: [nl][8] stencil neighbours of each point
   uint32_t* status;
 };
 

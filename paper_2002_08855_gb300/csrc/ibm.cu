@@ -576,13 +576,18 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_interp3_kernel(IbmArgs A, in
     }
   }
   __syncthreads();
-  // dF_b = 2 (U_b - u_b) and F_b, one thread per point (coalesced)
+  // dF_b = 2 (U_b - u_b) and F_b, one thread per point (coalesced); m < 0: the
+  // residual U_b - u_b after the last iteration
   for (int k = tid; k < A.nl; k += kMdf3Threads) {
     const long long b = (long long)i * A.nl + k;
     const float* row = tab + (size_t)k * kTab3;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float u = row[13 + c];
+      if (m < 0) {
+        A.res[b * 3 + c] = A.Ub[b * 3 + c] - u;
+        continue;
+      }
       const float d = 2.0f * (A.Ub[b * 3 + c] - u);
       A.dFb[b * 3 + c] = d;
       A.Fb[b * 3 + c] = (m == 1) ? d : A.Fb[b * 3 + c] + d;
@@ -763,10 +768,14 @@ __global__ void __launch_bounds__(256) ibm_interp3g_kernel(IbmArgs A, int m) {
     a1 += __shfl_xor_sync(0xffffffffu, a1, o);
     a2 += __shfl_xor_sync(0xffffffffu, a2, o);
   }
-  if (act && (lane & 15) == 0) {  // dF_b = 2 (U_b - u_b), F_b
+  if (act && (lane & 15) == 0) {  // dF_b = 2 (U_b - u_b), F_b; m < 0: the residual
     const float u[3] = {a0, a1, a2};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
+      if (m < 0) {
+        A.res[b * 3 + c] = A.Ub[b * 3 + c] - u[c];
+        continue;
+      }
       const float d = 2.0f * (A.Ub[b * 3 + c] - u[c]);
       A.dFb[b * 3 + c] = d;
       A.Fb[b * 3 + c] = (m == 1) ? d : A.Fb[b * 3 + c] + d;
@@ -799,27 +808,42 @@ __global__ void __launch_bounds__(256) ibm_spread3g_kernel(IbmArgs A) {
 // shared memory of the staged 3D kernels; above this a sphere takes the global path
 constexpr size_t kMdf3SmemMax = 227 * 1024;
 
-// one MDF iteration m >= 1 in 3D: the interpolation launch, then the spreading launch
-cudaError_t launch_ibm_mdf3(const IbmArgs& A, int m, cudaStream_t s) {
-  if (A.np == 0 || m < 1) return cudaSuccess;
+// 3D interpolation of MDF iteration m >= 1 (m < 0: the residual pass after the last
+// iteration), staged per sphere or, for spheres whose box exceeds shared memory, from
+// global memory
+cudaError_t launch_ibm_interp3(const IbmArgs& A, int m, cudaStream_t s) {
+  if (A.np == 0 || m == 0) return cudaSuccess;
   const size_t sm = ibm_mdf3_smem(A.nl, A.box);
   if (sm > kMdf3SmemMax) {
     const unsigned grid = (unsigned)((A.npts * 16 + 255) / 256);
     if (m == 1) ibm_interp3g_kernel<0><<<grid, 256, 0, s>>>(A, m);
     else ibm_interp3g_kernel<1><<<grid, 256, 0, s>>>(A, m);
-    ibm_spread3g_kernel<<<grid, 256, 0, s>>>(A);
     return cudaGetLastError();
   }
-#define IBMLBM_MDF3(SC)                                                    \
-  do {                                                                      \
+#define IBMLBM_I3(SC)                                                          \
+  do {                                                                          \
     if (m == 1) ibm_interp3_kernel<SC, 0><<<A.np, kMdf3Threads, sm, s>>>(A, m); \
     else ibm_interp3_kernel<SC, 1><<<A.np, kMdf3Threads, sm, s>>>(A, m);        \
-    ibm_spread3_kernel<SC><<<A.np, kMdf3Threads, sm, s>>>(A);                    \
   } while (0)
-  if (A.box == 18) IBMLBM_MDF3(18);
-  else if (A.box == 14) IBMLBM_MDF3(14);
-  else IBMLBM_MDF3(0);
-#undef IBMLBM_MDF3
+  if (A.box == 18) IBMLBM_I3(18);
+  else if (A.box == 14) IBMLBM_I3(14);
+  else IBMLBM_I3(0);
+#undef IBMLBM_I3
+  return cudaGetLastError();
+}
+
+// 3D spreading of an MDF iteration (after its interpolation launch)
+cudaError_t launch_ibm_spread3(const IbmArgs& A, cudaStream_t s) {
+  if (A.np == 0) return cudaSuccess;
+  const size_t sm = ibm_mdf3_smem(A.nl, A.box);
+  if (sm > kMdf3SmemMax)
+    ibm_spread3g_kernel<<<(unsigned)((A.npts * 16 + 255) / 256), 256, 0, s>>>(A);
+  else if (A.box == 18)
+    ibm_spread3_kernel<18><<<A.np, kMdf3Threads, sm, s>>>(A);
+  else if (A.box == 14)
+    ibm_spread3_kernel<14><<<A.np, kMdf3Threads, sm, s>>>(A);
+  else
+    ibm_spread3_kernel<0><<<A.np, kMdf3Threads, sm, s>>>(A);
   return cudaGetLastError();
 }
 
@@ -1130,7 +1154,7 @@ cudaError_t launch_ibm_interp(const IbmArgs& A, int m, cudaStream_t s) {
 #undef IBMLBM_INTERP2
 #undef IBMLBM_INTERP2_ST
   } else {
-    return launch_ibm_mdf3(A, m, s);  // the interpolation launch, then the spreading launch
+    return launch_ibm_interp3(A, m, s);
   }
   return cudaGetLastError();
 }
@@ -1199,7 +1223,9 @@ cudaError_t launch_ibm_spread(const IbmArgs& A, cudaStream_t s) {
       ibm_spread2_kernel<22, false><<<grid, W * 32, sm, s>>>(A, Fuse{});
     else
       ibm_spread2_kernel<0, false><<<grid, W * 32, sm, s>>>(A, Fuse{});
-  }  // 3D: the spreading launch follows the interpolation inside launch_ibm_interp
+  } else {
+    return launch_ibm_spread3(A, s);
+  }
   return cudaGetLastError();
 }
 

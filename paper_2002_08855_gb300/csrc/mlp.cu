@@ -1,4 +1,4 @@
-// Learned initializer of multi-direct forcing (2D): a multilayer perceptron maps each
+// Learned initializer of multi-direct forcing: a multilayer perceptron maps each
 // Lagrangian point's local velocity-deficit stencil to the force of the first MDF
 // iteration; the plain iterations (Sec. 2.2, MDF) then run from it as before.  No
 // counterpart in the paper (the MDF itself is named there, Sec. 1 and 2.2).
@@ -7,7 +7,8 @@
 // velocity the first interpolation gathers) at points k-4 .. k+4 of the same circle,
 // each as (normal, tangent, 0) components in the frame of point k (normal = unit
 // offset from the centre, tangent = normal rotated by +90 degrees).  Output (3): the
-// force in that frame (the third component is unused in 2D).
+// force in that frame (the third component is unused in 2D).  Spheres: the point and
+// its 8 nearest neighbours on the sphere in the point's (normal, t1, t2) frame (below).
 //
 // Parameters (FP32, row-major), kMlpParams floats:
 //   W1 [27][64], b1 [64], W2 [64][64], b2 [64], W3 [64][3], b3 [3], in_scale, out_scale
@@ -17,6 +18,7 @@
 // Kernels: features (for the step and for training samples), tensor-core inference
 // (mma.sync m16n8k16, FP16 operands, FP32 accumulation, one warp per 16 points) and
 // FP32 training: forward, backward, weight gradients, Adam.
+#include <algorithm>
 #include <cstdint>
 #include <string>
 
@@ -56,6 +58,23 @@ __device__ __forceinline__ void features_2d(const float* Ub, const float* ubs, c
   }
 }
 
+// 3D (spheres): the deficit at point k and at its 8 stencil neighbours (frame3, nbr3:
+// the 8 nearest other points of the reference sphere ordered by azimuth about the
+// normal), each as (normal, t1, t2) components in the frame of point k.  Output (3):
+// the force in that frame.
+__device__ __forceinline__ void features_3d(const IbmArgs& A, long long base, int k, float (&x)[kIn]) {
+  const float* F = A.frame3 + 9 * k;
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    const int kk = j == 0 ? k : A.nbr3[8 * k + j - 1];
+    const long long b = base + kk;
+    const float d0 = A.Ub[3 * b] - A.ubs[3 * b], d1 = A.Ub[3 * b + 1] - A.ubs[3 * b + 1],
+                d2 = A.Ub[3 * b + 2] - A.ubs[3 * b + 2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[3 * j + a] = d0 * F[3 * a] + d1 * F[3 * a + 1] + d2 * F[3 * a + 2];
+  }
+}
+
 // training samples of the last step: features and the step's total force F_b in the
 // frame of each point (thread per point)
 __global__ void mlp_samples_kernel(IbmArgs A, float* __restrict__ X, float* __restrict__ Y) {
@@ -63,15 +82,23 @@ __global__ void mlp_samples_kernel(IbmArgs A, float* __restrict__ X, float* __re
   if (b >= A.npts) return;
   const int k = (int)(b % A.nl);
   float x[kIn];
-  features_2d(A.Ub, A.ubs, A.ref_f, A.nl, b - k, k, x);
+  if (A.D == 3) {
+    features_3d(A, b - k, k, x);
+    const float* F = A.frame3 + 9 * k;
+    const float Fx = A.Fb[3 * b], Fy = A.Fb[3 * b + 1], Fz = A.Fb[3 * b + 2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Y[b * kOut + a] = Fx * F[3 * a] + Fy * F[3 * a + 1] + Fz * F[3 * a + 2];
+  } else {
+    features_2d(A.Ub, A.ubs, A.ref_f, A.nl, b - k, k, x);
+    float nx, ny;
+    point_frame(A.ref_f, k, nx, ny);
+    const float Fx = A.Fb[2 * b], Fy = A.Fb[2 * b + 1];
+    Y[b * kOut] = Fx * nx + Fy * ny;
+    Y[b * kOut + 1] = -Fx * ny + Fy * nx;
+    Y[b * kOut + 2] = 0.0f;
+  }
 #pragma unroll
   for (int c = 0; c < kIn; ++c) X[b * kIn + c] = x[c];
-  float nx, ny;
-  point_frame(A.ref_f, k, nx, ny);
-  const float Fx = A.Fb[2 * b], Fy = A.Fb[2 * b + 1];
-  Y[b * kOut] = Fx * nx + Fy * ny;
-  Y[b * kOut + 1] = -Fx * ny + Fy * nx;
-  Y[b * kOut + 2] = 0.0f;
 }
 
 // ------------------------------------------------------------------ inference
@@ -327,6 +354,59 @@ __global__ void __launch_bounds__(kInferWarps * 32) mlp_step_kernel(IbmArgs A, c
   }
 }
 
+// 3D: the same replacement of the first MDF force, point-parallel: a warp takes 16
+// points at a time (grid stride), gathers their stencils from global memory (the
+// deficits of a sphere's points stay in L1/L2 between the warp's rows), runs them
+// through the network and writes F_b = dF_b back in the global frame.
+__global__ void __launch_bounds__(kInferWarps * 32) mlp_step3_kernel(IbmArgs A, const float* __restrict__ P,
+                                                                    const WeightImage* __restrict__ img) {
+  __shared__ InferSmem S;
+  copy_image(S.W, img);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int gid = lane >> 2, tig = lane & 3;
+  const float ins = P[oInS], outs = P[oOutS];
+  __half* xs = S.x[w];
+  for (long long r0 = ((long long)blockIdx.x * kInferWarps + w) * 16; r0 < A.npts;
+       r0 += (long long)gridDim.x * kInferWarps * 16) {
+    if (lane < 16) {
+      const long long b = r0 + lane;
+      if (b < A.npts) {
+        const int k = (int)(b % A.nl);
+        float x[kIn];
+        features_3d(A, b - k, k, x);
+#pragma unroll
+        for (int c = 0; c < kK1; ++c) xs[lane * kXP + c] = __float2half_rn(c < kIn ? x[c] * ins : 0.0f);
+      } else {
+#pragma unroll
+        for (int c = 0; c < kK1; ++c) xs[lane * kXP + c] = __float2half_rn(0.0f);
+      }
+    }
+    __syncwarp();
+    float o[4];
+    mlp_rows(S, xs, lane, o);
+    // column 2 (t2 component) sits in the lane with tig = 1 of the same row group
+    const float c2a = __shfl_down_sync(0xffffffffu, o[0], 1), c2b = __shfl_down_sync(0xffffffffu, o[2], 1);
+    if (tig == 0) {
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const long long b = r0 + gid + 8 * half;
+        if (b >= A.npts) continue;
+        const int k = (int)(b % A.nl);
+        const float* F = A.frame3 + 9 * k;
+        const float fl[3] = {o[2 * half] * outs, o[2 * half + 1] * outs, (half ? c2b : c2a) * outs};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float v = fl[0] * F[c] + fl[1] * F[3 + c] + fl[2] * F[6 + c];
+          A.dFb[3 * b + c] = v;
+          A.Fb[3 * b + c] = v;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // ------------------------------------------------------------------ training (FP32)
 // forward, thread per sample: H1, H2 (after ReLU) and Y kept for the backward pass
 __global__ void __launch_bounds__(128) mlp_fwd_kernel(const float* __restrict__ P, const float* __restrict__ X,
@@ -460,6 +540,13 @@ cudaError_t launch_mlp_image(const float* P, void* img, cudaStream_t s) {
 }
 
 cudaError_t launch_mlp_step(const IbmArgs& A, const float* P, const void* img, cudaStream_t s) {
+  if (A.D == 3) {
+    if (A.npts == 0) return cudaSuccess;
+    const long long groups = (A.npts + 15) / 16;
+    const unsigned grid = (unsigned)std::min<long long>((groups + kInferWarps - 1) / kInferWarps, 152LL * 8);
+    mlp_step3_kernel<<<grid, kInferWarps * 32, 0, s>>>(A, P, static_cast<const WeightImage*>(img));
+    return cudaGetLastError();
+  }
   if (A.np == 0) return cudaSuccess;
   const unsigned grid = (unsigned)min((A.np + kInferWarps - 1) / kInferWarps, 152 * 4);
   mlp_step_kernel<<<grid, kInferWarps * 32, 0, s>>>(A, P, static_cast<const WeightImage*>(img));

@@ -107,3 +107,111 @@ def test_initializer_lowers_the_mdf_residual():
     print(f"training loss {losses[0]:.3e} -> {losses[-1]:.3e}; residual after 3 MDF iterations "
           f"plain {res[0]:.3e}, learned first force {res[1]:.3e} ({res[1] / res[0]:.2f}x)")
     assert res[1] < res[0]
+
+
+# ---------------------------------------------------------------- spheres (3D)
+def _workload3(seed, n=12, side=56, **kw):
+    kw = {"mdf_iters": 3, **kw}
+    return Workload(name="mlp3", dim=3, nx=side, ny=side, nz=side, tau=0.6, n_particles=n, n_lag=452,
+                    diameter=12.0, density_ratio=1.5, gravity=(0.0, -1e-4, 0.0), seed=seed, **kw)
+
+
+def _sphere_ref(w, X0, sim=None):
+    """The oracle's reference offsets of the spheres' points (its own Fibonacci lattice)."""
+    import oracle
+
+    ref = oracle.Sim(w.as_dict(), X0)
+    ref.step(1)  # the points of a step are placed from the centres at its start
+    lg = ref.get_lagrangian()
+    return lg["X_b"][: w.n_lag] - X0[0]
+
+
+def test_samples_3d_are_the_stencils_of_the_last_step():
+    """GPU stencil table (built by the library's host code) and features against the FP64
+    reference built from the oracle's own sphere points."""
+    require_gpu()
+    from paper_2002_08855_gb300.binding import Simulation
+
+    w = _workload3(31)
+    X0 = place_particles(w)
+    sim = Simulation(w, X0)
+    sim.step(3)
+    X, Y = sim.mdf_samples()
+    lg = sim.get_lagrangian()
+    ref = _sphere_ref(w, X0, sim)
+    Xr = mlp_ref.features_3d(lg["U_b"], lg["u_b_star"], ref)
+    assert rel_l2(X.cpu().numpy(), Xr) < 1e-5
+    Yr = mlp_ref.to_frame_3d(lg["F_b"], ref)
+    assert rel_l2(Y.cpu().numpy(), Yr) < 1e-5
+    sim.close()
+
+
+def test_step_3d_starts_from_the_network_prediction():
+    """With mdf_iters = 1 and the learned start, F_b of the step is the prediction of the
+    tensor-core network (FP16 operands) from the step's stencils."""
+    require_gpu()
+    from paper_2002_08855_gb300 import mlp
+    from paper_2002_08855_gb300.binding import Simulation
+
+    w = _workload3(32, mdf_iters=1, mlp_init=1, fixed_particles=1)
+    X0 = place_particles(w)
+    p = mlp.init_params(5)
+    p[-2], p[-1] = 200.0, 1e-3  # in_scale, out_scale of the deficits' size
+    sim = Simulation(w, X0)
+    sim.set_mlp(p)
+    sim.step(2)
+    lg = sim.get_lagrangian()
+    ref = _sphere_ref(w, X0, sim)
+    frames, _ = mlp_ref.sphere_stencil(ref)
+    Fl = mlp_ref.predict(p, mlp_ref.features_3d(lg["U_b"], lg["u_b_star"], ref))
+    k = np.arange(len(Fl)) % w.n_lag
+    F = np.einsum("pa,pac->pc", Fl, frames[k])
+    assert rel_l2(lg["F_b"], F) < 2e-2
+    sim.close()
+
+
+def test_residual_tracking_3d_matches_oracle():
+    require_gpu()
+    import oracle
+    from paper_2002_08855_gb300.binding import Simulation
+
+    w = _workload3(33, n=6, side=44)
+    X0 = place_particles(w)
+    sim = Simulation(w, X0)
+    ref = oracle.Sim(w.as_dict(), X0)
+    sim.set_residual_tracking(True)
+    sim.step(4)
+    ref.step(4)
+    rg, ro = sim.mdf_residual()[0], ref.get_mdf_residual()[0]
+    assert abs(rg - ro) < 1e-3 * ro
+    sim.close()
+
+
+def test_initializer_3d_lowers_the_mdf_residual():
+    """Trained on spheres of other seeds (converged forces, 10 iterations); on a held-out
+    box the learned start with M = 2 beats the plain M = 2."""
+    require_gpu()
+    from paper_2002_08855_gb300 import mlp
+    from paper_2002_08855_gb300.binding import Simulation
+
+    train = [_workload3(50 + s, n=20, side=64) for s in range(3)]
+    X, Y = mlp.collect_samples(train, [place_particles(w) for w in train], steps=30, every=3)
+    params, losses = mlp.train(X, Y, epochs=25, batch=4096, lr=2e-3, seed=3)
+    assert losses[-1] < 0.5 * losses[0]
+    w = _workload3(88, n=20, side=64, mdf_iters=2)  # held out
+    X0 = place_particles(w)
+    res = {}
+    for init in (0, 1):
+        sim = Simulation(w.with_(mlp_init=init), X0)
+        if init:
+            sim.set_mlp(params)
+        sim.set_residual_tracking(True)
+        r = []
+        for _ in range(20):
+            sim.step(1)
+            r.append(sim.mdf_residual()[0])
+        res[init] = float(np.mean(r[-10:]))
+        sim.close()
+    print(f"3D training loss {losses[0]:.3e} -> {losses[-1]:.3e}; residual after 2 MDF iterations "
+          f"plain {res[0]:.3e}, learned first force {res[1]:.3e} ({res[1] / res[0]:.2f}x)")
+    assert res[1] < res[0]
