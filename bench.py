@@ -236,10 +236,11 @@ def _deviation_from_fp32(storage, dev):
             "displacement": rel(out[storage][2], out[0][2]), "case": "128x256 cavity, 12 circles, 200 steps"}
 
 
-def _train_initializer(w, dev):
-    """The learned MDF initializer, trained on samples of the same configuration with
-    another seed: 10 MDF iterations (converged forces), samples at steps 40, 80, 120
-    (about 1e6 points), 20 epochs of Adam on the GPU kernels."""
+def _train_initializer(w, dev, steps=120, every=40):
+    """The learned MDF initializer, trained on samples of the configuration w with
+    another seed: 10 MDF iterations (converged forces), samples every `every` steps
+    (2D headline: steps 40, 80, 120, about 1e6 points), 20 epochs of Adam on the GPU
+    kernels."""
     import torch
 
     from paper_2002_08855_gb300 import binding, inputs, mlp
@@ -248,9 +249,9 @@ def _train_initializer(w, dev):
     wt = w.with_(seed=w.seed + 1000, mdf_iters=10)
     sim = binding.Simulation(wt, inputs.place_particles(wt), device=str(dev))
     Xs, Ys = [], []
-    for t in range(120):
+    for t in range(steps):
         sim.step(1)
-        if (t + 1) % 40 == 0:
+        if (t + 1) % every == 0:
             Xf, Yf = sim.mdf_samples()
             Xs.append(Xf)
             Ys.append(Yf)
@@ -378,8 +379,18 @@ def _cavity3d(args, dev, local):
     steps = max(3, min(args.steps, 20))
     out = {"workload": w.name, "lattice": "D3Q19 384x384x768", "particles": w.n_particles,
            "points_per_particle": w.n_lag, "steps": steps}
-    for st, name in ((0, "fp32"), (1, "fp16")):
-        sim = binding.Simulation(w.with_(pdf_storage=st), X, device=str(dev))
+    # learned initializer for spheres: trained on the 96 x 96 x 192 copy (same solid
+    # fraction, another seed), 10 MDF iterations for converged forces
+    wt = inputs.cavity_3d(4)
+    params, info = _train_initializer(wt, dev, steps=60, every=20)
+    out["learned_initializer"] = info
+    forms = ((0, "fp32", 3, None), (1, "fp16", 3, None), (0, "fp32_learned_m2", 2, params),
+             (1, "fp16_learned_m2", 2, params))
+    for st, name, M, p in forms:
+        sim = binding.Simulation(w.with_(pdf_storage=st, mdf_iters=M, mlp_init=int(p is not None)), X,
+                                 device=str(dev))
+        if p is not None:
+            sim.set_mlp(p)
         sim.step(3)
         sim.sync()
         with ClockSampler(local) as clk:
@@ -391,9 +402,16 @@ def _cavity3d(args, dev, local):
             sim.sync()
         ms = ev0.elapsed_time(ev1) / steps
         parts = sim.time_parts(3)
+        sim.set_residual_tracking(True)
+        res = []
+        for _ in range(3):
+            sim.step(1)
+            res.append(sim.mdf_residual()[0])
         sim.close()
-        out[name] = {"value": w.n_grid / (ms * 1e3), "unit": METRIC, "ms_per_step": ms,
+        out[name] = {"value": w.n_grid / (ms * 1e3), "unit": METRIC, "ms_per_step": ms, "mdf_iters": M,
+                     "mdf_residual_rms": float(np.mean(res)),
                      "parts_ms_per_step": {k: v / 3 for k, v in parts.items()}, "clocks": clk.summary()}
+    out["learned_m2_residual_vs_plain_m3"] = out["fp32_learned_m2"]["mdf_residual_rms"] / out["fp32"]["mdf_residual_rms"]
     return out
 
 
