@@ -144,6 +144,12 @@ __device__ __forceinline__ void interp2_body(const IbmArgs& A, int m, unsigned b
   const int ox = fix_anchor(A.Xcf[(long long)i * 2 + 0]) - A.rcell - 2;
   const int oy = fix_anchor(A.Xcf[(long long)i * 2 + 1]) - A.rcell - 2;
   if (MODE == 0) {
+    // Only the nodes within R + 2 sqrt(2) of the centre are needed: every support node
+    // of a point on the circle (at most 2 nodes from it along each axis) and the
+    // interior the momentum sums use.  The box corners beyond hold zero.
+    const float fx = fix_frac(A.Xcf[(long long)i * 2 + 0]), fy = fix_frac(A.Xcf[(long long)i * 2 + 1]);
+    const float Rn = A.radius_f + 2.8285f + 0.01f, Rn2 = Rn * Rn;
+    const int c0 = A.rcell + 2;  // box column / row of the anchor node
     // two box nodes per lane and round, both loaded before either is reduced
     for (int t0 = lane; t0 < S * S; t0 += 64) {
       float fa[2][9];
@@ -154,6 +160,8 @@ __device__ __forceinline__ void interp2_body(const IbmArgs& A, int m, unsigned b
         ok[k] = false;
         if (t >= S * S) continue;
         const int r = t / S, c = t - r * S;
+        const float dx = (float)(c - c0) - fx, dy = (float)(r - c0) - fy;
+        if (dx * dx + dy * dy > Rn2) continue;
         int gx, gy;
         ok[k] = box_node(A.g, ox, oy, r, c, gx, gy);
         if (!ok[k]) continue;
