@@ -234,6 +234,35 @@ struct PartState {
 // runs once for all members: block b of the launch belongs to member cav[b] and is
 // block b - first[cav[b]] of that member's own grid.  args holds the members'
 // argument structs (in device memory).
+// Programmatic dependent launch (sm_90 and later): a kernel launched with programmatic
+// stream serialization can be scheduled while its predecessor in the stream is still
+// running.  It calls pdl_enter() before its first global memory access: the wait
+// returns once the predecessor grid has completed and its writes are visible, then the
+// kernel lets its own successor be scheduled.  Under an ordinary launch both
+// instructions return at once, so the kernels call it unconditionally.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// host: launch with programmatic stream serialization (the kernel must call pdl_enter
+// before touching global memory)
+template <typename... Params, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<Args&&>(args)...);
+}
+
 struct Fuse {
   const void* args;   // [members]
   const int* cav;     // [blocks]

@@ -256,6 +256,7 @@ __device__ __forceinline__ void interp2_body(const IbmArgs& A, int m, unsigned b
 
 template <int SC, int PARITY, int MODE, int ST, bool FUSED>
 __global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A0, int m, Fuse FU) {
+  pdl_enter();
   IBMLBM_BIND(FUSED, IbmArgs, A, A0, FU, blk);
   if constexpr (FUSED) {  // members differ in box size: run the code compiled for this one
     switch (A.box) {
@@ -375,6 +376,7 @@ __device__ __forceinline__ void spread2_body(const IbmArgs& A, unsigned blk) {
 
 template <int SC, bool FUSED>
 __global__ void __launch_bounds__(kIbmWarps * 32) ibm_spread2_kernel(IbmArgs A0, Fuse FU) {
+  pdl_enter();
   IBMLBM_BIND(FUSED, IbmArgs, A, A0, FU, blk);
   if constexpr (FUSED) {  // members differ in box size: run the code compiled for this one
     switch (A.box) {
@@ -1029,6 +1031,7 @@ __device__ __forceinline__ void forces2_body(const IbmArgs& A, unsigned blk) {
 
 template <int SC, bool FUSED>
 __global__ void __launch_bounds__(256) ibm_forces2_kernel(IbmArgs A0, Fuse FU) {
+  pdl_enter();
   IBMLBM_BIND(FUSED, IbmArgs, A, A0, FU, blk);
   if constexpr (FUSED) {  // members differ in box size: run the code compiled for this one
     switch (A.box) {
@@ -1141,11 +1144,12 @@ cudaError_t launch_ibm_interp(const IbmArgs& A, int m, cudaStream_t s) {
     const unsigned grid = (unsigned)((A.np + W - 1) / W);
     const int mode = (m == 0 || m == 1) ? 0 : 1;  // m < 0: residual pass (box + f_IB/2)
     const size_t sm = sizeof(float) * W * (size_t)interp2_warp_floats(mode, A.box);
+    cudaError_t e = cudaSuccess;  // programmatic launches (the kernel waits on entry)
 #define IBMLBM_INTERP2_ST(SC, P)                                                             \
   do {                                                                                        \
-    if (A.store == STORE_F32) ibm_interp2_kernel<SC, P, 0, STORE_F32, false><<<grid, W * 32, sm, s>>>(A, m, Fuse{}); \
-    else if (A.store == STORE_F16) ibm_interp2_kernel<SC, P, 0, STORE_F16, false><<<grid, W * 32, sm, s>>>(A, m, Fuse{}); \
-    else ibm_interp2_kernel<SC, P, 0, STORE_BF16, false><<<grid, W * 32, sm, s>>>(A, m, Fuse{});      \
+    if (A.store == STORE_F32) e = launch_pdl(ibm_interp2_kernel<SC, P, 0, STORE_F32, false>, grid, W * 32, sm, s, A, m, Fuse{}); \
+    else if (A.store == STORE_F16) e = launch_pdl(ibm_interp2_kernel<SC, P, 0, STORE_F16, false>, grid, W * 32, sm, s, A, m, Fuse{}); \
+    else e = launch_pdl(ibm_interp2_kernel<SC, P, 0, STORE_BF16, false>, grid, W * 32, sm, s, A, m, Fuse{}); \
   } while (0)
 #define IBMLBM_INTERP2(SC)                                                                   \
   do {                                                                                        \
@@ -1153,7 +1157,7 @@ cudaError_t launch_ibm_interp(const IbmArgs& A, int m, cudaStream_t s) {
       if (A.parity == 0) IBMLBM_INTERP2_ST(SC, 0);                                            \
       else IBMLBM_INTERP2_ST(SC, 1);                                                          \
     } else {                                                                                  \
-      ibm_interp2_kernel<SC, 0, 1, STORE_F32, false><<<grid, W * 32, sm, s>>>(A, m, Fuse{});         \
+      e = launch_pdl(ibm_interp2_kernel<SC, 0, 1, STORE_F32, false>, grid, W * 32, sm, s, A, m, Fuse{}); \
     }                                                                                         \
   } while (0)
     if (A.box == 16) IBMLBM_INTERP2(16);
@@ -1161,6 +1165,7 @@ cudaError_t launch_ibm_interp(const IbmArgs& A, int m, cudaStream_t s) {
     else IBMLBM_INTERP2(0);
 #undef IBMLBM_INTERP2
 #undef IBMLBM_INTERP2_ST
+    if (e != cudaSuccess) return e;
   } else {
     return launch_ibm_interp3(A, m, s);
   }
@@ -1225,12 +1230,14 @@ cudaError_t launch_ibm_spread(const IbmArgs& A, cudaStream_t s) {
     const int W = ibm2_warps(A.box);
     const unsigned grid = (unsigned)((A.np + W - 1) / W);
     const size_t sm = sizeof(float) * W * (size_t)spread2_warp_floats(A.box);
+    cudaError_t e;  // programmatic launches (the kernel waits on entry)
     if (A.box == 16)
-      ibm_spread2_kernel<16, false><<<grid, W * 32, sm, s>>>(A, Fuse{});
+      e = launch_pdl(ibm_spread2_kernel<16, false>, grid, W * 32, sm, s, A, Fuse{});
     else if (A.box == 22)
-      ibm_spread2_kernel<22, false><<<grid, W * 32, sm, s>>>(A, Fuse{});
+      e = launch_pdl(ibm_spread2_kernel<22, false>, grid, W * 32, sm, s, A, Fuse{});
     else
-      ibm_spread2_kernel<0, false><<<grid, W * 32, sm, s>>>(A, Fuse{});
+      e = launch_pdl(ibm_spread2_kernel<0, false>, grid, W * 32, sm, s, A, Fuse{});
+    if (e != cudaSuccess) return e;
   } else {
     return launch_ibm_spread3(A, s);
   }
@@ -1241,12 +1248,14 @@ cudaError_t launch_ibm_forces(const IbmArgs& A, cudaStream_t s) {
   if (A.np == 0) return cudaSuccess;
   const unsigned grid = (unsigned)(((long long)A.np * 32 + 255) / 256);
   if (A.D == 2) {
+    cudaError_t e;  // programmatic launches (the kernel waits on entry)
     if (A.box == 16)
-      ibm_forces2_kernel<16, false><<<grid, 256, 0, s>>>(A, Fuse{});
+      e = launch_pdl(ibm_forces2_kernel<16, false>, grid, 256, 0, s, A, Fuse{});
     else if (A.box == 22)
-      ibm_forces2_kernel<22, false><<<grid, 256, 0, s>>>(A, Fuse{});
+      e = launch_pdl(ibm_forces2_kernel<22, false>, grid, 256, 0, s, A, Fuse{});
     else
-      ibm_forces2_kernel<0, false><<<grid, 256, 0, s>>>(A, Fuse{});
+      e = launch_pdl(ibm_forces2_kernel<0, false>, grid, 256, 0, s, A, Fuse{});
+    if (e != cudaSuccess) return e;
   } else {
     ibm_forces_kernel<3><<<grid, 256, 0, s>>>(A);
   }

@@ -583,6 +583,8 @@ static void launch_step_main(const LbmArgs& A, cudaStream_t s) {
   constexpr int K = step_k<ST>();
   const int spr = (A.g.nx + K * kLbmBlock - 1) / (K * kLbmBlock);
   const dim3 grid((unsigned)((long long)spr * A.g.rows));
+  // an ordinary launch: programmatic blocks of this large grid would sit resident ahead
+  // of the high-priority particle kernels (measured slower)
   lbm_step_kernel<L, PARITY, ST, K, false><<<grid, kLbmBlock, 0, s>>>(A, spr, Fuse{});
 }
 
