@@ -126,6 +126,17 @@ __device__ __forceinline__ FF ff_warp_sum(FF s) {
   }
   return s;
 }
+// the same sum over the lanes of each half-warp (every lane of the warp takes part)
+__device__ __forceinline__ FF ff_half_sum(FF s) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    const float h = __shfl_xor_sync(0xffffffffu, s.hi, o);
+    const float l = __shfl_xor_sync(0xffffffffu, s.lo, o);
+    ff_add(s, h);
+    s.lo += l;
+  }
+  return s;
+}
 __device__ __forceinline__ double ff_value(FF s) { return (double)s.hi + (double)s.lo; }
 
 // Row pitch (in cells) of a 2D particle box of side S: at least S, and 4 or 12 modulo

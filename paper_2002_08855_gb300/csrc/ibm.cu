@@ -858,10 +858,13 @@ cudaError_t launch_ibm_spread3(const IbmArgs& A, cudaStream_t s) {
 }
 
 // F_h, T_h of particle i from its points, and the write of the warp's sums (lane 0)
-template <int D>
-__device__ __forceinline__ void forces_finish(const IbmArgs& A, int i, int lane, FF (&P)[3], FF (&L)[3]) {
+// LP lanes per particle (32: a warp; 16: a half-warp, lane < 16 within the half);
+// valid = false: the lane takes part in the reductions only
+template <int D, int LP = 32>
+__device__ __forceinline__ void forces_finish(const IbmArgs& A, int i, int lane, FF (&P)[3], FF (&L)[3],
+                                              bool valid = true) {
   FF sF[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, sT[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-  for (int k = lane; k < A.nl; k += 32) {
+  for (int k = lane; valid && k < A.nl; k += LP) {
     const long long b = (long long)i * A.nl + k;
     float r[3] = {0.0f, 0.0f, 0.0f}, F[3] = {0.0f, 0.0f, 0.0f};
     for (int c = 0; c < D; ++c) {
@@ -877,14 +880,14 @@ __device__ __forceinline__ void forces_finish(const IbmArgs& A, int i, int lane,
   }
   // only the components that exist in this dimension (2D: x, y and the z rotation)
   for (int c = 0; c < D; ++c) {
-    P[c] = ff_warp_sum(P[c]);
-    sF[c] = ff_warp_sum(sF[c]);
+    P[c] = LP == 32 ? ff_warp_sum(P[c]) : ff_half_sum(P[c]);
+    sF[c] = LP == 32 ? ff_warp_sum(sF[c]) : ff_half_sum(sF[c]);
   }
   for (int c = (D == 2 ? 2 : 0); c < 3; ++c) {
-    L[c] = ff_warp_sum(L[c]);
-    sT[c] = ff_warp_sum(sT[c]);
+    L[c] = LP == 32 ? ff_warp_sum(L[c]) : ff_half_sum(L[c]);
+    sT[c] = LP == 32 ? ff_warp_sum(sT[c]) : ff_half_sum(sT[c]);
   }
-  if (lane == 0) {
+  if (valid && lane == 0) {
     const double dV = (double)A.dV;
     for (int c = 0; c < D; ++c) {
       A.Pint[(long long)i * D + c] = ff_value(P[c]);
@@ -964,31 +967,37 @@ __global__ void __launch_bounds__(256) ibm_forces_kernel(IbmArgs A) {
   forces_finish<D>(A, i, lane, P, L);
 }
 
-// 2D form of the same sums, with u* from the particle's box buffer.  Each lane takes
-// its candidate nodes kForceBatch at a time, so their loads are in flight together.
+// 2D form of the same sums, with u* from the particle's box buffer, LP lanes per
+// particle (a half-warp in a single run: 10^4 particles then fit one wave of the GPU;
+// a warp in the fused batch).  Each lane takes its candidate nodes NB at a time, so
+// their loads are in flight together.
 constexpr int kForceBatch = 6;
 
-template <int SC>
+template <int SC, int LP = 32>
 __device__ __forceinline__ void forces2_body(const IbmArgs& A, unsigned blk) {
-  const int i = (int)((blk * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (i >= A.np) return;
+  constexpr int NB = LP == 16 ? 9 : kForceBatch;
+  const unsigned gt = blk * blockDim.x + threadIdx.x;
+  if ((int)((gt & ~31u) / LP) >= A.np) return;  // the warp's first particle: whole warp
+  const int i = (int)(gt / LP);
+  const int lane = (int)(gt & (LP - 1));
+  const bool valid = i < A.np;  // (the second half-warp of the last warp may have none)
   const int S = SC ? SC : A.box, W = box_pitch(S), cells = S * W, ext = S - 4;  // ext = 2 rcell + 2
-  const long long vx = A.Xcf[(long long)i * 2], vy = A.Xcf[(long long)i * 2 + 1];
+  const int ic = valid ? i : 0;
+  const long long vx = A.Xcf[(long long)ic * 2], vy = A.Xcf[(long long)ic * 2 + 1];
   const int anx = fix_anchor(vx), any = fix_anchor(vy);
   const float frx = fix_frac(vx), fry = fix_frac(vy);
   const int lox = anx - A.rcell, loy = any - A.rcell;
   const float R2f = A.radius_f * A.radius_f;
   const float band = 1e-4f * R2f + 1e-5f;
-  const float2* ub = reinterpret_cast<const float2*>(A.ubox) + (size_t)i * cells;
+  const float2* ub = reinterpret_cast<const float2*>(A.ubox) + (size_t)ic * cells;
   const float2* fib2 = reinterpret_cast<const float2*>(A.fib);
   FF P[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, L[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-  for (int t0 = 0; t0 < ext * ext; t0 += 32 * kForceBatch) {
-    float rx[kForceBatch], ry[kForceBatch], u0[kForceBatch], u1[kForceBatch];
-    bool in[kForceBatch];
+  for (int t0 = 0; valid && t0 < ext * ext; t0 += LP * NB) {
+    float rx[NB], ry[NB], u0[NB], u1[NB];
+    bool in[NB];
 #pragma unroll
-    for (int q = 0; q < kForceBatch; ++q) {
-      const int t = t0 + lane + 32 * q;
+    for (int q = 0; q < NB; ++q) {
+      const int t = t0 + lane + LP * q;
       in[q] = false;
       rx[q] = ry[q] = u0[q] = u1[q] = 0.0f;
       if (t >= ext * ext) continue;
@@ -1019,14 +1028,14 @@ __device__ __forceinline__ void forces2_body(const IbmArgs& A, unsigned blk) {
       in[q] = true;
     }
 #pragma unroll
-    for (int q = 0; q < kForceBatch; ++q) {
+    for (int q = 0; q < NB; ++q) {
       if (!in[q]) continue;
       ff_add(P[0], u0[q]);
       ff_add(P[1], u1[q]);
       ff_add(L[2], rx[q] * u1[q] - ry[q] * u0[q]);
     }
   }
-  forces_finish<2>(A, i, lane, P, L);
+  forces_finish<2, LP>(A, i, lane, P, L, valid);
 }
 
 template <int SC, bool FUSED>
@@ -1043,7 +1052,7 @@ __global__ void __launch_bounds__(256) ibm_forces2_kernel(IbmArgs A0, Fuse FU) {
       default: forces2_body<0>(A, blk); return;
     }
   }
-  forces2_body<SC>(A, blk);
+  forces2_body<SC, 16>(A, blk);  // a single run: half-warp per particle
 }
 
 // One warp per particle: regenerate its Lagrangian points for the next step,
@@ -1246,7 +1255,7 @@ cudaError_t launch_ibm_spread(const IbmArgs& A, cudaStream_t s) {
 
 cudaError_t launch_ibm_forces(const IbmArgs& A, cudaStream_t s) {
   if (A.np == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)(((long long)A.np * 32 + 255) / 256);
+  const unsigned grid = (unsigned)(((long long)A.np * (A.D == 2 ? 16 : 32) + 255) / 256);
   if (A.D == 2) {
     cudaError_t e;  // programmatic launches (the kernel waits on entry)
     if (A.box == 16)
