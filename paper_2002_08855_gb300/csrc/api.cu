@@ -1213,10 +1213,47 @@ struct BatchPlan {
 };
 
 // the launch types of a batched step, in the order of their block maps
-enum { BK_LBM, BK_EDGE, BK_WARP, BK_LANE, BK_PCLEAR, BK_PINS, BK_PSEARCH, BK_PFORCE, BK_COUNT };
+// (BK_CW0 + c: the interpolation and spreading blocks of the members of box-size
+// class c, launched with that class's shared memory)
+constexpr int kMaxBoxClasses = 8;
+enum { BK_LBM, BK_EDGE, BK_WARP, BK_LANE, BK_PCLEAR, BK_PINS, BK_PSEARCH, BK_PFORCE, BK_CW0,
+       BK_COUNT = BK_CW0 + kMaxBoxClasses };
 
-unsigned member_blocks(int type, const Derived& d, const ibm_lbm_config& c) {
+// Box-size classes of a batch: the distinct particle-box sizes of the members with
+// particles, ascending (beyond kMaxBoxClasses the largest sizes share the last class).
+// cls[i]: the class of member i (-1 without particles); box[c]: the largest box of c.
+struct BoxClasses {
+  std::vector<int> cls, box;
+};
+
+BoxClasses box_classes(const ibm_lbm_config* cfgs, int32_t n) {
+  BoxClasses bc;
+  std::vector<int> sizes;
+  std::vector<int> mb(n, 0);
+  for (int32_t i = 0; i < n; ++i)
+    if (cfgs[i].n_particles > 0) {
+      mb[i] = derive(&cfgs[i]).box;
+      sizes.push_back(mb[i]);
+    }
+  std::sort(sizes.begin(), sizes.end());
+  sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+  for (size_t c = 0; c < sizes.size(); ++c) {
+    if (c < (size_t)kMaxBoxClasses) bc.box.push_back(sizes[c]);
+    else bc.box.back() = sizes[c];
+  }
+  bc.cls.assign(n, -1);
+  for (int32_t i = 0; i < n; ++i) {
+    if (cfgs[i].n_particles == 0) continue;
+    int c = 0;
+    while (c + 1 < (int)bc.box.size() && bc.box[c] < mb[i]) ++c;
+    bc.cls[i] = c;
+  }
+  return bc;
+}
+
+unsigned member_blocks(int type, const Derived& d, const ibm_lbm_config& c, int cls) {
   const int np = c.n_particles;
+  if (type >= BK_CW0) return (np > 0 && cls == type - BK_CW0) ? ibm_warp_blocks(np) : 0;
   switch (type) {
     case BK_LBM: return lbm_step_blocks(d.g, c.pdf_storage);
     case BK_EDGE: return lbm_edge_blocks(d.g, 2);
@@ -1253,9 +1290,10 @@ int check_batch(const ibm_lbm_config* cfgs, int32_t n) {
 
 size_t batch_table_bytes(const ibm_lbm_config* cfgs, int32_t n) {
   size_t blocks = 0;
+  const BoxClasses bc = box_classes(cfgs, n);
   for (int32_t i = 0; i < n; ++i) {
     const Derived d = derive(&cfgs[i]);
-    for (int t = 0; t < BK_COUNT; ++t) blocks += member_blocks(t, d, cfgs[i]);
+    for (int t = 0; t < BK_COUNT; ++t) blocks += member_blocks(t, d, cfgs[i], bc.cls[i]);
   }
   // args: Lbm x2, Ibm x2, Regen x2, Pair x4 per member; maps: first[] per type, cav[] per
   // block, and a tile prefix table [n + 1] per lbm_step tile shape (each table padded to 16 bytes)
@@ -1293,6 +1331,13 @@ struct ibm_lbm_batch {
   long long res_step;  // step whose residual the buffer holds (-1: none)
   int store, mdf;
   size_t smem;                   // 2D IBM shared memory for the largest box
+  // box-size classes: one interpolation / spreading launch per class, with the class's
+  // shared memory, on its own high-priority stream (forked and joined per phase)
+  int nclass;
+  size_t class_smem[kMaxBoxClasses];
+  cudaStream_t cstream[kMaxBoxClasses];
+  cudaEvent_t cev[kMaxBoxClasses];
+  cudaEvent_t phase;
   unsigned blocks[BK_COUNT];
   // device tables
   LbmArgs* lbm_args[2];
@@ -1324,15 +1369,36 @@ int enqueue_batch_step(ibm_lbm_batch* b, int parity, int have_prev, int* nk, cud
   int k = 0;
   const unsigned* B = b->blocks;
   const void* ia = b->ibm_args[parity];
-  if (B[BK_WARP]) {
-    if (b->mdf == 0) {
-      CUDA_TRY(launch_ibm_interp_fused(fuse(b, BK_WARP, ia), B[BK_WARP], b->smem, 0, parity, b->store, s));
+  // one interpolation or spreading phase: a single launch over all members, or one
+  // launch per box-size class on the class streams (forked from and joined into s)
+  auto phase = [&](bool spread, int m) -> int {
+    auto one = [&](int type, size_t smem, cudaStream_t st) -> cudaError_t {
+      return spread ? launch_ibm_spread_fused(fuse(b, type, ia), B[type], smem, st)
+                    : launch_ibm_interp_fused(fuse(b, type, ia), B[type], smem, m, parity, b->store, st);
+    };
+    if (b->nclass <= 1) {
+      CUDA_TRY(one(BK_WARP, b->smem, s));
+      ++k;
+      return IBMLBM_OK;
+    }
+    CUDA_TRY(cudaEventRecord(b->phase, s));
+    for (int c = 0; c < b->nclass; ++c) {
+      if (!B[BK_CW0 + c]) continue;
+      CUDA_TRY(cudaStreamWaitEvent(b->cstream[c], b->phase, 0));
+      CUDA_TRY(one(BK_CW0 + c, b->class_smem[c], b->cstream[c]));
+      CUDA_TRY(cudaEventRecord(b->cev[c], b->cstream[c]));
       ++k;
     }
+    for (int c = 0; c < b->nclass; ++c)
+      if (B[BK_CW0 + c]) CUDA_TRY(cudaStreamWaitEvent(s, b->cev[c], 0));
+    return IBMLBM_OK;
+  };
+  if (B[BK_WARP]) {
+    int rc;
+    if (b->mdf == 0 && (rc = phase(false, 0)) != IBMLBM_OK) return rc;
     for (int m = 1; m <= b->mdf; ++m) {
-      CUDA_TRY(launch_ibm_interp_fused(fuse(b, BK_WARP, ia), B[BK_WARP], b->smem, m, parity, b->store, s));
-      CUDA_TRY(launch_ibm_spread_fused(fuse(b, BK_WARP, ia), B[BK_WARP], b->smem, s));
-      k += 2;
+      if ((rc = phase(false, m)) != IBMLBM_OK) return rc;
+      if ((rc = phase(true, m)) != IBMLBM_OK) return rc;
     }
     CUDA_TRY(launch_ibm_forces_fused(fuse(b, BK_LANE, ia), B[BK_LANE], s));
     ++k;
@@ -1400,6 +1466,14 @@ void destroy_batch(ibm_lbm_batch* b) {
   }
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->join) cudaEventDestroy(b->join);
+  for (int c = 0; c < kMaxBoxClasses; ++c) {
+    if (b->cstream[c]) {
+      cudaStreamSynchronize(b->cstream[c]);
+      cudaStreamDestroy(b->cstream[c]);
+    }
+    if (b->cev[c]) cudaEventDestroy(b->cev[c]);
+  }
+  if (b->phase) cudaEventDestroy(b->phase);
   delete b;
 }
 
@@ -1472,6 +1546,18 @@ int ibm_lbm_batch_init(const ibm_lbm_config* cfgs, int32_t n, void* d_workspace,
   b->smem = maxbox ? ibm_box2_smem(maxbox) : 0;
   if (maxbox && b->smem > 227 * 1024) return bail(fail(IBMLBM_ERR_UNSUPPORTED, "particle too large"));
   if (maxbox) BATCH_TRY(prepare_ibm_spread(2, b->smem));
+  const BoxClasses bc = box_classes(cfgs, n);
+  b->nclass = (int)bc.box.size();
+  for (int c = 0; c < b->nclass; ++c) b->class_smem[c] = ibm_box2_smem(bc.box[c]);
+  if (b->nclass > 1) {
+    int lo_ = 0, hi_ = 0;
+    BATCH_TRY(cudaDeviceGetStreamPriorityRange(&lo_, &hi_));
+    for (int c = 0; c < b->nclass; ++c) {
+      BATCH_TRY(cudaStreamCreateWithPriority(&b->cstream[c], cudaStreamNonBlocking, hi_));
+      BATCH_TRY(cudaEventCreateWithFlags(&b->cev[c], cudaEventDisableTiming));
+    }
+    BATCH_TRY(cudaEventCreateWithFlags(&b->phase, cudaEventDisableTiming));
+  }
   // host copies of the tables, then one copy to the device
   std::vector<char> host(batch_table_bytes(cfgs, n), 0);
   size_t o = 0;
@@ -1504,7 +1590,7 @@ int ibm_lbm_batch_init(const ibm_lbm_config* cfgs, int32_t n, void* d_workspace,
     std::vector<int> first(n), cav;
     for (int32_t i = 0; i < n; ++i) {
       first[i] = (int)cav.size();
-      const unsigned c = member_blocks(t, b->m[i]->d, cfgs[i]);
+      const unsigned c = member_blocks(t, b->m[i]->d, cfgs[i], bc.cls[i]);
       cav.insert(cav.end(), c, i);
     }
     b->blocks[t] = (unsigned)cav.size();
