@@ -247,6 +247,20 @@ int ibm_lbm_pair_search_static(int32_t dim, const int32_t* n_nodes, const int32_
                                int32_t max_neighbors, int32_t* d_pairs, int64_t cap,
                                int64_t* h_count, void* stream);
 
+/* Checkpoint and resume.  A state holds what the next step reads: the PDFs (as
+ * stored, in the layout of the step counter's AA parity), the step counter, the
+ * particle centres, velocities and angular velocities, and the history the particle
+ * update carries (previous accelerations, hydrodynamic force and torque, interior
+ * momenta), and the learned initializer's parameters when set.  The Lagrangian points,
+ * node masks and fixed-point centres are regenerated on restore; f_IB is zero between
+ * steps.  Host buffers; both calls synchronise the stream.  set_state needs a run of
+ * the same lattice, particle count, points per particle, storage, boundaries and pair
+ * search (INVALID_ARG otherwise, or for a buffer that is not a state of this library
+ * version); tau, gravity and the other physical parameters may differ. */
+int ibm_lbm_state_size(ibm_lbm_handle* h, size_t* bytes);
+int ibm_lbm_get_state(ibm_lbm_handle* h, void* h_buf, size_t bytes);
+int ibm_lbm_set_state(ibm_lbm_handle* h, const void* h_buf, size_t bytes);
+
 /* ---------------------------------------------------------------------------
  * Learned MDF initializer (no counterpart in the paper, which runs the plain
  * iteration).  A perceptron 27 -> 64 -> 64 -> 3 (ReLU) maps the velocity-deficit

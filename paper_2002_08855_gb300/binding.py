@@ -122,6 +122,9 @@ SIGNATURES = {
     "ibm_lbm_mlp_grad": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp, _dp, _vp, C.c_size_t, _vp]),
     "ibm_lbm_mlp_adam": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, C.c_float, _vp]),
     "ibm_lbm_mlp_infer": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp]),
+    "ibm_lbm_state_size": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
+    "ibm_lbm_get_state": (C.c_int, [_vp, _vp, C.c_size_t]),
+    "ibm_lbm_set_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "ibm_lbm_batch_workspace_size": (C.c_int, [C.POINTER(Config), C.c_int32, C.POINTER(C.c_size_t)]),
     "ibm_lbm_batch_init": (C.c_int, [C.POINTER(Config), C.c_int32, _vp, C.c_size_t, _vp,
                                      C.POINTER(_dp), C.POINTER(_vp)]),
@@ -318,6 +321,21 @@ class Simulation:
         _check(lib().ibm_lbm_mdf_samples(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(Y.data_ptr())),
                "mdf_samples")
         return X, Y
+
+    def get_state(self) -> np.ndarray:
+        """Checkpoint of the run (host bytes)."""
+        n = C.c_size_t(0)
+        _check(lib().ibm_lbm_state_size(self.h, C.byref(n)), "state_size")
+        buf = np.zeros(n.value, dtype=np.uint8)
+        self._wait_torch()
+        _check(lib().ibm_lbm_get_state(self.h, C.c_void_p(buf.ctypes.data), n.value), "get_state")
+        return buf
+
+    def set_state(self, buf):
+        """Resume from a checkpoint of a run of the same configuration."""
+        b = np.ascontiguousarray(np.asarray(buf, dtype=np.uint8))
+        self._wait_torch()
+        _check(lib().ibm_lbm_set_state(self.h, C.c_void_p(b.ctypes.data), b.size), "set_state")
 
     def set_residual_tracking(self, on: bool = True):
         _check(lib().ibm_lbm_set_residual_tracking(self.h, int(bool(on))), "set_residual_tracking")

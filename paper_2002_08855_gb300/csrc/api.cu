@@ -875,6 +875,143 @@ int ibm_lbm_set_particles(ibm_lbm_handle* h, const double* X, const double* U,
   return IBMLBM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Checkpoint blob: header, the raw PDF buffer (its layout is the AA parity of the
+// stored step counter), the particle arrays the update carries from step to step, and
+// the learned initializer's parameters when they are set.
+struct StateHeader {
+  char magic[8];
+  uint32_t version, header_bytes;
+  int32_t dim, nx, ny, nz, periodic[3], n_particles, n_lag, pdf_storage, boundary, pair_search;
+  int64_t step;
+  int32_t have_prev, mlp_set;
+  uint64_t f_bytes, part_bytes, mlp_bytes;
+};
+constexpr char kStateMagic[8] = {'I', 'B', 'L', 'B', 'M', 'S', 'T', '1'};
+
+// the particle arrays of a checkpoint: (device pointer, doubles), in blob order
+std::vector<std::pair<double*, size_t>> state_arrays(const ibm_lbm_handle* h) {
+  const size_t np = (size_t)h->cfg.n_particles, D = (size_t)h->d.D;
+  if (np == 0) return {};
+  const Layout& l = h->l;
+  return {{h->X((int)(h->step & 1)), np * D}, {h->at<double>(l.U), np * D}, {h->at<double>(l.Om), np * 3},
+          {h->at<double>(l.Fh), np * D},      {h->at<double>(l.Th), np * 3}, {h->at<double>(l.acc), np * D},
+          {h->at<double>(l.alp), np * 3},     {h->at<double>(l.Pprev), np * D},
+          {h->at<double>(l.Lprev), np * 3}};
+}
+
+size_t state_f_bytes(const ibm_lbm_handle* h) {
+  return (h->cfg.pdf_storage == IBMLBM_PDF_FP32 ? 4 : 2) * ((size_t)h->d.Q * h->d.g.Np + 64);
+}
+
+StateHeader state_header(const ibm_lbm_handle* h) {
+  StateHeader H{};
+  std::memcpy(H.magic, kStateMagic, 8);
+  H.version = 1;
+  H.header_bytes = sizeof(StateHeader);
+  H.dim = h->cfg.dim;
+  H.nx = h->cfg.nx;
+  H.ny = h->cfg.ny;
+  H.nz = h->cfg.nz;
+  for (int k = 0; k < 3; ++k) H.periodic[k] = h->cfg.periodic[k];
+  H.n_particles = h->cfg.n_particles;
+  H.n_lag = h->cfg.n_lag;
+  H.pdf_storage = h->cfg.pdf_storage;
+  H.boundary = h->cfg.boundary;
+  H.pair_search = h->cfg.pair_search;
+  H.step = h->step;
+  H.have_prev = h->have_prev;
+  H.mlp_set = h->mlp_set ? 1 : 0;
+  H.f_bytes = state_f_bytes(h);
+  size_t pb = 0;
+  for (const auto& a : state_arrays(h)) pb += sizeof(double) * a.second;
+  H.part_bytes = pb;
+  H.mlp_bytes = h->mlp_set ? sizeof(float) * kMlpParams : 0;
+  return H;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ibm_lbm_state_size(ibm_lbm_handle* h, size_t* bytes) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!bytes) return fail(IBMLBM_ERR_INVALID_ARG, "bytes is NULL");
+  const StateHeader H = state_header(h);
+  *bytes = sizeof(StateHeader) + H.f_bytes + H.part_bytes + H.mlp_bytes;
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_get_state(ibm_lbm_handle* h, void* h_buf, size_t bytes) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  const StateHeader H = state_header(h);
+  const size_t need = sizeof(StateHeader) + H.f_bytes + H.part_bytes + H.mlp_bytes;
+  if (!h_buf || bytes < need) return fail(IBMLBM_ERR_INVALID_ARG, "state buffer missing or too small");
+  char* p = static_cast<char*>(h_buf);
+  std::memcpy(p, &H, sizeof(H));
+  p += sizeof(H);
+  CUDA_TRY(cudaMemcpyAsync(p, h->at<char>(h->l.f), H.f_bytes, cudaMemcpyDeviceToHost, h->s));
+  p += H.f_bytes;
+  for (const auto& a : state_arrays(h)) {
+    CUDA_TRY(cudaMemcpyAsync(p, a.first, sizeof(double) * a.second, cudaMemcpyDeviceToHost, h->s));
+    p += sizeof(double) * a.second;
+  }
+  if (H.mlp_bytes)
+    CUDA_TRY(cudaMemcpyAsync(p, h->at<float>(h->l.mlp), H.mlp_bytes, cudaMemcpyDeviceToHost, h->s));
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_set_state(ibm_lbm_handle* h, const void* h_buf, size_t bytes) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!h_buf || bytes < sizeof(StateHeader)) return fail(IBMLBM_ERR_INVALID_ARG, "state buffer missing or too small");
+  StateHeader H;
+  std::memcpy(&H, h_buf, sizeof(H));
+  StateHeader mine = state_header(h);
+  if (std::memcmp(H.magic, kStateMagic, 8) != 0 || H.version != 1 || H.header_bytes != sizeof(StateHeader))
+    return fail(IBMLBM_ERR_INVALID_ARG, "not a state of this library version");
+  if (H.dim != mine.dim || H.nx != mine.nx || H.ny != mine.ny || H.nz != mine.nz ||
+      H.periodic[0] != mine.periodic[0] || H.periodic[1] != mine.periodic[1] || H.periodic[2] != mine.periodic[2] ||
+      H.n_particles != mine.n_particles || H.n_lag != mine.n_lag || H.pdf_storage != mine.pdf_storage ||
+      H.boundary != mine.boundary || H.pair_search != mine.pair_search || H.f_bytes != mine.f_bytes ||
+      H.part_bytes != mine.part_bytes || H.step < 0 ||
+      (H.mlp_bytes != 0 && H.mlp_bytes != sizeof(float) * kMlpParams))
+    return fail(IBMLBM_ERR_INVALID_ARG, "state of another configuration");
+  if (bytes < sizeof(StateHeader) + H.f_bytes + H.part_bytes + H.mlp_bytes)
+    return fail(IBMLBM_ERR_INVALID_ARG, "state buffer too small");
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  h->step = H.step;  // fixes the parity of the PDF layout and of the point buffers
+  h->have_prev = H.have_prev;
+  h->res_step = -1;
+  const char* p = static_cast<const char*>(h_buf) + sizeof(StateHeader);
+  CUDA_TRY(cudaMemcpyAsync(h->at<char>(h->l.f), p, H.f_bytes, cudaMemcpyHostToDevice, h->s));
+  p += H.f_bytes;
+  for (const auto& a : state_arrays(h)) {
+    CUDA_TRY(cudaMemcpyAsync(a.first, p, sizeof(double) * a.second, cudaMemcpyHostToDevice, h->s));
+    p += sizeof(double) * a.second;
+  }
+  if (H.mlp_bytes) {
+    CUDA_TRY(cudaMemcpyAsync(h->at<float>(h->l.mlp), p, H.mlp_bytes, cudaMemcpyHostToDevice, h->s));
+    CUDA_TRY(launch_mlp_image(h->at<float>(h->l.mlp), h->at<void>(h->l.mlp_img), h->s));
+    h->mlp_set = true;
+  }
+  // between steps f_IB is zero; the points, fixed-point centres and masks follow from
+  // the restored centres and velocities
+  const size_t fib_bytes = sizeof(float) * (h->d.D == 3 ? 4 : 2) * (size_t)h->d.g.N;
+  if (h->cfg.n_particles > 0 || h->d.D == 3)
+    CUDA_TRY(cudaMemsetAsync(h->at<float>(h->l.fib), 0, fib_bytes, h->s));
+  rc = regenerate_points(h);
+  if (rc) return rc;
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  return IBMLBM_OK;
+}
+
 int ibm_lbm_get_particles(ibm_lbm_handle* h, double* X, double* U, double* Omega,
                           double* F_h, double* T_h, double* F_c) {
   int rc = check_handle(h);
