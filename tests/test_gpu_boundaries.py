@@ -82,3 +82,15 @@ def test_smallest_domain_and_mixed_axes():
     w = Workload(name="tiny", dim=3, nx=5, ny=3, nz=3, periodic=(1, 0, 0), tau=0.75,
                  body_force=(2e-5, 0.0, 0.0), boundary=2, u_inlet=0.01)
     _compare(w, np.zeros((0, 3)), 41)
+
+
+def test_closed_cavity_3d_settling_with_extrapolation_walls():
+    """The 3D form of Sec. 6.2's setting: spheres (d = 10, density ratio 1.01, 3-point
+    delta, drs = 1.9) settling in a closed cube whose walls are extrapolation
+    boundaries, with the grid search of Table 5 for the contacts."""
+    require_gpu()
+    w = Workload(name="settle3", dim=3, nx=40, ny=40, nz=48, tau=0.6, n_particles=6, n_lag=314,
+                 diameter=10.0, delta_kind=3, drs=1.9, density_ratio=1.01,
+                 gravity=(0.0, 0.0, -1e-3), boundary=1, pair_search=1, seed=23)
+    X = inputs.place_particles(w)
+    _compare(w, X, 41)
