@@ -142,6 +142,18 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def whole_job(ms_local, n_grid, steps, world, dist=None, device="cpu"):
+    """Replicas only: every rank steps its own copy of the workload.  The job's time is
+    the slowest rank's (max over ranks); its MLUPS count every rank's node updates."""
+    import torch
+
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * n_grid * steps / (1e3 * ms_max)
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -589,11 +601,7 @@ def run(args):
     ms = ev0.elapsed_time(ev1)
     launches = sim.launch_count() - launches0
     clocks = clk.summary()
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    mlups = world * w.n_grid * args.steps / (1e3 * ms_max)
+    ms_max, mlups = whole_job(ms, w.n_grid, args.steps, world, dist, dev)
 
     # per-part device times (eager launches, CUDA events on the same stream)
     parts = sim.time_parts(max(3, min(args.steps, 50)))
