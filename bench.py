@@ -45,6 +45,9 @@ def _workload():
     return inputs.cavity_2d_large(PHI)
 
 
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, the vendor figure (context beside the measured peak)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -224,6 +227,13 @@ STATED_ERROR = {
     "fp32": {"velocity": 4.4e-6, "displacement": 2.7e-6},
     "fp16": {"velocity": 3.0e-4, "pressure": 5.0e-4, "displacement": 2.0e-5},
     "bf16": {"velocity": 2.4e-3, "pressure": 3.9e-3, "displacement": 1.8e-4},
+}
+# 3D cavity copy (48 x 48 x 96, 30 spheres of d = 12), relative L2 against the FP64
+# oracle after 60 steps (tests/test_gpu_precision.py)
+STATED_ERROR_3D = {
+    "fp32": {"velocity": 1.2e-6, "pressure": 4.8e-6, "displacement": 5.0e-7, "F_h": 3.1e-6},
+    "fp16": {"velocity": 1.9e-4, "pressure": 2.3e-4, "displacement": 5.9e-6, "F_h": 2.6e-4},
+    "bf16": {"velocity": 1.3e-3, "pressure": 1.5e-3, "displacement": 5.4e-5, "F_h": 2.2e-3},
 }
 
 
@@ -424,6 +434,7 @@ def _cavity3d(args, dev, local):
                      "mdf_residual_rms": float(np.mean(res)),
                      "parts_ms_per_step": {k: v / 3 for k, v in parts.items()}, "clocks": clk.summary()}
     out["learned_m2_residual_vs_plain_m3"] = out["fp32_learned_m2"]["mdf_residual_rms"] / out["fp32"]["mdf_residual_rms"]
+    out["stated_error_vs_oracle"] = STATED_ERROR_3D
     return out
 
 
@@ -513,6 +524,38 @@ def _pair_search_modes(dev, w2, X2):
             n_pairs = len(sim.get_pairs())
             sim.close()
             out[name][mname] = {"pairs_ms_per_step": parts["pairs"] / reps, "pairs": n_pairs}
+    return out
+
+
+def _cavity2d_series(args, dev, local):
+    """The other configurations of the 2048 x 4096 cavity (solid fraction 0, 0.2, 0.4:
+    0, 21361, 42723 circles; FP32 and FP16 storage) and the 128 x 256 cavity (12
+    circles of d = 16, a latency case that fits in L2): ms and MLUPS per step over
+    min(steps, 100) graph-replayed steps."""
+    import torch
+
+    from paper_2002_08855_gb300 import binding, inputs
+
+    steps = max(3, min(args.steps, 100))
+    out = {"steps": steps}
+    cases = [(f"2048x4096_phi{phi}", inputs.cavity_2d_large(phi)) for phi in (0.0, 0.2, 0.4)]
+    cases.append(("128x256_12_circles", inputs.cavity_2d_small()))
+    for name, w in cases:
+        X = inputs.place_particles(w)
+        out[name] = {"particles": w.n_particles}
+        for st, sname in ((0, "fp32"), (1, "fp16")):
+            sim = binding.Simulation(w.with_(pdf_storage=st), X, device=str(dev))
+            sim.step(3)
+            sim.sync()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(sim.stream)
+            sim.step(steps)
+            ev1.record(sim.stream)
+            ev1.synchronize()
+            sim.sync()
+            sim.close()
+            ms = ev0.elapsed_time(ev1) / steps
+            out[name][sname] = {"value": w.n_grid / (ms * 1e3), "unit": METRIC, "ms_per_step": ms}
     return out
 
 
@@ -620,6 +663,7 @@ def run(args):
     cavity3d = _cavity3d(args, dev, local)
     poiseuille = _poiseuille(args, dev, local)
     pair_modes = _pair_search_modes(dev, w, X)
+    series2d = _cavity2d_series(args, dev, local)
 
     # end to end through the C ABI with host buffers: init from host centres, then per
     # step one ibm_lbm_step and a read of the particle state into pinned host memory
@@ -657,7 +701,8 @@ def run(args):
             "roofline": {"bound": "hbm", "kernel": "lbm_step", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "algorithmic_bytes": bytes_lbm,
-                         "forced_nodes": nforced, "ms_per_launch": t_lbm * 1e3},
+                         "forced_nodes": nforced, "ms_per_launch": t_lbm * 1e3,
+                         "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS},
             "parts_ms_per_step": {k: v / nparts for k, v in parts.items()},
             "clocks": clocks, "gpu_launches": launches,
             "e2e": {"value": e2e, "unit": METRIC, "h2d_bytes_per_step": int(X.nbytes / e2e_steps),
@@ -669,6 +714,7 @@ def run(args):
             "cavity3d": cavity3d,
             "poiseuille_sec61": poiseuille,
             "pair_search": pair_modes,
+            "cavity2d_series": series2d,
         }
         print(json.dumps(line))
     if dist is not None:

@@ -88,3 +88,41 @@ def test_cavity_error_against_oracle(storage):
     b = BOUNDS[storage]
     assert e_u < b["u"] and e_p < b["p"] and e_x < b["x"]
     sim.close()
+
+
+# 3D (the 384 x 384 x 768 cavity scaled to 48 x 48 x 96 with 30 spheres of d = 12,
+# solid fraction 0.12: random placement with the contact gap stalls before the full
+# cavity's 0.16 in this small box), relative L2 against the FP64 oracle after 60 steps
+# measured on a GB300: FP32 velocity 1.2e-6, pressure 4.8e-6, displacement 5.0e-7, F_h
+# 3.1e-6; FP16 1.9e-4, 2.3e-4, 5.9e-6, 2.6e-4; BF16 1.3e-3, 1.5e-3, 5.4e-5, 2.2e-3
+BOUNDS3 = {0: {"u": 1e-5, "p": 1e-5, "x": 1e-5, "f": 1e-5},
+           1: {"u": 4e-4, "p": 5e-4, "x": 2e-5, "f": 6e-4},
+           2: {"u": 3e-3, "p": 4e-3, "x": 2e-4, "f": 5e-3}}
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2])
+def test_cavity_3d_error_per_field(storage):
+    """Velocity, pressure, particle displacement and hydrodynamic force of the 3D
+    cavity per PDF storage against the FP64 oracle."""
+    require_gpu()
+    from paper_2002_08855_gb300.binding import Simulation
+
+    w = inputs.cavity_3d(8).with_(n_particles=30, pdf_storage=storage)
+    X0 = inputs.place_particles(w)
+    sim = Simulation(w, X0)
+    ref = oracle.Sim(w.as_dict(), X0)
+    sim.step(60)
+    sim.sync()
+    ref.step(60)
+    pg_, ug = sim.get_fields()
+    po_, uo = ref.get_fields()
+    e_u = rel_l2(ug.cpu().numpy(), uo)
+    e_p = rel_l2(pg_.cpu().numpy(), po_)
+    pg, po = sim.get_particles(), ref.get_particles()
+    e_x = rel_l2(pg["X"] - X0, po["X"] - X0)
+    e_f = rel_l2(pg["F_h"], po["F_h"])
+    print(f"3D storage {storage}: velocity {e_u:.3e}, pressure {e_p:.3e}, displacement {e_x:.3e}, "
+          f"F_h {e_f:.3e}")
+    b = BOUNDS3[storage]
+    assert e_u < b["u"] and e_p < b["p"] and e_x < b["x"] and e_f < b["f"]
+    sim.close()
