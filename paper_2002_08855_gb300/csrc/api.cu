@@ -66,13 +66,14 @@ struct Derived {
   int box, rcell;
   double radius, dV, Mp, meff, Ip, Kt, Kr, c_ij, thr2;
   float mark_radius;
+  int slen;  // 3D: entries of the staging list (0: none)
 };
 
 struct Layout {
   size_t f, ustar, fib, mask;
   size_t X0, X1, U, Om, Fh, Th, FhN, ThN, acc, alp, Pint, Lint, Pprev, Lprev, Fc;
   size_t Uf, Omf, ref_fix, ref_f, Xcf, Xb0, Xb1, Ub0, Ub1, Fb, dFb, ubs, ubox, res, mlp, mlp_img;
-  size_t frame3, nbr3;
+  size_t frame3, nbr3, slist;
   size_t cell_count, cell_ids, nbr, nbr_count, gt, pairs, status;
   size_t grid, over, over_count;
   size_t total;
@@ -147,6 +148,36 @@ void cell_grid(int D, const double* L, const int* per, double reach, int* nc, do
   }
 }
 
+// Staging list of a 3D sphere's node box: the cells (lx | ly << 5 | lz << 10) that are
+// a support node of some point of the sphere for some position of its centre within
+// its anchor cell.  Cell l lies k = l - (rcell + 2) nodes from the anchor; with the
+// centre at anchor + fr, fr in [0, 1)^3, the node is a support node of the surface
+// point c + y (|y| = R) iff y lies in the cube of half-width h around k - fr (h = 2
+// for the 4-point delta, 1.5 for the nonzero weights of the 3-point one), so over all
+// fr the cube [k - 1 - h, k + h]^3 must meet the sphere.  The margin of 0.02 is wider
+// than the one of the test each block makes with its own fr.  Empty where the box
+// side passes 32 or the offsets of a box could pass 2^31.
+std::vector<int> stage3_list(const Derived& d, int delta_kind) {
+  std::vector<int> out;
+  const int S = d.box;
+  if (d.D != 3 || S > 32 || (double)d.g.nx * d.g.ny * S >= 2147483647.0) return out;
+  const double h = delta_kind == 3 ? 1.5 : 2.0, Rlo = std::max(0.0, d.radius - 0.02), Rhi = d.radius + 0.02;
+  for (int lz = 0; lz < S; ++lz)
+    for (int ly = 0; ly < S; ++ly)
+      for (int lx = 0; lx < S; ++lx) {
+        const int l[3] = {lx, ly, lz};
+        double dmin2 = 0.0, dmax2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          const double k = l[a] - (d.rcell + 2), lo = k - 1.0 - h, hi = k + h;
+          const double e = lo > 0.0 ? lo : (hi < 0.0 ? -hi : 0.0), g = std::max(std::fabs(lo), std::fabs(hi));
+          dmin2 += e * e;
+          dmax2 += g * g;
+        }
+        if (dmin2 <= Rhi * Rhi && dmax2 >= Rlo * Rlo) out.push_back(lx | ly << 5 | lz << 10);
+      }
+  return out;
+}
+
 Derived derive(const ibm_lbm_config* c) {
   Derived d{};
   d.D = c->dim;
@@ -204,6 +235,7 @@ Derived derive(const ibm_lbm_config* c) {
   d.c_ij = std::fabs((c->density_ratio - 1.0) * V) * std::sqrt(g2);
   const double thr = Dp + c->zeta;
   d.thr2 = thr * thr;
+  d.slen = c->n_particles > 0 ? (int)stage3_list(d, c->delta_kind).size() : 0;
   return d;
 }
 
@@ -250,6 +282,7 @@ Layout carve(const ibm_lbm_config* c, const Derived& d) {
   // 3D stencil of the learned initializer: frames [nl][9] and neighbours [nl][8]
   l.frame3 = cv.take(D == 3 ? sizeof(float) * 9 * (size_t)c->n_lag : 0);
   l.nbr3 = cv.take(D == 3 ? sizeof(int) * 8 * (size_t)c->n_lag : 0);
+  l.slist = cv.take(sizeof(int) * (size_t)d.slen);  // 3D staging list of the node box
   // 2D: u* of each particle's node box (box rows of box_pitch(box) float2 cells)
   l.ubox = cv.take(D == 2 ? sizeof(float) * np * 2 * (size_t)d.box * box_pitch(d.box) : 0);
   const size_t ncells = (size_t)d.nc[0] * d.nc[1] * d.nc[2];
@@ -417,6 +450,11 @@ struct ibm_lbm_handle {
     a.res = at<float>(l.res);
     a.frame3 = at<float>(l.frame3);
     a.nbr3 = at<int>(l.nbr3);
+    a.slist = d.slen ? at<int>(l.slist) : nullptr;
+    a.slen = d.slen;
+    a.shell_h = cfg.delta_kind == 3 ? 1.5f : 2.0f;
+    a.shell_lo2 = (float)(std::max(0.0, d.radius - 0.01) * std::max(0.0, d.radius - 0.01));
+    a.shell_hi2 = (float)((d.radius + 0.01) * (d.radius + 0.01));
     a.Xc = X(parity);
     a.Xcf = at<long long>(l.Xcf);
     a.ref_f = at<float>(l.ref_f);
@@ -751,6 +789,10 @@ int ibm_lbm_init(const ibm_lbm_config* cfg, void* d_workspace, size_t bytes, voi
       INIT_TRY(cudaMemcpyAsync(h->at<int>(l.nbr3), nbrs.data(), sizeof(int) * nbrs.size(),
                                cudaMemcpyHostToDevice, h->s));
     }
+    const std::vector<int> slist = stage3_list(d, cfg->delta_kind);
+    if (!slist.empty())
+      INIT_TRY(cudaMemcpyAsync(h->at<int>(l.slist), slist.data(), sizeof(int) * slist.size(),
+                               cudaMemcpyHostToDevice, h->s));
     INIT_TRY(cudaStreamSynchronize(h->s));  // host vectors go out of scope
     if (spread_smem(d.D, cfg->n_lag, d.box) <= 227 * 1024)
       INIT_TRY(prepare_ibm_spread(d.D, spread_smem(d.D, cfg->n_lag, d.box)));

@@ -195,6 +195,10 @@ struct IbmArgs {
   float* res;        // [npts][D] U_b - D_I u^(M) (residual pass)
   const float* frame3;  // 3D learned initializer: [nl][3][3] rows n, t1, t2 of each point
   const int* nbr3;      // 3D learned initializer: [nl][8] stencil neighbours of each point
+  const int* slist;     // 3D: [slen] cells (lx | ly << 5 | lz << 10) of the node box that
+  int slen;             //   can be a support node (null, 0: stage by rows)
+  float shell_h;        // 3D: support half-width (2 for the 4-point delta, 1.5 for the 3-point)
+  float shell_lo2, shell_hi2;  // 3D: squared radii bounding the points' distance from the centre
   uint32_t* status;
 };
 

@@ -470,6 +470,67 @@ __device__ __forceinline__ void mdf3_table(const IbmArgs& A, int i, const int (&
   }
 }
 
+// Whether sphere i's node box lies inside the domain on every axis (its staging list
+// then applies, with plain offsets from the box origin).
+__device__ __forceinline__ bool box3_inside(const IbmArgs& A, const int (&org)[3], int S) {
+  return A.slen > 0 && org[0] >= 0 && org[1] >= 0 && org[2] >= 0 && org[0] + S <= A.g.nx &&
+         org[1] + S <= A.g.ny && org[2] + S <= A.g.nz;
+}
+
+// Linear offset of box cell (lx, ly, lz) from the box origin (below 2^31: the host
+// builds no list otherwise)
+__device__ __forceinline__ int box3_goff(const Geo& g, int lx, int ly, int lz) {
+  return lx + g.nx * (ly + g.ny * lz);
+}
+
+// Staging of u^(m-1) from the staging list (box inside the domain): thread t takes
+// entries t, t + kMdf3Threads, ..., kListU at a time with all their loads in flight.
+// An entry is staged when the cube of half-width shell_h around the node (its offset
+// from the centre is a = l - cen) meets the shell between the points' radii: every
+// support node of every point passes, and the rest of the box is never read.
+constexpr int kListU = 4;
+
+template <int MODE>
+__device__ __forceinline__ void stage3_from_list(const IbmArgs& A, float* box, int cells, int Py, int Pz,
+                                                 long long n0, const float (&cen)[3]) {
+  const float4* us4 = reinterpret_cast<const float4*>(A.ustar);
+  const float4* fib4 = reinterpret_cast<const float4*>(A.fib);
+  const float h = A.shell_h;
+  for (int j0 = threadIdx.x; j0 < A.slen; j0 += kMdf3Threads * kListU) {
+    float4 v[kListU];
+    int cell[kListU];
+#pragma unroll
+    for (int u = 0; u < kListU; ++u) {
+      const int j = j0 + u * kMdf3Threads;
+      cell[u] = -1;
+      v[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (j >= A.slen) continue;
+      const int e = A.slist[j];
+      const int lx = e & 31, ly = (e >> 5) & 31, lz = (e >> 10) & 31;
+      const float ax = fabsf((float)lx - cen[0]), ay = fabsf((float)ly - cen[1]), az = fabsf((float)lz - cen[2]);
+      const float ex = fmaxf(ax - h, 0.0f), ey = fmaxf(ay - h, 0.0f), ez = fmaxf(az - h, 0.0f);
+      const float gx = ax + h, gy = ay + h, gz = az + h;
+      if (ex * ex + ey * ey + ez * ez > A.shell_hi2 || gx * gx + gy * gy + gz * gz < A.shell_lo2) continue;
+      cell[u] = lx + Py * ly + Pz * lz;
+      const long long n = n0 + box3_goff(A.g, lx, ly, lz);
+      v[u] = us4[n];
+      if (MODE == 1) {
+        const float4 f = fib4[n];
+        v[u].x += 0.5f * f.x;
+        v[u].y += 0.5f * f.y;
+        v[u].z += 0.5f * f.z;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kListU; ++u)
+      if (cell[u] >= 0) {
+        box[cell[u]] = v[u].x;
+        box[cells + cell[u]] = v[u].y;
+        box[2 * cells + cell[u]] = v[u].z;
+      }
+  }
+}
+
 // Interpolation of MDF iteration m, one block per sphere (Eq. 47, 10):
 //   1. stage u^(m-1) = u* + f_IB/2 (m = 1: u*) of the nodes of the sphere's box that
 //      lie in the marked ball (every support node does) into shared memory, one box
@@ -480,7 +541,7 @@ __device__ __forceinline__ void mdf3_table(const IbmArgs& A, int i, const int (&
 // with the increments of iterations 1 .. m-1 of all spheres and none of iteration m
 // (the iteration of the FP64 oracle).
 template <int SC, int MODE>
-__global__ void __launch_bounds__(kMdf3Threads) ibm_interp3_kernel(IbmArgs A, int m) {
+__global__ void __launch_bounds__(kMdf3Threads, 2) ibm_interp3_kernel(IbmArgs A, int m) {
   extern __shared__ __align__(16) float sm3[];
   const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int S = SC ? SC : A.box, Py = box3_pitch(S), Pz = Py * S, cells = Pz * S;
@@ -493,6 +554,7 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_interp3_kernel(IbmArgs A, in
   float fr[3];
   mdf3_origin(A, i, an, fr, org);
   const float Rm2 = A.mark_radius * A.mark_radius;
+  const bool inside = box3_inside(A, org, S);
   // this lane's column of every box row: grid x, and whether it is inside the domain
   // (S <= 22 here: a larger box does not fit in shared memory and takes the global path)
   int gx = org[0] + lane;
@@ -502,14 +564,21 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_interp3_kernel(IbmArgs A, in
   }
   const float dx = (float)(org[0] + lane - an[0]) - fr[0];
 
-  // 1. stage the ball of the box, kRows3 rows per warp and round.  The 3-point delta's
-  //    fourth (zero-weight) node can lie outside the ball: the box starts from zero then.
+  // 1. stage the box: from the staging list where the box lies inside the domain, else
+  //    the marked ball of the box, kRows3 rows per warp and round.  The 3-point delta's
+  //    fourth (zero-weight) node is staged by neither: the box starts from zero then.
   if (A.delta_kind == 3) {
     const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     for (int q = tid; q < 3 * cells / 4; q += kMdf3Threads) reinterpret_cast<float4*>(box)[q] = z4;
     __syncthreads();
   }
-  const int rows = S * S;
+  if (inside) {
+    const float cen[3] = {(float)(an[0] - org[0]) + fr[0], (float)(an[1] - org[1]) + fr[1],
+                          (float)(an[2] - org[2]) + fr[2]};
+    const long long n0 = (long long)org[0] + (long long)nn[0] * ((long long)org[1] + (long long)nn[1] * org[2]);
+    stage3_from_list<MODE>(A, box, cells, Py, Pz, n0, cen);
+  }
+  const int rows = inside ? 0 : S * S;  // otherwise by box rows
   for (int r0 = warp; r0 < rows; r0 += kMdf3Warps * kRows3) {
     float4 v[kRows3];
     int cell[kRows3];
@@ -591,16 +660,23 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_interp3_kernel(IbmArgs A, in
   for (int k = tid; k < A.nl; k += kMdf3Threads) {
     const long long b = (long long)i * A.nl + k;
     const float* row = tab + (size_t)k * kTab3;
+    float U[3], F[3] = {0.0f, 0.0f, 0.0f};  // all loads ahead of the stores
+#pragma unroll
+    for (int c = 0; c < 3; ++c) U[c] = A.Ub[b * 3 + c];
+    if (m > 1) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) F[c] = A.Fb[b * 3 + c];
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float u = row[13 + c];
       if (m < 0) {
-        A.res[b * 3 + c] = A.Ub[b * 3 + c] - u;
+        A.res[b * 3 + c] = U[c] - u;
         continue;
       }
-      const float d = 2.0f * (A.Ub[b * 3 + c] - u);
+      const float d = 2.0f * (U[c] - u);
       A.dFb[b * 3 + c] = d;
-      A.Fb[b * 3 + c] = (m == 1) ? d : A.Fb[b * 3 + c] + d;
+      A.Fb[b * 3 + c] = (m == 1) ? d : F[c] + d;
       if (m == 1) A.ubs[b * 3 + c] = u;
     }
   }
@@ -680,7 +756,21 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_spread3_kernel(IbmArgs A) {
   }
   __syncthreads();
 
-  // 3. flush the non-zero cells to f_IB, one box row per warp and round
+  // 3. flush the non-zero cells to f_IB: the staging list's cells where the box lies
+  //    inside the domain (every support node is one), else one box row per warp and round
+  if (box3_inside(A, org, S)) {
+    const long long n0 = (long long)org[0] + (long long)nn[0] * ((long long)org[1] + (long long)nn[1] * org[2]);
+    for (int j = tid; j < A.slen; j += kMdf3Threads) {
+      const int e = A.slist[j];
+      const int lx = e & 31, ly = (e >> 5) & 31, lz = (e >> 10) & 31;
+      const int c = lx + Py * ly + Pz * lz;
+      const int v0 = boxi[c], v1 = boxi[cells + c], v2 = boxi[2 * cells + c];
+      if ((v0 | v1 | v2) == 0) continue;
+      atomicAdd(fib4 + n0 + box3_goff(A.g, lx, ly, lz),
+                make_float4((float)v0 * inv, (float)v1 * inv, (float)v2 * inv, 0.0f));
+    }
+    return;
+  }
   const int rows = S * S;
   int gx = org[0] + lane;
   if (gx < 0 || gx >= nn[0]) gx = ((gx % nn[0]) + nn[0]) % nn[0];  // only periodic x reaches the add
@@ -968,14 +1058,14 @@ __global__ void __launch_bounds__(256) ibm_forces_kernel(IbmArgs A) {
 }
 
 // 2D form of the same sums, with u* from the particle's box buffer, LP lanes per
-// particle (a half-warp in a single run: 10^4 particles then fit one wave of the GPU;
-// a warp in the fused batch).  Each lane takes its candidate nodes NB at a time, so
-// their loads are in flight together.
+// particle (a half-warp in a single run, at most 48 registers a thread: 10^4 particles
+// then fit one wave of the GPU; a warp in the fused batch).  Each lane takes its
+// candidate nodes NB at a time, so their loads are in flight together.
 constexpr int kForceBatch = 6;
 
 template <int SC, int LP = 32>
 __device__ __forceinline__ void forces2_body(const IbmArgs& A, unsigned blk) {
-  constexpr int NB = LP == 16 ? 9 : kForceBatch;
+  constexpr int NB = LP == 16 ? 5 : kForceBatch;
   const unsigned gt = blk * blockDim.x + threadIdx.x;
   if ((int)((gt & ~31u) / LP) >= A.np) return;  // the warp's first particle: whole warp
   const int i = (int)(gt / LP);
@@ -1039,7 +1129,7 @@ __device__ __forceinline__ void forces2_body(const IbmArgs& A, unsigned blk) {
 }
 
 template <int SC, bool FUSED>
-__global__ void __launch_bounds__(256) ibm_forces2_kernel(IbmArgs A0, Fuse FU) {
+__global__ void __launch_bounds__(256, FUSED ? 1 : 5) ibm_forces2_kernel(IbmArgs A0, Fuse FU) {
   pdl_enter();
   IBMLBM_BIND(FUSED, IbmArgs, A, A0, FU, blk);
   if constexpr (FUSED) {  // members differ in box size: run the code compiled for this one
