@@ -37,6 +37,30 @@ __device__ __forceinline__ float delta3(float r) {
 
 __device__ __forceinline__ float delta_w(int kind, float r) { return kind == 3 ? delta3(r) : delta4(r); }
 
+// The weights of the four support nodes along one axis, at offsets (t - 1) - f from
+// the point (t = 0..3, f as support_first gives it).  At these four offsets every
+// branch of a delta function takes the same square root, so one suffices:
+//   4-point (f in [0, 1)), q = sqrt(1 + 4 f - 4 f^2):
+//     (3 - 2f - q) / 8, (3 - 2f + q) / 8, (1 + 2f + q) / 8, (1 + 2f - q) / 8;
+//   3-point (f in [-1/2, 1/2)), q = sqrt(1 - 3 f^2):
+//     (2 - 3f - q) / 6, (1 + q) / 3, (2 + 3f - q) / 6, 0.
+// (Substituting |r| = 1 + f, f, 1 - f, 2 - f into the two branches of each function.)
+__device__ __forceinline__ void delta_weights(int kind, float f, float (&w)[4]) {
+  if (kind == 3) {
+    const float q = sqrtf(fmaxf(0.0f, 1.0f - 3.0f * f * f));
+    w[0] = (2.0f - 3.0f * f - q) * (1.0f / 6.0f);
+    w[1] = (1.0f + q) * (1.0f / 3.0f);
+    w[2] = (2.0f + 3.0f * f - q) * (1.0f / 6.0f);
+    w[3] = 0.0f;
+  } else {
+    const float q = sqrtf(fmaxf(0.0f, 1.0f + 4.0f * f - 4.0f * f * f));
+    w[0] = 0.125f * (3.0f - 2.0f * f - q);
+    w[1] = 0.125f * (3.0f - 2.0f * f + q);
+    w[2] = 0.125f * (1.0f + 2.0f * f + q);
+    w[3] = 0.125f * (1.0f + 2.0f * f - q);
+  }
+}
+
 // First support node along one axis of a fixed-point coordinate X, and fr such that
 // the offset of support node t (t = 0..3) from X is (t - 1) - fr: 4-point nodes
 // floor(X)-1 .. floor(X)+2 (fr = frac X); 3-point nodes round(X)-1 .. round(X)+1
@@ -211,12 +235,12 @@ __device__ __forceinline__ void interp2_body(const IbmArgs& A, int m, unsigned b
     if (lx0 < 0 || ly0 < 0 || lx0 + 3 >= S || ly0 + 3 >= S) {
       atomicOr(A.status, ST_CAPACITY);
     } else {
-      float wx[4];
-#pragma unroll
-      for (int sx = 0; sx < 4; ++sx) wx[sx] = delta_w(A.delta_kind, (float)(sx - 1) - rx);
+      float wx[4], wyv[4];
+      delta_weights(A.delta_kind, rx, wx);
+      delta_weights(A.delta_kind, ry, wyv);
 #pragma unroll
       for (int sy = 0; sy < 4; ++sy) {
-        const float wy = delta_w(A.delta_kind, (float)(sy - 1) - ry);
+        const float wy = wyv[sy];
         const int o = (ly0 + sy) * P + lx0;
         float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
@@ -311,11 +335,13 @@ __device__ __forceinline__ void spread2_body(const IbmArgs& A, unsigned blk) {
       valid = lbx >= 0 && lby >= 0 && lbx + 3 < S && lby + 3 < S;
       if (!valid) atomicOr(A.status, ST_CAPACITY);
       float wx[4], wy[4];
+      delta_weights(A.delta_kind, rx, wx);
+      delta_weights(A.delta_kind, ry, wy);
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
+      for (int t = 0; t < 4; ++t) {  // no weight beyond a wall
         const int gx = bx + t, gy = by + t;
-        wx[t] = (!A.g.per[0] && (gx < 0 || gx >= A.g.nx)) ? 0.0f : delta_w(A.delta_kind, (float)(t - 1) - rx);
-        wy[t] = (!A.g.per[1] && (gy < 0 || gy >= A.g.ny)) ? 0.0f : delta_w(A.delta_kind, (float)(t - 1) - ry);
+        if (!A.g.per[0] && (gx < 0 || gx >= A.g.nx)) wx[t] = 0.0f;
+        if (!A.g.per[1] && (gy < 0 || gy >= A.g.ny)) wy[t] = 0.0f;
       }
       float* row = tw + lane * kTw;
 #pragma unroll
@@ -449,15 +475,16 @@ __device__ __forceinline__ void mdf3_table(const IbmArgs& A, int i, const int (&
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const long long X = A.Xb[b * 3 + a];
-      float f;
+      float f, w[4];
       const int s0 = support_first(A.delta_kind, X, f);
       const int l0 = s0 - org[a];
       if (l0 < 0 || l0 + 3 >= S) valid = false;
       base += l0 * (a == 0 ? 1 : a == 1 ? Py : Pz);
+      delta_weights(A.delta_kind, f, w);
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const int gc = s0 + t;
-        row[4 * a + t] = (!A.g.per[a] && (gc < 0 || gc >= nn[a])) ? 0.0f : delta_w(A.delta_kind, (float)(t - 1) - f);
+        row[4 * a + t] = (!A.g.per[a] && (gc < 0 || gc >= nn[a])) ? 0.0f : w[t];
       }
     }
     if (!valid) {
@@ -621,33 +648,43 @@ __global__ void __launch_bounds__(kMdf3Threads, 2) ibm_interp3_kernel(IbmArgs A,
   mdf3_table(A, i, org, S, Py, Pz, tab);
   __syncthreads();
 
-  // 2. interpolation: warp w takes points 2 (w + kMdf3Warps j) + h, half h
-  const int h = lane >> 4, sx = lane & 3, sy = (lane >> 2) & 3;
-  const int colo = sx + Py * sy;
-  for (int p0 = 2 * warp; p0 < A.nl; p0 += 2 * kMdf3Warps) {
-    const int p = p0 + h;
+  // 2. interpolation: warp w takes points 8 (w + kMdf3Warps j) + slot, four lanes a
+  //    point, lane sz of the point the 16 support nodes of z level sz
+  const int slot = lane >> 2, sz = lane & 3;
+  for (int p0 = 8 * warp; p0 < A.nl; p0 += 8 * kMdf3Warps) {
+    const int p = p0 + slot;
     const bool act = p < A.nl;
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
     if (act) {
       const float* row = tab + (size_t)p * kTab3;
-      const float wxy = row[sx] * row[4 + sy];
-      const int c0 = __float_as_int(row[12]) + colo;
+      const float wz = row[8 + sz];
+      float wx[4], wy[4];
 #pragma unroll
-      for (int sz = 0; sz < 4; ++sz) {
-        const float w = wxy * row[8 + sz];
-        const int c = c0 + Pz * sz;
-        a0 += w * box[c];
-        a1 += w * box[cells + c];
-        a2 += w * box[2 * cells + c];
+      for (int t = 0; t < 4; ++t) {
+        wx[t] = row[t];
+        wy[t] = row[4 + t];
+      }
+      const int c0 = __float_as_int(row[12]) + Pz * sz;
+#pragma unroll
+      for (int sy = 0; sy < 4; ++sy) {
+        const float wyz = wy[sy] * wz;
+        const int cr = c0 + Py * sy;
+#pragma unroll
+        for (int sx = 0; sx < 4; ++sx) {
+          const float w = wx[sx] * wyz;
+          a0 += w * box[cr + sx];
+          a1 += w * box[cells + cr + sx];
+          a2 += w * box[2 * cells + cr + sx];
+        }
       }
     }
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) {
+    for (int o = 1; o < 4; o <<= 1) {
       a0 += __shfl_xor_sync(0xffffffffu, a0, o);
       a1 += __shfl_xor_sync(0xffffffffu, a1, o);
       a2 += __shfl_xor_sync(0xffffffffu, a2, o);
     }
-    if (act && (lane & 15) == 0) {  // u_b into the table
+    if (act && sz == 0) {  // u_b into the table
       float* row = tab + (size_t)p * kTab3;
       row[13] = a0;
       row[14] = a1;
