@@ -4,9 +4,9 @@
 //   interpolation  u_b = sum delta(x - X_b) (u* + dt f_IB / (2 rho_f))   (Eq. 7, 12, 47)
 //                  dF_b = 2 rho_f (U_b - u_b) / dt, F_b += dF_b           (Eq. 10)
 //   spreading      f_IB += sum_b dF_b delta(x - X_b) dV                    (Eq. 11, 13, 48)
-// Each particle's node box lives in shared memory: 2D one warp per particle (one
-// interpolation and one spreading launch per iteration), 3D one block per sphere (both
-// in one launch).  The box cells reach f_IB with one global atomic per cell.
+// Each particle's node box lives in shared memory: 2D one warp per particle, 3D one
+// block per sphere, with one interpolation and one spreading launch per iteration.
+// The box cells reach f_IB with one global atomic per cell.
 // Gathering u* + f_IB/2 equals the paper's u^(m-1) = u^(m-2) + dt D_E dF/(2 rho_f)
 // by linearity, so no separate velocity field is updated between iterations.
 #include <cmath>
@@ -418,21 +418,12 @@ __global__ void __launch_bounds__(kIbmWarps * 32) ibm_spread2_kernel(IbmArgs A0,
 }
 
 // ------------------------------------------------------------------ 3D
-// One block per sphere and MDF iteration m (Eq. 47, 10, 48 in one launch):
-//   1. stage u^(m-1) = u* + f_IB/2 (m = 1: u*) of the nodes of the sphere's box that
-//      lie in the marked ball (every support node does) into shared memory, one box
-//      row per warp and round, one node per lane (u* and f_IB are [N][4]);
-//   2. interpolate every point, one point per half-warp, lane (sx, sy) of the 4 x 4
-//      support columns, the 4 z levels in a loop; dF_b = 2 (U_b - u_b);
-//   3. spread dF_b dV into the same box (reused), accumulated as 32-bit fixed point
-//      with integer shared-memory atomics.  The scale of the sphere is 2^30 over
-//      (max |dF_b dV| times N_L times 1/8), a bound on any node's sum (every weight
-//      is at most 1/8), so no sum overflows and the rounding is that of single
-//      precision;
-//   4. add the non-zero box cells to f_IB with one vector atomic per cell.
-// Box rows are box3_pitch(S) cells apart (4 modulo 8), so the 16 columns of a support
-// fall on 16 banks.  Each point's row of the table holds its 12 weights, its first
-// box cell and dF_b dV.
+// One block per sphere, two launches per MDF iteration m (Eq. 47, 10, then 48):
+// the interpolation stages u^(m-1) of the sphere's node box in shared memory and
+// interpolates every point from it; the spreading accumulates dF_b dV into the box and
+// adds its non-zero cells to f_IB.  Box rows are box3_pitch(S) cells apart (4 modulo
+// 8), so the 16 columns of a support fall on 16 banks.  Each point's row of the table
+// holds its 12 weights, its first box cell and u_b or dF_b dV.
 constexpr int kMdf3Threads = 512;
 constexpr int kMdf3Warps = kMdf3Threads / 32;
 constexpr int kTab3 = 17;  // table floats per point: 16 used; an odd stride keeps the rows
@@ -559,11 +550,10 @@ __device__ __forceinline__ void stage3_from_list(const IbmArgs& A, float* box, i
 }
 
 // Interpolation of MDF iteration m, one block per sphere (Eq. 47, 10):
-//   1. stage u^(m-1) = u* + f_IB/2 (m = 1: u*) of the nodes of the sphere's box that
-//      lie in the marked ball (every support node does) into shared memory, one box
-//      row per warp and round, one node per lane (u* and f_IB are [N][4]);
-//   2. interpolate every point, one point per half-warp, lane (sx, sy) of the 4 x 4
-//      support columns, the 4 z levels in a loop; dF_b = 2 (U_b - u_b), F_b += dF_b.
+//   1. stage u^(m-1) = u* + f_IB/2 (m = 1: u*) of the box nodes that can be support
+//      nodes into shared memory (u* and f_IB are [N][4]);
+//   2. interpolate every point, four lanes a point (one z level each, the 16 nodes of
+//      the level in a loop); dF_b = 2 (U_b - u_b), F_b += dF_b.
 // The spreading of the iteration is a separate launch, so every sphere reads f_IB
 // with the increments of iterations 1 .. m-1 of all spheres and none of iteration m
 // (the iteration of the FP64 oracle).
@@ -771,21 +761,21 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_spread3_kernel(IbmArgs A) {
   const float scale = 1073741824.0f / (gmax * 0.125f * (float)A.nl);  // 2^30 / bound
   const float inv = 1.0f / scale;
 
-  // 2. spreading, one point per half-warp as in the interpolation
-  const int h = lane >> 4, sx = lane & 3, sy = (lane >> 2) & 3;
-  const int colo = sx + Py * sy;
-  for (int p0 = 2 * warp; p0 < A.nl; p0 += 2 * kMdf3Warps) {
-    const int p = p0 + h;
-    if (p >= A.nl) continue;
+  // 2. spreading, one point per warp: lane (sx, sy, zh) adds to the support nodes of
+  //    z levels 2 zh and 2 zh + 1 (two box planes apart, 2 Pz = 16 modulo 32 for the
+  //    box sides used, so the 32 lanes of an atomic touch 32 banks)
+  const int zh = lane >> 4, sx = lane & 3, sy = (lane >> 2) & 3;
+  const int colo = sx + Py * sy + 2 * Pz * zh;
+  for (int p = warp; p < A.nl; p += kMdf3Warps) {
     const float* row = tab + (size_t)p * kTab3;
     const float wxy = row[sx] * row[4 + sy] * scale;
     const int c0 = __float_as_int(row[12]) + colo;
     const float f0 = row[13], f1 = row[14], f2 = row[15];
 #pragma unroll
-    for (int sz = 0; sz < 4; ++sz) {
-      const float w = wxy * row[8 + sz];
+    for (int k = 0; k < 2; ++k) {
+      const float w = wxy * row[8 + 2 * zh + k];
       if (w == 0.0f) continue;
-      const int c = c0 + Pz * sz;
+      const int c = c0 + Pz * k;
       atomicAdd(&boxi[c], __float2int_rn(w * f0));
       atomicAdd(&boxi[cells + c], __float2int_rn(w * f1));
       atomicAdd(&boxi[2 * cells + c], __float2int_rn(w * f2));

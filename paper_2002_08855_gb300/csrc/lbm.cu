@@ -248,9 +248,11 @@ __device__ __forceinline__ void step_row_nodes(const LbmArgs& A, long long row, 
 }
 
 // Row tiles: a block of kLbmBlock threads takes K * kLbmBlock consecutive nodes of one
-// row (spr blocks per row).
+// row (spr blocks per row).  Blocks per SM the registers must allow: D2Q9 10 (48
+// registers a thread); D3Q19 7 (72 registers, a few bytes spilled: more PDF loads in
+// flight than at the 80 registers it takes unbounded).
 template <class L, int PARITY, int ST, int K, bool FUSED>
-__global__ void __launch_bounds__(kLbmBlock) lbm_step_kernel(LbmArgs A0, int spr0, Fuse FU) {
+__global__ void __launch_bounds__(kLbmBlock, L::dim == 3 ? 7 : 10) lbm_step_kernel(LbmArgs A0, int spr0, Fuse FU) {
   IBMLBM_BIND(FUSED, LbmArgs, A, A0, FU, blk);
   const Geo& g = A.g;
   const int spr = FUSED ? (g.nx + K * kLbmBlock - 1) / (K * kLbmBlock) : spr0;
