@@ -1085,14 +1085,16 @@ __global__ void __launch_bounds__(256) ibm_forces_kernel(IbmArgs A) {
 }
 
 // 2D form of the same sums, with u* from the particle's box buffer, LP lanes per
-// particle (a half-warp in a single run, at most 48 registers a thread: 10^4 particles
-// then fit one wave of the GPU; a warp in the fused batch).  Each lane takes its
-// candidate nodes NB at a time, so their loads are in flight together.
+// particle (a half-warp in a single run; a warp in the fused batch).  Each lane takes
+// its candidate nodes NB at a time, so their loads are in flight together.  The common
+// box sizes (16, 22) take 5 at a time within 48 registers a thread, so that 10^4
+// particles fit one wave of the GPU; the general box (large particles, few of them)
+// takes 9.
 constexpr int kForceBatch = 6;
 
 template <int SC, int LP = 32>
 __device__ __forceinline__ void forces2_body(const IbmArgs& A, unsigned blk) {
-  constexpr int NB = LP == 16 ? 5 : kForceBatch;
+  constexpr int NB = LP == 16 ? (SC ? 5 : 9) : kForceBatch;
   const unsigned gt = blk * blockDim.x + threadIdx.x;
   if ((int)((gt & ~31u) / LP) >= A.np) return;  // the warp's first particle: whole warp
   const int i = (int)(gt / LP);
@@ -1156,7 +1158,7 @@ __device__ __forceinline__ void forces2_body(const IbmArgs& A, unsigned blk) {
 }
 
 template <int SC, bool FUSED>
-__global__ void __launch_bounds__(256, FUSED ? 1 : 5) ibm_forces2_kernel(IbmArgs A0, Fuse FU) {
+__global__ void __launch_bounds__(256, FUSED ? 1 : (SC == 0 ? 3 : 5)) ibm_forces2_kernel(IbmArgs A0, Fuse FU) {
   pdl_enter();
   IBMLBM_BIND(FUSED, IbmArgs, A, A0, FU, blk);
   if constexpr (FUSED) {  // members differ in box size: run the code compiled for this one
