@@ -43,7 +43,7 @@ extern "C" {
 
 #define IBMLBM_OK 0
 #define IBMLBM_ERR_INVALID_ARG (-1)   /* bad pointer, size or configuration value */
-#define IBMLBM_ERR_UNSUPPORTED (-2)   /* valid request outside what this build does */
+#define IBMLBM_ERR_UNSUPPORTED (-2)   /* valid request outside what the library supports */
 #define IBMLBM_ERR_WORKSPACE (-3)     /* workspace missing, misaligned or too small */
 #define IBMLBM_ERR_CUDA (-4)          /* a CUDA runtime call failed */
 #define IBMLBM_ERR_NONFINITE (-5)     /* NaN/Inf in a particle state (device check) */

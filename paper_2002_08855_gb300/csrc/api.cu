@@ -1380,8 +1380,8 @@ int ibm_lbm_pair_search(int32_t dim, const int32_t* n_nodes, const int32_t* peri
 }  // extern "C"
 
 // ============================================================= batched ensemble
-// Many independent 2D cavities stepped together (the ensemble of SURVEY-style config
-// 5): every member is an ordinary run in its own slice of one workspace, and every
+// Many independent 2D cavities stepped together (an ensemble of cavities of uneven
+// size): every member is an ordinary run in its own slice of one workspace, and every
 // kernel of a step runs once for all members (fused launches, see Fuse).
 namespace {
 
