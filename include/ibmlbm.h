@@ -110,6 +110,18 @@ typedef struct ibm_lbm_handle ibm_lbm_handle;
  * Errors: IBMLBM_ERR_INVALID_ARG for a configuration ibm_lbm_init would reject. */
 int ibm_lbm_workspace_size(const ibm_lbm_config* cfg, size_t* bytes);
 
+/* The 3D staging list of the configuration (host only, no device call): the cells of
+ * a sphere's node box (side S = 2 ceil(D_p / 2) + 6, the box starting rcell + 2 nodes
+ * before the centre's anchor node, rcell = ceil(D_p / 2)) that can be a support node
+ * of some Lagrangian point for some position of the centre within its anchor cell
+ * (Eq. 47-48 with the configuration's delta function), packed lx | ly << 5 | lz << 10.
+ * The interpolation stages, and the spreading flushes, only these cells of spheres
+ * whose box lies inside the domain.  cells: host [cap] (may be NULL with cap = 0 to
+ * query the count); n: the number of entries, 0 where no list is used (2D, no
+ * particles, box side above 32).  Errors: INVALID_ARG (configuration, NULL n),
+ * CAPACITY (n > cap, with cells not NULL). */
+int ibm_lbm_stage_list(const ibm_lbm_config* cfg, int32_t* cells, int64_t cap, int64_t* n);
+
 /* Create a run.  d_workspace: device memory of at least ibm_lbm_workspace_size
  * bytes, borrowed (not owned) until ibm_lbm_destroy.  stream: every kernel and
  * copy of the run is ordered on it (within a step the particle update runs on a

@@ -103,6 +103,7 @@ SIGNATURES = {
     "ibm_lbm_get_pairs": (C.c_int, [_vp, _ip, C.c_int64, _i64p]),
     "ibm_lbm_get_launch_count": (C.c_int, [_vp, _i64p]),
     "ibm_lbm_time_parts": (C.c_int, [_vp, C.c_int32, _dp]),
+    "ibm_lbm_stage_list": (C.c_int, [C.POINTER(Config), _ip, C.c_int64, _i64p]),
     "ibm_lbm_destroy": (None, [_vp]),
     "ibm_lbm_last_error": (C.c_char_p, []),
     "ibm_lbm_pair_search_scratch_size": (C.c_int, [C.c_int32, _ip, C.c_double, C.c_double,
@@ -165,6 +166,19 @@ def _check(rc: int, where: str):
 
 def _ptr(a, ctype):
     return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def stage_list(w):
+    """The 3D staging list of a workload's node box (host only): int32 array of cells
+    packed lx | ly << 5 | lz << 10 (empty where no list is used)."""
+    import numpy as np
+
+    cfg = make_config(w)
+    n = C.c_int64(0)
+    _check(lib().ibm_lbm_stage_list(C.byref(cfg), None, 0, C.byref(n)), "stage_list")
+    out = np.zeros(max(n.value, 1), dtype=np.int32)
+    _check(lib().ibm_lbm_stage_list(C.byref(cfg), _ptr(out, C.c_int32), n.value, C.byref(n)), "stage_list")
+    return out[:n.value]
 
 
 def workspace_size(w, max_neighbors: int = 0) -> int:

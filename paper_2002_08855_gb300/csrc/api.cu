@@ -691,6 +691,19 @@ int check_handle(ibm_lbm_handle* h) {
 
 extern "C" {
 
+int ibm_lbm_stage_list(const ibm_lbm_config* cfg, int32_t* cells, int64_t cap, int64_t* n) {
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  if (!n) return fail(IBMLBM_ERR_INVALID_ARG, "n is NULL");
+  const Derived d = derive(cfg);
+  const std::vector<int> list = cfg->n_particles > 0 ? stage3_list(d, cfg->delta_kind) : std::vector<int>();
+  *n = (int64_t)list.size();
+  if (!cells) return IBMLBM_OK;
+  if (*n > cap) return fail(IBMLBM_ERR_CAPACITY, "staging list longer than cap");
+  for (size_t k = 0; k < list.size(); ++k) cells[k] = list[k];
+  return IBMLBM_OK;
+}
+
 int ibm_lbm_workspace_size(const ibm_lbm_config* cfg, size_t* bytes) {
   int rc = check_config(cfg);
   if (rc) return rc;
