@@ -1158,7 +1158,7 @@ __device__ __forceinline__ void forces2_body(const IbmArgs& A, unsigned blk) {
 }
 
 template <int SC, bool FUSED>
-__global__ void __launch_bounds__(256, FUSED ? 1 : (SC == 0 ? 3 : 5)) ibm_forces2_kernel(IbmArgs A0, Fuse FU) {
+__global__ void __launch_bounds__(256, (FUSED || SC == 0) ? 3 : 5) ibm_forces2_kernel(IbmArgs A0, Fuse FU) {
   pdl_enter();
   IBMLBM_BIND(FUSED, IbmArgs, A, A0, FU, blk);
   if constexpr (FUSED) {  // members differ in box size: run the code compiled for this one
