@@ -169,3 +169,29 @@ def test_thickened_shell_and_iterations_reduce_slip():
     df = _moving_cylinder(1, 1.0).get_mdf_residual()[0]
     # Sec. 2.2: with drs = dh (conventional DF) the slip after one pass is much larger
     assert res[1] < 0.25 * df
+
+
+def test_drag_converges_with_mdf_iterations():
+    """A fixed cylinder in a periodic box of fluid started at a uniform velocity: the
+    hydrodynamic force after 30 steps converges as the number of MDF iterations grows
+    (each difference to M = 10 smaller than the last, below 0.2 % from M = 3), and the
+    boundary residual after the last iteration does not grow with M."""
+    N = 96 * 64
+    res = {}
+    for M in (1, 2, 3, 4, 10):
+        w = Workload(name="drag", dim=2, nx=96, ny=64, periodic=(1, 1, 0), tau=0.8, n_particles=1,
+                     n_lag=50, diameter=16.0, delta_kind=4, drs=2.6, mdf_iters=M, fixed_particles=1,
+                     density_ratio=1.5)
+        S = oracle.Sim(w.as_dict(), np.array([[40.3, 31.7]]))
+        u = np.zeros((2, N))
+        u[0] = 0.01
+        S.set_fields(np.zeros(N), u)
+        S.step(30)
+        res[M] = (S.get_particles()["F_h"][0], S.get_mdf_residual()[0])
+        S.close()
+    ref = res[10][0]
+    gap = [np.linalg.norm(res[M][0] - ref) / np.linalg.norm(ref) for M in (1, 2, 3, 4)]
+    assert gap[0] > gap[1] > gap[2] > gap[3]
+    assert gap[2] < 2e-3
+    rms = [res[M][1] for M in (1, 2, 3, 4, 10)]
+    assert all(a >= b for a, b in zip(rms, rms[1:]))
