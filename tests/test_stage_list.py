@@ -64,3 +64,15 @@ def test_no_list_in_2d_or_without_particles():
     assert binding.stage_list(w2).size == 0
     w0 = _workload(12.0, 4).with_(n_particles=0)
     assert binding.stage_list(w0).size == 0
+
+
+def test_query_errors():
+    import ctypes as C
+
+    lib = binding.lib()
+    cfg = binding.make_config(_workload(12.0, 4))
+    n = C.c_int64(0)
+    assert lib.ibm_lbm_stage_list(C.byref(cfg), None, 0, C.byref(n)) == 0 and n.value > 0
+    small = (C.c_int32 * 8)()
+    assert lib.ibm_lbm_stage_list(C.byref(cfg), small, 8, C.byref(n)) == -7  # IBMLBM_ERR_CAPACITY
+    assert lib.ibm_lbm_stage_list(C.byref(cfg), None, 0, None) == -1  # IBMLBM_ERR_INVALID_ARG
