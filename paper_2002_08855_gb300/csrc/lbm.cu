@@ -39,25 +39,26 @@ __device__ __forceinline__ void put_pdfs(const Geo& g, void* __restrict__ f, int
   }
 }
 
-// post-collision store of the given parity (after which the opposite parity holds)
-template <class L, int PARITY, int ST, bool INNER = false>
+// post-collision store of the given parity (after which the opposite parity holds);
+// RAW: fa holds the stored variable (h_a for the 16-bit storages)
+template <class L, int PARITY, int ST, bool INNER = false, bool RAW = false>
 __device__ __forceinline__ void store_post(const Geo& g, void* __restrict__ f, int x, int y,
                                            int z, long long n, const float (&fa)[L::Q]) {
   const long long N = g.Np;  // plane stride
 #pragma unroll
   for (int a = 0; a < L::Q; ++a) {
     if (a == 0) {
-      pdf_store<L, ST>(f, n, 0, fa[0]);
+      pdf_store<L, ST, RAW>(f, n, 0, fa[0]);
     } else if (PARITY == 0) {
-      pdf_store<L, ST>(f, opp<L>(a) * N + n, a, fa[a]);
+      pdf_store<L, ST, RAW>(f, opp<L>(a) * N + n, a, fa[a]);
     } else if (INNER) {
-      pdf_store<L, ST>(f, a * N + n + inner_offset<L>(g, a, -1), a, fa[a]);
+      pdf_store<L, ST, RAW>(f, a * N + n + inner_offset<L>(g, a, -1), a, fa[a]);
     } else {
       long long dst;
       if (neighbour<L>(g, a, -1, x, y, z, n, dst))
-        pdf_store<L, ST>(f, a * N + dst, a, fa[a]);
+        pdf_store<L, ST, RAW>(f, a * N + dst, a, fa[a]);
       else
-        pdf_store<L, ST>(f, opp<L>(a) * N + n, a, fa[a]);
+        pdf_store<L, ST, RAW>(f, opp<L>(a) * N + n, a, fa[a]);
     }
   }
 }
@@ -110,6 +111,60 @@ __device__ __forceinline__ void collide(float (&f)[L::Q], const float (&F)[3], f
     const int b = a + L::H;
     f[a] = f[a] - omega * (f[a] - (eq_even + eq_odd)) + (F_even + F_odd);
     f[b] = f[b] - omega * (f[b] - (eq_even - eq_odd)) + (F_even - F_odd);
+  }
+}
+
+// The same collision on the stored variable h_a = f_a / w_a (16-bit storages): the
+// moments weigh each h_a by w_a, and the equilibrium and force terms are divided by
+// w_a, which removes w_a from them (Eq. 4, 8): h_a^eq = 3 p + 4.5 (e_a.u)^2 - 1.5 u.u
+// + 3 e_a.u for a >= 1, h_0^eq = 3 (1 - 1/w_0) p - 1.5 u.u; F_a / w_a likewise.
+template <class L>
+__device__ __forceinline__ void collide_h(float (&h)[L::Q], const float (&F)[3], float omega,
+                                          float kforce) {
+  float us[3] = {0.0f, 0.0f, 0.0f}, s1 = 0.0f;
+#pragma unroll
+  for (int a = 1; a < L::Q; ++a) {
+    const float fa = L::w(a) * h[a];
+    s1 += fa;
+#pragma unroll
+    for (int k = 0; k < L::dim; ++k) {
+      if (L::e(a, k) == 1) us[k] += fa;
+      if (L::e(a, k) == -1) us[k] -= fa;
+    }
+  }
+  float u[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) u[k] = (k < L::dim) ? us[k] + 0.5f * F[k] : 0.0f;  // Eq. 7
+  const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+  const float p = pressure<L>(s1, uu);
+  {
+    constexpr float w0 = L::w(0);
+    const float heq = 3.0f * (1.0f - 1.0f / w0) * p - 1.5f * uu;
+    h[0] = h[0] - omega * (h[0] - heq) - 3.0f * kforce * uF;
+  }
+  const float p3 = 3.0f * p - 1.5f * uu;
+#pragma unroll
+  for (int a = 1; a <= L::H; ++a) {
+    float eu = 0.0f, eF = 0.0f;
+#pragma unroll
+    for (int k = 0; k < L::dim; ++k) {
+      if (L::e(a, k) == 1) {
+        eu += u[k];
+        eF += F[k];
+      }
+      if (L::e(a, k) == -1) {
+        eu -= u[k];
+        eF -= F[k];
+      }
+    }
+    const float eq_even = p3 + 4.5f * eu * eu;
+    const float eq_odd = 3.0f * eu;
+    const float F_even = kforce * (9.0f * eu * eF - 3.0f * uF);
+    const float F_odd = 3.0f * kforce * eF;
+    const int b = a + L::H;
+    h[a] = h[a] - omega * (h[a] - (eq_even + eq_odd)) + (F_even + F_odd);
+    h[b] = h[b] - omega * (h[b] - (eq_even - eq_odd)) + (F_even - F_odd);
   }
 }
 
@@ -192,14 +247,16 @@ __device__ __forceinline__ void ib_force_clear(const LbmArgs& A, long long n, co
 template <class L, int PARITY, int ST>
 __device__ __forceinline__ void step_node(const LbmArgs& A, long long row, int x, int y, int z,
                                           long long n) {
+  constexpr bool H = ST != STORE_F32;  // 16-bit storages collide the stored h = f / w
   float fa[L::Q], fv[3];
-  load_pdfs<L, PARITY, ST>(A.g, A.f, x, y, z, n, fa);
+  load_pdfs<L, PARITY, ST, false, H>(A.g, A.f, x, y, z, n, fa);
   ib_force<L>(A, row, x, n, fv);
   float F[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) F[k] = A.body[k] + fv[k];
-  collide<L>(fa, F, A.omega, A.kforce);
-  store_post<L, PARITY, ST>(A.g, A.f, x, y, z, n, fa);
+  if constexpr (H) collide_h<L>(fa, F, A.omega, A.kforce);
+  else collide<L>(fa, F, A.omega, A.kforce);
+  store_post<L, PARITY, ST, false, H>(A.g, A.f, x, y, z, n, fa);
   ib_force_clear<L>(A, n, fv);
 }
 
@@ -230,7 +287,7 @@ __device__ __forceinline__ void step_row_nodes(const LbmArgs& A, long long row, 
     act[k] = x < g.nx && !(PARITY == 1 && (x == 0 || x == g.nx - 1));
     if (!act[k]) continue;
     const long long n = (long long)x + (long long)g.nx * row;
-    load_pdfs<L, PARITY, ST, PARITY == 1>(g, A.f, x, y, z, n, fa[k]);
+    load_pdfs<L, PARITY, ST, PARITY == 1, (ST != STORE_F32)>(g, A.f, x, y, z, n, fa[k]);
     ib_force<L>(A, row, x, n, fv[k]);  // with the PDFs: one memory latency
   }
 #pragma unroll
@@ -241,8 +298,9 @@ __device__ __forceinline__ void step_row_nodes(const LbmArgs& A, long long row, 
     float F[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) F[c] = A.body[c] + fv[k][c];
-    collide<L>(fa[k], F, A.omega, A.kforce);
-    store_post<L, PARITY, ST, PARITY == 1>(g, A.f, x, y, z, n, fa[k]);
+    if constexpr (ST != STORE_F32) collide_h<L>(fa[k], F, A.omega, A.kforce);  // on h = f / w
+    else collide<L>(fa[k], F, A.omega, A.kforce);
+    store_post<L, PARITY, ST, PARITY == 1, (ST != STORE_F32)>(g, A.f, x, y, z, n, fa[k]);
     ib_force_clear<L>(A, n, fv[k]);
   }
 }

@@ -35,25 +35,28 @@ struct PdfType<STORE_BF16> {
   using T = __nv_bfloat16;
 };
 
-template <class L, int ST>
+// RAW: the stored variable itself (h_a for the 16-bit storages), without the weight
+template <class L, int ST, bool RAW = false>
 __device__ __forceinline__ float pdf_load(const void* f, long long idx, int a) {
   if constexpr (ST == STORE_F32) {
     return static_cast<const float*>(f)[idx];
   } else if constexpr (ST == STORE_F16) {
-    return L::w(a) * __half2float(static_cast<const __half*>(f)[idx]);
+    const float h = __half2float(static_cast<const __half*>(f)[idx]);
+    return RAW ? h : L::w(a) * h;
   } else {
-    return L::w(a) * __bfloat162float(static_cast<const __nv_bfloat16*>(f)[idx]);
+    const float h = __bfloat162float(static_cast<const __nv_bfloat16*>(f)[idx]);
+    return RAW ? h : L::w(a) * h;
   }
 }
 
-template <class L, int ST>
+template <class L, int ST, bool RAW = false>
 __device__ __forceinline__ void pdf_store(void* f, long long idx, int a, float v) {
   if constexpr (ST == STORE_F32) {
     static_cast<float*>(f)[idx] = v;
   } else if constexpr (ST == STORE_F16) {
-    static_cast<__half*>(f)[idx] = __float2half_rn(v * (1.0f / L::w(a)));
+    static_cast<__half*>(f)[idx] = __float2half_rn(RAW ? v : v * (1.0f / L::w(a)));
   } else {
-    static_cast<__nv_bfloat16*>(f)[idx] = __float2bfloat16_rn(v * (1.0f / L::w(a)));
+    static_cast<__nv_bfloat16*>(f)[idx] = __float2bfloat16_rn(RAW ? v : v * (1.0f / L::w(a)));
   }
 }
 
@@ -100,23 +103,24 @@ __device__ __forceinline__ long long inner_offset(const Geo& g, int a, int s) {
 }
 
 // pre-collision PDFs f_a(x) of the current time under the layout of the given parity;
-// INNER: the node is at least one node away from every domain face
-template <class L, int PARITY, int ST, bool INNER = false>
+// INNER: the node is at least one node away from every domain face; RAW: the stored
+// variable (h_a = f_a / w_a for the 16-bit storages)
+template <class L, int PARITY, int ST, bool INNER = false, bool RAW = false>
 __device__ __forceinline__ void load_pdfs(const Geo& g, const void* __restrict__ f, int x,
                                           int y, int z, long long n, float (&fa)[L::Q]) {
   const long long N = g.Np;  // plane stride
 #pragma unroll
   for (int a = 0; a < L::Q; ++a) {
     if (PARITY == 0 || a == 0) {
-      fa[a] = pdf_load<L, ST>(f, a * N + n, a);
+      fa[a] = pdf_load<L, ST, RAW>(f, a * N + n, a);
     } else if (INNER) {
-      fa[a] = pdf_load<L, ST>(f, opp<L>(a) * N + n + inner_offset<L>(g, a, 1), opp<L>(a));
+      fa[a] = pdf_load<L, ST, RAW>(f, opp<L>(a) * N + n + inner_offset<L>(g, a, 1), opp<L>(a));
     } else {
       long long src;
       if (neighbour<L>(g, a, 1, x, y, z, n, src))
-        fa[a] = pdf_load<L, ST>(f, opp<L>(a) * N + src, opp<L>(a));
+        fa[a] = pdf_load<L, ST, RAW>(f, opp<L>(a) * N + src, opp<L>(a));
       else
-        fa[a] = pdf_load<L, ST>(f, a * N + n, a);
+        fa[a] = pdf_load<L, ST, RAW>(f, a * N + n, a);
     }
   }
 }
