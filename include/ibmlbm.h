@@ -69,7 +69,8 @@ typedef struct ibm_lbm_config {
   double gravity[3];      /* g acting on the particles (Eq. 14, weight less buoyancy)    */
   double zeta;            /* range of the repulsive force of Eq. 16                      */
   double eps_pp, E_pp;    /* stiffness parameters of Eq. 16 (E_pp < eps_pp)              */
-  int32_t fixed_particles;/* 1: particles keep centre and velocity (static bodies)       */
+  int32_t fixed_particles;/* 0: free; 1: particles keep centre, velocity and spin (static
+                             bodies); 2: centre and velocity held, the spin integrated  */
   int32_t max_neighbors;  /* capacity of each particle's contact list; 0 selects 32      */
   int32_t pdf_storage;    /* IBMLBM_PDF_FP32 (0), IBMLBM_PDF_FP16 (1), IBMLBM_PDF_BF16 (2):
                              element type of the stored PDFs.  FP16 and BF16 hold

@@ -834,8 +834,8 @@ static void move_particles(or_sim* S) {
       S->thp[3 * i + c] = Th[c];
       S->pint[3 * i + c] = Pn[c];
       S->lint[3 * i + c] = Ln[c];
-      if (P->fixed_particles) continue;
-      if (c < P->dim) {
+      if (P->fixed_particles == 1) continue;
+      if (c < P->dim && P->fixed_particles == 0) {
         double F = Fm + S->fc[3 * i + c] + dP + meff * P->gravity[c];
         double a = (F + Kt * S->acc[3 * i + c]) / (Mp + Kt);
         double u0 = S->uc[3 * i + c], u1 = u0 + a;

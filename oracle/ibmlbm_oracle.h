@@ -47,7 +47,8 @@ typedef struct or_params {
   double density_ratio;     /* rho_p / rho_f                                     */
   double gravity[3];        /* g acting on particles                             */
   double zeta, eps_pp, E_pp;/* Eq. 16 range and stiffness parameters             */
-  int32_t fixed_particles;  /* 1: particles keep their state (static bodies)     */
+  int32_t fixed_particles;  /* 1: particles keep their state (static bodies);
+                               2: centres and velocities held, rotation integrated */
   int32_t boundary;         /* 0: halfway bounce-back walls at -1/2, n - 1/2;
                                1: non-equilibrium extrapolation walls on the outermost
                                   nodes of every non-periodic axis;

@@ -131,6 +131,8 @@ int check_config(const ibm_lbm_config* c) {
       return fail(IBMLBM_ERR_INVALID_ARG, "density_ratio must be > 0");
     if (!(c->zeta > 0.0) || !(c->eps_pp > 0.0) || !(c->E_pp > 0.0))
       return fail(IBMLBM_ERR_INVALID_ARG, "zeta, eps_pp and E_pp must be > 0");
+    if (c->fixed_particles < 0 || c->fixed_particles > 2)
+      return fail(IBMLBM_ERR_INVALID_ARG, "fixed_particles must be 0, 1 or 2");
   }
   return IBMLBM_OK;
 }

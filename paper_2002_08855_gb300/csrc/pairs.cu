@@ -88,6 +88,7 @@ __device__ __forceinline__ double eq16_magnitude(const PairArgs& A, double d) {
 //   (M_p + K) a^n - K a^{n-1} = (F_h^n + F_h^{n-1})/2 + F_c + (P_int^n - P_int^{n-1})
 //                              + (M_p - rho_f V_p) g
 //   U^{n+1} = U^n + a^n, X^{n+1} = X^n + (U^n + U^{n+1})/2; rotation alike with I_p, K_r.
+// fixed = 1 holds the whole state, fixed = 2 holds centre and velocity but spins.
 // The K terms telescope, so momentum is conserved; they keep the explicit coupling
 // stable when the IB shell outweighs the particle.
 template <int D>
@@ -103,7 +104,7 @@ __device__ void advance_particle(const PairArgs& A, int i, const double* X, cons
     P.Fh[o] = fh;
     P.Pprev[o] = P.Pint[o];
     double x = X[c];
-    if (!P.fixed) {
+    if (P.fixed == 0) {
       const double F = Fm + Fc[c] + dP + P.meff * P.grav[c];
       const double a = (F + P.Kt * P.acc[o]) / (P.Mp + P.Kt);
       const double u0 = P.U[o], u1 = u0 + a;
@@ -132,7 +133,7 @@ __device__ void advance_particle(const PairArgs& A, int i, const double* X, cons
     const double dL = A.have_prev ? P.Lint[o] - P.Lprev[o] : 0.0;
     P.Th[o] = th;
     P.Lprev[o] = P.Lint[o];
-    if (!P.fixed) {
+    if (P.fixed != 1) {
       const double al = (Tm + dL + P.Kr * P.alp[o]) / (P.Ip + P.Kr);
       P.alp[o] = al;
       P.Om[o] += al;

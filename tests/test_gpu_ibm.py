@@ -147,3 +147,40 @@ def test_large_spheres_several_steps():
     _, uo = ref.get_fields()
     assert rel_l2(ug.cpu().numpy(), uo) < 1e-5
     sim.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_spin_in_a_shear_wave(dim):
+    """Centres held, spins integrated (fixed_particles = 2): bodies at the zero of a
+    shear wave u_x = U0 sin(k y) and one off it, so the torque, the rotational closure
+    (interior angular momentum, K_r) and Omega x r in the boundary velocity carry the
+    whole coupling; spin and field against the oracle."""
+    require_gpu()
+    if dim == 2:
+        L, D, steps = 96, 8.0, 150
+        w = Workload(name="spin", dim=2, nx=L, ny=L, periodic=(1, 1, 0), tau=1.0, n_particles=2,
+                     n_lag=25, diameter=D, density_ratio=1.0, fixed_particles=2)
+        xc = np.array([[30.3, 48.0], [70.6, 20.2]])
+    else:
+        L, D, steps = 36, 6.0, 60
+        w = Workload(name="spin3", dim=3, nx=L, ny=L, nz=L, periodic=(1, 1, 1), tau=1.0,
+                     n_particles=2, n_lag=113, diameter=D, density_ratio=1.0, fixed_particles=2)
+        xc = np.array([[9.3, 18.0, 17.8], [26.4, 8.1, 20.5]])
+    N = w.n_grid
+    y = (np.arange(N) // L) % L
+    u = np.zeros((dim, N))
+    u[0] = 1e-3 * np.sin(2 * np.pi * y / L)
+    sim, ref = _pair(w, xc, None)
+    sim.set_fields(np.zeros(N), u)
+    ref.set_fields(np.zeros(N), u)
+    sim.step(steps)
+    ref.step(steps)
+    pg, po = sim.get_particles(), ref.get_particles()
+    assert np.abs(po["Omega"]).max() > 1e-5
+    assert np.array_equal(pg["X"], xc) and np.abs(pg["U"]).max() == 0.0
+    assert rel_l2(pg["Omega"], po["Omega"]) < 1e-5
+    assert rel_l2(pg["T_h"], po["T_h"]) < 1e-4
+    _, ug = sim.get_fields()
+    _, uo = ref.get_fields()
+    assert rel_l2(ug.cpu().numpy(), uo) < 1e-5
+    sim.close()
