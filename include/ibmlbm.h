@@ -244,8 +244,9 @@ int ibm_lbm_pair_search(int32_t dim, const int32_t* n_nodes, const int32_t* peri
  * device array inside this library instead of caller-provided scratch, and the call
  * makes no cudaMalloc, cudaFree or other allocating call.  It is meant for callers
  * that cannot provide or allocate device scratch: code without access to a CUDA
- * allocator, code running while another thread captures a graph in global mode,
- * code that must not pay the implicit synchronisation of cudaMalloc/cudaFree.
+ * allocator (a plug-in handed only its input and output buffers), code that must not
+ * pay the implicit synchronisation of cudaMalloc/cudaFree.  It reads the pair count
+ * back and synchronises the stream, so the call itself cannot be captured.
  *   - A problem whose scratch (cells, per-particle lists) exceeds 16 MiB returns
  *     IBMLBM_ERR_CAPACITY and writes nothing; use ibm_lbm_pair_search for it.
  *   - Every GPU that loads the array keeps the 16 MiB until the process exits.
@@ -254,6 +255,7 @@ int ibm_lbm_pair_search(int32_t dim, const int32_t* n_nodes, const int32_t* peri
  *     that overlap on the GPU race on it.  Order them on one stream.
  *   - The first call on a device (with that device current) looks up the array's
  *     device address and caches it; make that first call before any stream capture.
+ *     After cudaDeviceReset the cached address is stale: reload the library first.
  * Synchronises the stream before returning. */
 int ibm_lbm_pair_search_static(int32_t dim, const int32_t* n_nodes, const int32_t* periodic,
                                double diameter, double zeta, int32_t n, const double* d_X,

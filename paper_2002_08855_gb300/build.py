@@ -16,7 +16,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libibmlbm.so")
 UNITS = ["lbm.cu", "ibm.cu", "pairs.cu", "api.cu", "pairs_static.cu", "mlp.cu"]
-HEADERS = ["common.cuh", "launch.h", "pdf_access.cuh", "mlp.h"]
+HEADERS = ["common.cuh", "launch.h", "pdf_access.cuh", "mlp.h", "pair_grid.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "-I" + os.path.join(ROOT, "include"), "-I" + SRC]

@@ -18,6 +18,7 @@
 #include "ibmlbm.h"
 #include "common.cuh"
 #include "launch.h"
+#include "pair_grid.h"
 #include "mlp.h"
 
 using namespace ibmlbm;
@@ -135,19 +136,6 @@ int check_config(const ibm_lbm_config* c) {
       return fail(IBMLBM_ERR_INVALID_ARG, "fixed_particles must be 0, 1 or 2");
   }
   return IBMLBM_OK;
-}
-
-void cell_grid(int D, const double* L, const int* per, double reach, int* nc, double* H) {
-  for (int k = 0; k < 3; ++k) {
-    nc[k] = 1;
-    H[k] = k < D ? L[k] : 1.0;
-    if (k >= D) continue;
-    int c = (int)std::floor(L[k] / reach);
-    if (c < 1) c = 1;
-    if (per[k] && c < 3) c = 1;
-    nc[k] = c;
-    H[k] = L[k] / c;
-  }
 }
 
 // Staging list of a 3D sphere's node box: the cells (lx | ly << 5 | lz << 10) that are
@@ -1281,25 +1269,6 @@ extern "C" {
 
 // ------------------------------------------------------ standalone pair search
 namespace {
-struct PairScratch {
-  size_t cell_count, cell_ids, nbr, nbr_count, gt, status, total;
-};
-
-PairScratch pair_scratch(int D, int n, int kmax, const int* nc) {
-  PairScratch p{};
-  Carver cv;
-  const size_t ncells = (size_t)nc[0] * nc[1] * nc[2];
-  (void)D;
-  p.cell_count = cv.take(sizeof(int) * ncells);
-  p.cell_ids = cv.take(sizeof(int) * ncells * cell_capacity(n, (long long)ncells));
-  p.nbr = cv.take(sizeof(int) * (size_t)n * kmax);
-  p.nbr_count = cv.take(sizeof(int) * (size_t)n);
-  p.gt = cv.take(sizeof(int) * 2 * ((size_t)n + 1));
-  p.status = cv.take(sizeof(uint32_t));
-  p.total = cv.off;
-  return p;
-}
-
 int pair_domain(int32_t dim, const int32_t* n_nodes, const int32_t* periodic, double diameter,
                 double zeta, int32_t n, int32_t max_neighbors, double* L, int* per, int* nc,
                 double* H, int* kmax) {
@@ -1329,7 +1298,9 @@ int ibm_lbm_pair_search_scratch_size(int32_t dim, const int32_t* n_nodes, double
   int rc = pair_domain(dim, n_nodes, nullptr, diameter, zeta, n, max_neighbors, L, per, nc, H, &kmax);
   if (rc) return rc;
   if (!bytes) return fail(IBMLBM_ERR_INVALID_ARG, "bytes is NULL");
-  *bytes = pair_scratch(dim, n, kmax, nc).total;
+  const PairScratch ps = pair_scratch(n, kmax, nc);
+  if (!ps.ok) return fail(IBMLBM_ERR_CAPACITY, "pair-search scratch size does not fit in size_t");
+  *bytes = ps.total;
   return IBMLBM_OK;
 }
 
@@ -1345,7 +1316,8 @@ int ibm_lbm_pair_search(int32_t dim, const int32_t* n_nodes, const int32_t* peri
   *h_count = 0;
   if (n == 0) return IBMLBM_OK;
   if (!d_X || (cap > 0 && !d_pairs)) return fail(IBMLBM_ERR_INVALID_ARG, "X or pairs is NULL");
-  const PairScratch ps = pair_scratch(dim, n, kmax, nc);
+  const PairScratch ps = pair_scratch(n, kmax, nc);
+  if (!ps.ok) return fail(IBMLBM_ERR_CAPACITY, "pair-search scratch size does not fit in size_t");
   if (!d_scratch || scratch_bytes < ps.total || reinterpret_cast<uintptr_t>(d_scratch) % kAlign)
     return fail(IBMLBM_ERR_WORKSPACE, "scratch missing, misaligned or too small");
   char* sc = static_cast<char*>(d_scratch);
@@ -1371,7 +1343,7 @@ int ibm_lbm_pair_search(int32_t dim, const int32_t* n_nodes, const int32_t* peri
   a.X = d_X;
   a.cell_count = reinterpret_cast<int*>(sc + ps.cell_count);
   a.cell_ids = reinterpret_cast<int*>(sc + ps.cell_ids);
-  a.cell_cap = cell_capacity(n, (long long)nc[0] * nc[1] * nc[2]);
+  a.cell_cap = ps.cell_cap;
   a.nbr = reinterpret_cast<int*>(sc + ps.nbr);
   a.nbr_count = reinterpret_cast<int*>(sc + ps.nbr_count);
   a.gt_count = reinterpret_cast<int*>(sc + ps.gt);

@@ -713,8 +713,10 @@ __global__ void __launch_bounds__(kMdf3Threads, 2) ibm_interp3_kernel(IbmArgs A,
 //   1. the table of weights (as in the interpolation) and dF_b dV of every point;
 //   2. spread into the sphere's box, accumulated as 32-bit fixed point with integer
 //      shared-memory atomics.  The scale of the sphere is 2^30 over (max |dF_b dV|
-//      times N_L times 1/8), a bound on any node's sum (every weight is at most 1/8),
-//      so no sum overflows and the rounding is that of single precision;
+//      times N_L times w_max), a bound on any node's sum (w_max, the largest product
+//      of three one-dimensional weights: phi(0)^3 = 1/8 for the 4-point delta, 8/27
+//      for the 3-point one), so no sum overflows; each addend is rounded to a step of
+//      1 / scale;
 //   3. add the non-zero box cells to f_IB with one vector atomic per cell.
 template <int SC>
 __global__ void __launch_bounds__(kMdf3Threads) ibm_spread3_kernel(IbmArgs A) {
@@ -758,7 +760,8 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_spread3_kernel(IbmArgs A) {
     if (!isfinite(gmax) && tid == 0) atomicOr(A.status, ST_NONFINITE);
     return;  // nothing to spread (the same decision in every thread of the block)
   }
-  const float scale = 1073741824.0f / (gmax * 0.125f * (float)A.nl);  // 2^30 / bound
+  const float wmax = A.delta_kind == 3 ? 8.0f / 27.0f : 0.125f;
+  const float scale = 1073741824.0f / (gmax * wmax * (float)A.nl);  // 2^30 / bound
   const float inv = 1.0f / scale;
 
   // 2. spreading, one point per warp: lane (sx, sy, zh) adds to the support nodes of

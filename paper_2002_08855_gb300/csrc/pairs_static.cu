@@ -2,11 +2,11 @@
 // fixed device array of this library instead of caller-provided scratch.
 //
 // It serves callers that cannot hand over device memory and must not allocate any:
-// code without access to a CUDA allocator (a plugin or callback inside a larger
-// application), code running while another thread captures a CUDA graph in global
-// mode (cudaMalloc is refused then), or code that must not pay the implicit device
-// synchronisation cudaMalloc/cudaFree may cause.  The caller still owns the inputs
-// (centres) and the output (pair list).
+// code without access to a CUDA allocator (a plug-in or callback inside a larger
+// application that is handed only its input and output buffers), or code that must
+// not pay the implicit device synchronisation cudaMalloc/cudaFree may cause.  The
+// caller still owns the inputs (centres) and the output (pair list).  The call reads
+// the pair count back and synchronises its stream, so it cannot itself be captured.
 //
 // Costs and rules of the shared array:
 //   - kStaticScratchBytes (16 MiB) of device memory is reserved on every GPU that
@@ -18,6 +18,8 @@
 //     status word are cleared on the caller's stream at the start of each call.
 //   - The first call on each device looks up the array's device address (with that
 //     device current) and caches it; make that first call before any stream capture.
+//     The cached address belongs to the device's context: after cudaDeviceReset the
+//     library must be loaded again before this entry point is used.
 #include <cstdint>
 #include <mutex>
 #include <string>
@@ -25,6 +27,7 @@
 #include "ibmlbm.h"
 #include "common.cuh"
 #include "launch.h"
+#include "pair_grid.h"
 
 using namespace ibmlbm;
 
@@ -32,7 +35,6 @@ namespace {
 
 constexpr size_t kStaticScratchBytes = 16u << 20;
 constexpr int kMaxDevices = 64;
-constexpr size_t kScratchAlign = 256;
 
 static __device__ __align__(256) unsigned char g_pair_scratch[kStaticScratchBytes];
 
@@ -62,12 +64,6 @@ int scratch_address(void** out) {
   return IBMLBM_OK;
 }
 
-size_t take(size_t& off, size_t bytes) {
-  const size_t o = off;
-  off = (off + (bytes ? bytes : 1) + kScratchAlign - 1) / kScratchAlign * kScratchAlign;
-  return o;
-}
-
 }  // namespace
 
 extern "C" int ibm_lbm_pair_search_static(int32_t dim, const int32_t* n_nodes, const int32_t* periodic,
@@ -84,36 +80,22 @@ extern "C" int ibm_lbm_pair_search_static(int32_t dim, const int32_t* n_nodes, c
   *h_count = 0;
   PairArgs a{};
   a.wall_lo = -0.5;
-  const double reach = diameter + zeta;
   for (int k = 0; k < 3; ++k) {
     if (k < dim && n_nodes[k] < 1) return static_fail(IBMLBM_ERR_INVALID_ARG, "n_nodes must be >= 1");
     a.L[k] = k < dim ? (double)n_nodes[k] : 1.0;
     a.g.per[k] = (k < dim && periodic) ? (periodic[k] ? 1 : 0) : 0;
-    int c = 1;
-    if (k < dim) {
-      c = (int)(a.L[k] / reach);
-      if (c < 1) c = 1;
-      if (a.g.per[k] && c < 3) c = 1;
-    }
-    a.nc[k] = c;
-    a.H[k] = a.L[k] / c;
   }
+  // the cells of ibm_lbm_pair_search and of a run (pair_grid.h)
+  cell_grid(dim, a.L, a.g.per, diameter + zeta, a.nc, a.H);
   if (n == 0) return IBMLBM_OK;
   if (!d_X || (cap > 0 && !d_pairs)) return static_fail(IBMLBM_ERR_INVALID_ARG, "X or pairs is NULL");
   const int kmax = max_neighbors ? max_neighbors : 32;
-  const size_t ncells = (size_t)a.nc[0] * a.nc[1] * a.nc[2];
-  size_t off = 0;
-  const size_t o_count = take(off, sizeof(int) * ncells);
-  const int cell_cap = cell_capacity(n, (long long)ncells);
-  const size_t o_ids = take(off, sizeof(int) * ncells * cell_cap);
-  const size_t o_nbr = take(off, sizeof(int) * (size_t)n * kmax);
-  const size_t o_ncnt = take(off, sizeof(int) * (size_t)n);
-  const size_t o_gt = take(off, sizeof(int) * 2 * ((size_t)n + 1));
-  const size_t o_status = take(off, sizeof(uint32_t));
-  if (off > kStaticScratchBytes)
+  const PairScratch ps = pair_scratch(n, kmax, a.nc);
+  if (!ps.ok || ps.total > kStaticScratchBytes)
     return static_fail(IBMLBM_ERR_CAPACITY,
-                       "problem needs " + std::to_string(off) + " bytes of scratch, above the fixed " +
-                           std::to_string(kStaticScratchBytes) + "; use ibm_lbm_pair_search");
+                       "problem needs " + (ps.ok ? std::to_string(ps.total) : std::string("more than 2^64")) +
+                           " bytes of scratch, above the fixed " + std::to_string(kStaticScratchBytes) +
+                           "; use ibm_lbm_pair_search");
   void* base = nullptr;
   int rc = scratch_address(&base);
   if (rc) return rc;
@@ -126,16 +108,16 @@ extern "C" int ibm_lbm_pair_search_static(int32_t dim, const int32_t* n_nodes, c
   a.n = n;
   a.diam = diameter;
   a.zeta = zeta;
-  a.thr2 = reach * reach;
+  a.thr2 = (diameter + zeta) * (diameter + zeta);
   a.kmax = kmax;
   a.X = d_X;
-  a.cell_count = reinterpret_cast<int*>(sc + o_count);
-  a.cell_ids = reinterpret_cast<int*>(sc + o_ids);
-  a.cell_cap = cell_capacity(n, (long long)ncells);
-  a.nbr = reinterpret_cast<int*>(sc + o_nbr);
-  a.nbr_count = reinterpret_cast<int*>(sc + o_ncnt);
-  a.gt_count = reinterpret_cast<int*>(sc + o_gt);
-  a.status = reinterpret_cast<uint32_t*>(sc + o_status);
+  a.cell_count = reinterpret_cast<int*>(sc + ps.cell_count);
+  a.cell_ids = reinterpret_cast<int*>(sc + ps.cell_ids);
+  a.cell_cap = ps.cell_cap;
+  a.nbr = reinterpret_cast<int*>(sc + ps.nbr);
+  a.nbr_count = reinterpret_cast<int*>(sc + ps.nbr_count);
+  a.gt_count = reinterpret_cast<int*>(sc + ps.gt);
+  a.status = reinterpret_cast<uint32_t*>(sc + ps.status);
   a.Fc = nullptr;
 #define STATIC_TRY(expr)                                                                      \
   do {                                                                                        \

@@ -88,6 +88,24 @@ def test_pair_scratch_size_host_only(lib):
     assert n.value > 42723 * 32 * 4
 
 
+def test_pair_search_sizes_stay_bounded_for_a_tiny_reach(lib):
+    """A diameter and range far below one node on a 2^15 x 2^15 lattice would ask for
+    2^60 cells: the cell grid merges cells down to 2^30 (a larger side keeps the search
+    complete), the scratch size is finite, and the allocation-free entry point rejects
+    the problem as too large for its fixed array before any device work (host only)."""
+    nodes = (C.c_int32 * 3)(1 << 15, 1 << 15, 1)
+    n = C.c_size_t(0)
+    assert lib.ibm_lbm_pair_search_scratch_size(2, nodes, 1e-9, 1e-9, 100, 0, C.byref(n)) == 0
+    assert (1 << 30) * 4 < n.value < (1 << 30) * 4 * 20
+    dummy = (C.c_double * 200)()
+    cnt = C.c_int64(-1)
+    per = (C.c_int32 * 3)(0, 0, 0)
+    rc = lib.ibm_lbm_pair_search_static(2, nodes, per, 1e-9, 1e-9, 100, C.cast(dummy, C.c_void_p),
+                                        0, None, 0, C.byref(cnt), None)
+    assert rc == -7 and cnt.value == 0
+    assert "16777216" in lib.ibm_lbm_last_error().decode()
+
+
 def _batch_sizes(ws):
     cfgs = (binding.Config * len(ws))(*[binding.make_config(w) for w in ws])
     n = C.c_size_t(0)

@@ -126,7 +126,7 @@ def test_cavity_3d_full_lattice_beyond_2_31_elements_streaming_bit_exact():
 
 def test_cavity_3d_full_lattice_beyond_2_31_elements_spheres():
     """The 384 x 384 x 768 cavity's own sphere positions (20000 spheres, d = 12, 452
-    points), keeping those in the top planes (about 1200), with seeded PDFs there and
+    points), keeping those in the top planes (975 of them), with seeded PDFs there and
     seeded sphere velocities and spins: four whole steps (MDF, collision, streaming,
     contacts, Newton-Euler update) against the oracle's sub-box."""
     torch = require_gpu()
@@ -137,7 +137,7 @@ def test_cavity_3d_full_lattice_beyond_2_31_elements_spheres():
     R = 0.5 * w3.diameter
     Xall = inputs.place_particles(w3)
     X = Xall[Xall[:, 2] >= z0 + R + 2 + k + 2]  # supports stay k + 2 planes above z0
-    assert len(X) > 1000
+    assert len(X) > 900
     U0, Om0 = _seeded_motion(len(X), 3, seed=3841, u=1e-3)
     w = w3.with_(n_particles=len(X))
     sim = Simulation(w, X)

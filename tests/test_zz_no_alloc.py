@@ -3,9 +3,12 @@
 ibm_lbm_pair_search_static keeps its cell and neighbour lists in a fixed device array
 inside the library, for callers that cannot provide or allocate device scratch.  It
 must return exactly the pair list of ibm_lbm_pair_search (pair lists are compared
-bit for bit), on two calls in a row, since every call reuses the same array."""
+bit for bit; that list is also checked against the oracle's brute-force list), on two
+calls in a row, since every call reuses the same array."""
 import numpy as np
 import pytest
+
+import oracle
 
 from paper_2002_08855_gb300 import inputs
 
@@ -25,6 +28,8 @@ def test_static_scratch_matches_caller_scratch_twice(dim, shape, per, n, seed):
     X = inputs.random_points(n, dim, [-0.5] * dim, [s - 0.5 - 1e-9 for s in shape[:dim]], seed)
     ref = pair_search(dim, shape, per, 10.0, 2.0, X, max_neighbors=64)
     assert len(ref) > 100
+    cfg = dict(dim=dim, nx=shape[0], ny=shape[1], nz=shape[2], periodic=per, diameter=10.0, zeta=2.0)
+    assert np.array_equal(ref, oracle.pairs_bruteforce(cfg, X))
     for _ in range(2):
         got = pair_search_static(dim, shape, per, 10.0, 2.0, X, max_neighbors=64)
         assert np.array_equal(got, ref)
