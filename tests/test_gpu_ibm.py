@@ -173,13 +173,17 @@ def test_spin_in_a_shear_wave(dim):
     sim, ref = _pair(w, xc, None)
     sim.set_fields(np.zeros(N), u)
     ref.set_fields(np.zeros(N), u)
-    sim.step(steps)
-    ref.step(steps)
+    # during spin-up the torque is large; near the torque-free state it is a nearly
+    # complete cancellation of the points' contributions, so it is compared early
+    sim.step(5)
+    ref.step(5)
+    assert rel_l2(sim.get_particles()["T_h"], ref.get_particles()["T_h"]) < 1e-4
+    sim.step(steps - 5)
+    ref.step(steps - 5)
     pg, po = sim.get_particles(), ref.get_particles()
     assert np.abs(po["Omega"]).max() > 1e-5
     assert np.array_equal(pg["X"], xc) and np.abs(pg["U"]).max() == 0.0
     assert rel_l2(pg["Omega"], po["Omega"]) < 1e-5
-    assert rel_l2(pg["T_h"], po["T_h"]) < 1e-4
     _, ug = sim.get_fields()
     _, uo = ref.get_fields()
     assert rel_l2(ug.cpu().numpy(), uo) < 1e-5
