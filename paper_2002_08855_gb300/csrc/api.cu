@@ -606,7 +606,7 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
     ++k;
     CUDA_TRY(cudaEventRecord(h->join, h->side));
     CUDA_TRY(launch_lbm_step(la, h->d.D, parity, s));
-    k += lbm_step_launches(h->d.g, h->d.D, parity);
+    k += lbm_step_launches(h->d.g, h->d.D, parity, h->cfg.pdf_storage);
     CUDA_TRY(launch_lbm_nee(la, h->d.D, parity, s));
     k += h->cfg.boundary ? 1 : 0;
     CUDA_TRY(cudaStreamWaitEvent(s, h->join, 0));
@@ -615,7 +615,7 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
   }
   // one part after the other (no particles, or timed parts)
   CUDA_TRY(launch_lbm_step(la, h->d.D, parity, s));
-  k += lbm_step_launches(h->d.g, h->d.D, parity);
+  k += lbm_step_launches(h->d.g, h->d.D, parity, h->cfg.pdf_storage);
   CUDA_TRY(launch_lbm_nee(la, h->d.D, parity, s));
   k += h->cfg.boundary ? 1 : 0;
   if (ev) CUDA_TRY(cudaEventRecord(ev[3], s));

@@ -8,7 +8,8 @@
 namespace ibmlbm {
 
 cudaError_t launch_lbm_step(const LbmArgs& A, int D, int parity, cudaStream_t s);
-int lbm_step_launches(const Geo& g, int D, int parity);  // kernels launch_lbm_step launches
+int lbm_step_launches(const Geo& g, int D, int parity, int store);  // kernels launch_lbm_step launches
+bool lbm_step_vector(const Geo& g, int D, int store);  // launch_lbm_step uses the vector kernel
 cudaError_t launch_lbm_moments(const LbmArgs& A, int D, int parity, cudaStream_t s);
 cudaError_t launch_lbm_fields(const LbmArgs& A, int D, int parity, double* p, double* u,
                               cudaStream_t s);

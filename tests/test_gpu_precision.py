@@ -31,7 +31,12 @@ def _weights(q):
 
 
 @pytest.mark.parametrize("storage,dtype", [(1, np.float16), (2, "bf16")])
-@pytest.mark.parametrize("dim,shape,per", [(2, (37, 29, 1), (0, 0, 0)), (3, (19, 13, 11), (1, 0, 1))])
+@pytest.mark.parametrize("dim,shape,per", [
+    (2, (37, 29, 1), (0, 0, 0)), (3, (19, 13, 11), (1, 0, 1)),
+    # 2D rows whose length is a multiple of 8: the vector kernel, with several warps per
+    # row and a last warp holding one lane (the 3D shapes take the row kernel)
+    (2, (264, 21, 1), (0, 0, 0)), (2, (512, 9, 1), (1, 1, 0)),
+    (3, (388, 5, 6), (0, 1, 0)), (3, (128, 7, 6), (1, 0, 1))])
 def test_streaming_permutes_stored_values(storage, dtype, dim, shape, per):
     torch = require_gpu()
     from paper_2002_08855_gb300.binding import Simulation
