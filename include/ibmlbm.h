@@ -49,6 +49,8 @@ extern "C" {
 #define IBMLBM_ERR_NONFINITE (-5)     /* NaN/Inf in a particle state (device check) */
 #define IBMLBM_ERR_OUT_OF_DOMAIN (-6) /* a particle centre left the fluid domain */
 #define IBMLBM_ERR_CAPACITY (-7)      /* a fixed-capacity list overflowed */
+#define IBMLBM_ERR_BOUNDS (-8)        /* bounds-checked build (libibmlbm_checked.so) only: a
+                                         kernel's index check failed; the access was skipped */
 
 /* Problem statement of one run (Sec. 2, Sec. 6.2 and Table 7 of the paper). */
 typedef struct ibm_lbm_config {

@@ -15,12 +15,13 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libibmlbm.so")
+LIB_CHECKED_PATH = os.path.join(_HERE, "_build", "libibmlbm_checked.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "ibmlbm.h")
 
 OK = 0
 ERRORS = {
     -1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "WORKSPACE", -4: "CUDA", -5: "NONFINITE",
-    -6: "OUT_OF_DOMAIN", -7: "CAPACITY",
+    -6: "OUT_OF_DOMAIN", -7: "CAPACITY", -8: "BOUNDS",
 }
 PARTS = ("macro", "ibm", "collide_stream", "pairs", "particles")
 
@@ -84,7 +85,7 @@ def make_config(w, max_neighbors: int = 0) -> Config:
 
 
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 _vp, _dp, _fp, _ip, _i64p = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_float), \
     C.POINTER(C.c_int32), C.POINTER(C.c_int64)
 SIGNATURES = {
@@ -142,26 +143,27 @@ SIGNATURES = {
 }
 
 
-def lib():
-    """Load the CUDA library; raise if it has not been built (there is no fallback)."""
-    global _lib
+def lib(checked: bool = False):
+    """Load the CUDA library (or its bounds-checked variant); raise if it has not been
+    built (there is no fallback)."""
+    path = LIB_CHECKED_PATH if checked else LIB_PATH
     with _lock:
-        if _lib is None:
-            if not os.path.exists(LIB_PATH):
-                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+        if path not in _libs:
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with "
                                    "paper_2002_08855_gb300.build.build() (there is no CPU path)")
-            L = C.CDLL(LIB_PATH)
+            L = C.CDLL(path)
             for name, (res, args) in SIGNATURES.items():
                 fn = getattr(L, name)
                 fn.restype = res
                 fn.argtypes = args
-            _lib = L
-    return _lib
+            _libs[path] = L
+    return _libs[path]
 
 
-def _check(rc: int, where: str):
+def _check(rc: int, where: str, L=None):
     if rc != OK:
-        raise IbmLbmError(rc, where, lib().ibm_lbm_last_error().decode())
+        raise IbmLbmError(rc, where, (L or lib()).ibm_lbm_last_error().decode())
 
 
 def _ptr(a, ctype):
@@ -192,10 +194,11 @@ class Simulation:
     """One run on one GPU: fluid cavity plus rigid particles (C ABI handle)."""
 
     def __init__(self, w, centres=None, device: str = "cuda", stream=None,
-                 max_neighbors: int = 0):
+                 max_neighbors: int = 0, checked: bool = False):
         import torch
 
         self.torch = torch
+        self.L = lib(checked)  # checked: the bounds-checked library
         self.cfg = make_config(w, max_neighbors)
         self.dim = self.cfg.dim
         self.q = 9 if self.dim == 2 else 19
@@ -213,26 +216,26 @@ class Simulation:
             if centres is None:
                 raise ValueError("particle centres are required")
             xc = np.ascontiguousarray(np.asarray(centres, dtype=np.float64).reshape(self.np, self.dim))
-        _check(lib().ibm_lbm_init(C.byref(self.cfg), C.c_void_p(self.workspace.data_ptr()),
+        _check(self.L.ibm_lbm_init(C.byref(self.cfg), C.c_void_p(self.workspace.data_ptr()),
                                   nbytes, C.c_void_p(self.stream.cuda_stream),
                                   _ptr(xc, C.c_double) if xc is not None else None,
-                                  C.byref(self.h)), "init")
+                                  C.byref(self.h)), "init", self.L)
 
     # ------------------------------------------------------------ stepping
     def step(self, n: int = 1):
-        _check(lib().ibm_lbm_step(self.h, int(n)), "step")
+        _check(self.L.ibm_lbm_step(self.h, int(n)), "step", self.L)
 
     def sync(self):
-        _check(lib().ibm_lbm_sync(self.h), "sync")
+        _check(self.L.ibm_lbm_sync(self.h), "sync", self.L)
 
     def time_parts(self, n: int) -> dict:
         ms = np.zeros(5)
-        _check(lib().ibm_lbm_time_parts(self.h, int(n), _ptr(ms, C.c_double)), "time_parts")
+        _check(self.L.ibm_lbm_time_parts(self.h, int(n), _ptr(ms, C.c_double)), "time_parts", self.L)
         return dict(zip(PARTS, ms.tolist()))
 
     def launch_count(self) -> int:
         v = C.c_int64(0)
-        _check(lib().ibm_lbm_get_launch_count(self.h, C.byref(v)), "launch_count")
+        _check(self.L.ibm_lbm_get_launch_count(self.h, C.byref(v)), "launch_count", self.L)
         return v.value
 
     # ------------------------------------------------------------ fields
@@ -242,13 +245,13 @@ class Simulation:
     def set_pdfs(self, f):
         t = self.torch.as_tensor(f, dtype=self.torch.float32, device=self.device).reshape(self.q, self.N).contiguous()
         self._wait_torch()
-        _check(lib().ibm_lbm_set_pdfs(self.h, C.c_void_p(t.data_ptr())), "set_pdfs")
+        _check(self.L.ibm_lbm_set_pdfs(self.h, C.c_void_p(t.data_ptr())), "set_pdfs", self.L)
         self.stream.synchronize()
 
     def get_pdfs(self):
         t = self.torch.empty((self.q, self.N), dtype=self.torch.float32, device=self.device)
         self._wait_torch()
-        _check(lib().ibm_lbm_get_pdfs(self.h, C.c_void_p(t.data_ptr())), "get_pdfs")
+        _check(self.L.ibm_lbm_get_pdfs(self.h, C.c_void_p(t.data_ptr())), "get_pdfs", self.L)
         self.stream.synchronize()
         return t
 
@@ -256,14 +259,14 @@ class Simulation:
         tp = self.torch.as_tensor(p, dtype=self.torch.float64, device=self.device).reshape(self.N).contiguous()
         tu = self.torch.as_tensor(u, dtype=self.torch.float64, device=self.device).reshape(self.dim, self.N).contiguous()
         self._wait_torch()
-        _check(lib().ibm_lbm_set_fields(self.h, C.c_void_p(tp.data_ptr()), C.c_void_p(tu.data_ptr())), "set_fields")
+        _check(self.L.ibm_lbm_set_fields(self.h, C.c_void_p(tp.data_ptr()), C.c_void_p(tu.data_ptr())), "set_fields", self.L)
         self.stream.synchronize()
 
     def get_fields(self):
         tp = self.torch.empty(self.N, dtype=self.torch.float64, device=self.device)
         tu = self.torch.empty((self.dim, self.N), dtype=self.torch.float64, device=self.device)
         self._wait_torch()
-        _check(lib().ibm_lbm_get_fields(self.h, C.c_void_p(tp.data_ptr()), C.c_void_p(tu.data_ptr())), "get_fields")
+        _check(self.L.ibm_lbm_get_fields(self.h, C.c_void_p(tp.data_ptr()), C.c_void_p(tu.data_ptr())), "get_fields", self.L)
         self.stream.synchronize()
         return tp, tu
 
@@ -277,34 +280,34 @@ class Simulation:
                 return None
             return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(self.np, cols))
         X, U, Om = arr(X, self.dim), arr(U, self.dim), arr(Omega, self._rot())
-        _check(lib().ibm_lbm_set_particles(
+        _check(self.L.ibm_lbm_set_particles(
             self.h, *[(_ptr(a, C.c_double) if a is not None else None) for a in (X, U, Om)]),
-            "set_particles")
+            "set_particles", self.L)
 
     def get_particles(self) -> dict:
         n, d, r = max(self.np, 1), self.dim, self._rot()
         out = dict(X=np.zeros((n, d)), U=np.zeros((n, d)), Omega=np.zeros((n, r)),
                    F_h=np.zeros((n, d)), T_h=np.zeros((n, r)), F_c=np.zeros((n, d)))
-        _check(lib().ibm_lbm_get_particles(self.h, *[_ptr(out[k], C.c_double) for k in
+        _check(self.L.ibm_lbm_get_particles(self.h, *[_ptr(out[k], C.c_double) for k in
                                                       ("X", "U", "Omega", "F_h", "T_h", "F_c")]),
-               "get_particles")
+               "get_particles", self.L)
         return {k: v[: self.np] for k, v in out.items()}
 
     def get_lagrangian(self) -> dict:
         m, d = max(self.np * self.nl, 1), self.dim
         Xb = np.zeros((m, d))
         Ub, Fb, us = (np.zeros((m, d), dtype=np.float32) for _ in range(3))
-        _check(lib().ibm_lbm_get_lagrangian(self.h, _ptr(Xb, C.c_double), _ptr(Ub, C.c_float),
+        _check(self.L.ibm_lbm_get_lagrangian(self.h, _ptr(Xb, C.c_double), _ptr(Ub, C.c_float),
                                             _ptr(Fb, C.c_float), _ptr(us, C.c_float)),
-               "get_lagrangian")
+               "get_lagrangian", self.L)
         k = self.np * self.nl
         return dict(X_b=Xb[:k], U_b=Ub[:k], F_b=Fb[:k], u_b_star=us[:k])
 
     def get_interior_momentum(self):
         n = max(self.np, 1)
         P, L = np.zeros((n, self.dim)), np.zeros((n, self._rot()))
-        _check(lib().ibm_lbm_get_interior_momentum(self.h, _ptr(P, C.c_double), _ptr(L, C.c_double)),
-               "get_interior_momentum")
+        _check(self.L.ibm_lbm_get_interior_momentum(self.h, _ptr(P, C.c_double), _ptr(L, C.c_double)),
+               "get_interior_momentum", self.L)
         return P[: self.np], L[: self.np]
 
     def get_pairs(self) -> np.ndarray:
@@ -312,19 +315,19 @@ class Simulation:
         cap = max(16, self.np * 8)
         while True:
             buf = np.zeros(2 * cap, dtype=np.int32)
-            rc = lib().ibm_lbm_get_pairs(self.h, _ptr(buf, C.c_int32), cap, C.byref(n))
+            rc = self.L.ibm_lbm_get_pairs(self.h, _ptr(buf, C.c_int32), cap, C.byref(n))
             if rc == -7 and n.value > cap:
                 cap = int(n.value)
                 continue
-            _check(rc, "get_pairs")
+            _check(rc, "get_pairs", self.L)
             return buf[: 2 * n.value].reshape(-1, 2)
 
     # ------------------------------------------------------------ learned initializer
     def set_mlp(self, params):
         p = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
-        if p.size != lib().ibm_lbm_mlp_param_count():
+        if p.size != self.L.ibm_lbm_mlp_param_count():
             raise ValueError("wrong number of parameters")
-        _check(lib().ibm_lbm_set_mlp(self.h, _ptr(p, C.c_float)), "set_mlp")
+        _check(self.L.ibm_lbm_set_mlp(self.h, _ptr(p, C.c_float)), "set_mlp", self.L)
 
     def mdf_samples(self):
         """(features [npts][27], targets [npts][3]) of the last step, as CUDA tensors."""
@@ -332,37 +335,37 @@ class Simulation:
         X = self.torch.empty((n, 27), dtype=self.torch.float32, device=self.device)
         Y = self.torch.empty((n, 3), dtype=self.torch.float32, device=self.device)
         self._wait_torch()
-        _check(lib().ibm_lbm_mdf_samples(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(Y.data_ptr())),
-               "mdf_samples")
+        _check(self.L.ibm_lbm_mdf_samples(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(Y.data_ptr())),
+               "mdf_samples", self.L)
         return X, Y
 
     def get_state(self) -> np.ndarray:
         """Checkpoint of the run (host bytes)."""
         n = C.c_size_t(0)
-        _check(lib().ibm_lbm_state_size(self.h, C.byref(n)), "state_size")
+        _check(self.L.ibm_lbm_state_size(self.h, C.byref(n)), "state_size", self.L)
         buf = np.zeros(n.value, dtype=np.uint8)
         self._wait_torch()
-        _check(lib().ibm_lbm_get_state(self.h, C.c_void_p(buf.ctypes.data), n.value), "get_state")
+        _check(self.L.ibm_lbm_get_state(self.h, C.c_void_p(buf.ctypes.data), n.value), "get_state", self.L)
         return buf
 
     def set_state(self, buf):
         """Resume from a checkpoint of a run of the same configuration."""
         b = np.ascontiguousarray(np.asarray(buf, dtype=np.uint8))
         self._wait_torch()
-        _check(lib().ibm_lbm_set_state(self.h, C.c_void_p(b.ctypes.data), b.size), "set_state")
+        _check(self.L.ibm_lbm_set_state(self.h, C.c_void_p(b.ctypes.data), b.size), "set_state", self.L)
 
     def set_residual_tracking(self, on: bool = True):
-        _check(lib().ibm_lbm_set_residual_tracking(self.h, int(bool(on))), "set_residual_tracking")
+        _check(self.L.ibm_lbm_set_residual_tracking(self.h, int(bool(on))), "set_residual_tracking", self.L)
 
     def mdf_residual(self):
         rms, mx = C.c_double(0), C.c_double(0)
-        _check(lib().ibm_lbm_get_mdf_residual(self.h, C.byref(rms), C.byref(mx)), "get_mdf_residual")
+        _check(self.L.ibm_lbm_get_mdf_residual(self.h, C.byref(rms), C.byref(mx)), "get_mdf_residual", self.L)
         return rms.value, mx.value
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:
             self.stream.synchronize()
-            lib().ibm_lbm_destroy(self.h)
+            self.L.ibm_lbm_destroy(self.h)
             self.h = C.c_void_p(None)
 
     def __del__(self):
@@ -378,6 +381,7 @@ class BatchMember(Simulation):
 
     def __init__(self, batch, i, w):
         self.torch = batch.torch
+        self.L = batch.L
         self.cfg = make_config(w)
         self.dim = self.cfg.dim
         self.q = 9 if self.dim == 2 else 19
@@ -386,9 +390,9 @@ class BatchMember(Simulation):
         self.nl = self.cfg.n_lag
         self.device = batch.device
         self.stream = batch.stream
-        ptr = lib().ibm_lbm_batch_member(batch.h, int(i))
+        ptr = self.L.ibm_lbm_batch_member(batch.h, int(i))
         if not ptr:
-            raise IbmLbmError(-1, "batch_member", lib().ibm_lbm_last_error().decode())
+            raise IbmLbmError(-1, "batch_member", self.L.ibm_lbm_last_error().decode())
         self.h = C.c_void_p(ptr)
 
     def step(self, n: int = 1):
@@ -418,12 +422,13 @@ class Batch:
         import torch
 
         self.torch = torch
+        self.L = lib()
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
         n = len(workloads)
         cfgs = (Config * n)(*[make_config(w) for w in workloads])
         size = C.c_size_t(0)
-        _check(lib().ibm_lbm_batch_workspace_size(cfgs, n, C.byref(size)), "batch_workspace_size")
+        _check(self.L.ibm_lbm_batch_workspace_size(cfgs, n, C.byref(size)), "batch_workspace_size", self.L)
         self.workspace = torch.empty(size.value, dtype=torch.uint8, device=self.device)
         self.stream.wait_stream(torch.cuda.current_stream(self.device))
         self._xc = []
@@ -434,35 +439,35 @@ class Batch:
                 self._xc.append(xc)
                 ptrs[i] = _ptr(xc, C.c_double)
         self.h = C.c_void_p(None)
-        _check(lib().ibm_lbm_batch_init(cfgs, n, C.c_void_p(self.workspace.data_ptr()), size.value,
+        _check(self.L.ibm_lbm_batch_init(cfgs, n, C.c_void_p(self.workspace.data_ptr()), size.value,
                                         C.c_void_p(self.stream.cuda_stream), ptrs, C.byref(self.h)),
-               "batch_init")
+               "batch_init", self.L)
         self.members = [BatchMember(self, i, w) for i, w in enumerate(workloads)]
         self.n_grid = sum(w.n_grid for w in workloads)
 
     def step(self, n: int = 1):
-        _check(lib().ibm_lbm_batch_step(self.h, int(n)), "batch_step")
+        _check(self.L.ibm_lbm_batch_step(self.h, int(n)), "batch_step", self.L)
 
     def sync(self):
-        _check(lib().ibm_lbm_batch_sync(self.h), "batch_sync")
+        _check(self.L.ibm_lbm_batch_sync(self.h), "batch_sync", self.L)
 
     def launch_count(self) -> int:
-        return int(lib().ibm_lbm_batch_launch_count(self.h))
+        return int(self.L.ibm_lbm_batch_launch_count(self.h))
 
     def set_tile_shape(self, shape: int):
-        _check(lib().ibm_lbm_batch_set_tile_shape(self.h, int(shape)), "batch_set_tile_shape")
+        _check(self.L.ibm_lbm_batch_set_tile_shape(self.h, int(shape)), "batch_set_tile_shape", self.L)
 
     def tile_shape(self) -> int:
         v = C.c_int32(0)
-        _check(lib().ibm_lbm_batch_get_tile_shape(self.h, C.byref(v)), "batch_get_tile_shape")
+        _check(self.L.ibm_lbm_batch_get_tile_shape(self.h, C.byref(v)), "batch_get_tile_shape", self.L)
         return v.value
 
     def autotune(self, steps_per_shape: int = 2) -> tuple:
         """Time every tile shape on steps_per_shape real steps; keep the fastest.
         Returns (chosen shape, mean ms per step of each shape's collide-stream launches)."""
-        ms = np.zeros(lib().ibm_lbm_tile_shape_count(), dtype=np.float32)
-        _check(lib().ibm_lbm_batch_autotune(self.h, int(steps_per_shape), _ptr(ms, C.c_float)),
-               "batch_autotune")
+        ms = np.zeros(self.L.ibm_lbm_tile_shape_count(), dtype=np.float32)
+        _check(self.L.ibm_lbm_batch_autotune(self.h, int(steps_per_shape), _ptr(ms, C.c_float)),
+               "batch_autotune", self.L)
         return self.tile_shape(), [float(v) for v in ms]
 
     def close(self):
@@ -470,7 +475,7 @@ class Batch:
             self.stream.synchronize()
             for m in self.members:
                 m.close()
-            lib().ibm_lbm_batch_destroy(self.h)
+            self.L.ibm_lbm_batch_destroy(self.h)
             self.h = C.c_void_p(None)
 
     def __del__(self):

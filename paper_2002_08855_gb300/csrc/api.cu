@@ -44,6 +44,21 @@ constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
+// Bounds-checked build: the first failed index check of any translation unit since
+// the last call, reported as IBMLBM_ERR_BOUNDS (the ordinary build has none).
+int report_check_faults() {
+  const unsigned long long f[3] = {check_fault_lbm(), check_fault_ibm(), check_fault_pairs()};
+  const char* unit[3] = {"lbm.cu", "ibm.cu", "pairs.cu"};
+  for (int k = 0; k < 3; ++k) {
+    if (!f[k]) continue;
+    char msg[160];
+    std::snprintf(msg, sizeof(msg), "index check failed in %s line %llu (index %llu)", unit[k],
+                  (f[k] >> 40) & 0x7fffffull, f[k] & 0xffffffffffull);
+    return fail(IBMLBM_ERR_BOUNDS, msg);
+  }
+  return IBMLBM_OK;
+}
+
 struct Carver {
   size_t off = 0;
   size_t take(size_t bytes) {
@@ -839,6 +854,8 @@ int ibm_lbm_sync(ibm_lbm_handle* h) {
   int rc = check_handle(h);
   if (rc) return rc;
   CUDA_TRY(cudaStreamSynchronize(h->s));
+  rc = report_check_faults();
+  if (rc) return rc;
   uint32_t st = 0;
   CUDA_TRY(cudaMemcpy(&st, h->at<uint32_t>(h->l.status), sizeof(st), cudaMemcpyDeviceToHost));
   if (st) {

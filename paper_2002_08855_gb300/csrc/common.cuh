@@ -24,6 +24,39 @@
 
 namespace ibmlbm {
 
+// ------------------------------------------------------------ bounds-checked build
+// Compiled with -DIBMLBM_CHECKED (libibmlbm_checked.so), every global index a kernel
+// forms from the geometry or from particle positions is checked against its array's
+// extent before the access; a failed check skips the access and records the source
+// line and the index in this translation unit's fault word (first failure wins), which
+// ibm_lbm_sync reports as IBMLBM_ERR_BOUNDS.  Nothing traps.  In the ordinary build
+// the checks compile to nothing.
+#ifdef IBMLBM_CHECKED
+static __device__ unsigned long long g_check_fault;
+__device__ __forceinline__ bool check_index(long long i, long long n, int line) {
+  if (i >= 0 && i < n) return true;
+  atomicCAS(&g_check_fault, 0ull,
+            (1ull << 63) | ((unsigned long long)(line & 0x7fffff) << 40) | ((unsigned long long)i & 0xffffffffffull));
+  return false;
+}
+#define IBMLBM_CHK(i, n) (::ibmlbm::check_index((long long)(i), (long long)(n), __LINE__))
+#else
+#define IBMLBM_CHK(i, n) true
+#endif
+
+// this translation unit's fault word, cleared after reading (0: no failure, or the
+// ordinary build)
+static inline unsigned long long take_check_fault() {
+#ifdef IBMLBM_CHECKED
+  unsigned long long v = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&v, g_check_fault, sizeof(v)) != cudaSuccess) return 0;
+  if (v) cudaMemcpyToSymbol(g_check_fault, &z, sizeof(z));
+  return v;
+#else
+  return 0;
+#endif
+}
+
 // device status word bits
 enum : uint32_t {
   ST_NONFINITE = 1u,

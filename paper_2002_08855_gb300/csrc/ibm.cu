@@ -219,7 +219,8 @@ __device__ __forceinline__ void interp2_body(const IbmArgs& A, int m, unsigned b
       const int r = t / S, c = t - r * S;
       int gx, gy;
       const bool ok = box_node(A.g, ox, oy, r, c, gx, gy);
-      cp_async8(aux + r * P + c, fib2 + (ok ? (long long)gx + (long long)A.g.nx * gy : 0), ok);
+      const long long n = ok ? (long long)gx + (long long)A.g.nx * gy : 0;
+      cp_async8(aux + r * P + c, fib2 + n, ok && IBMLBM_CHK(n, A.g.N));
     }
     cp_async_wait_all();
     __syncwarp();
@@ -396,7 +397,8 @@ __device__ __forceinline__ void spread2_body(const IbmArgs& A, unsigned blk) {
     int gx = ox + c, gy = oy + r;
     if (gx < 0 || gx >= A.g.nx) gx = ((gx % A.g.nx) + A.g.nx) % A.g.nx;  // only periodic
     if (gy < 0 || gy >= A.g.ny) gy = ((gy % A.g.ny) + A.g.ny) % A.g.ny;  // axes reach here
-    atomicAdd(fib2 + ((long long)gx + (long long)A.g.nx * gy), v);
+    const long long n = (long long)gx + (long long)A.g.nx * gy;
+    if (IBMLBM_CHK(n, A.g.N)) atomicAdd(fib2 + n, v);
   }
 }
 
@@ -531,6 +533,7 @@ __device__ __forceinline__ void stage3_from_list(const IbmArgs& A, float* box, i
       if (ex * ex + ey * ey + ez * ez > A.shell_hi2 || gx * gx + gy * gy + gz * gz < A.shell_lo2) continue;
       cell[u] = lx + Py * ly + Pz * lz;
       const long long n = n0 + box3_goff(A.g, lx, ly, lz);
+      if (!IBMLBM_CHK(n, A.g.N)) continue;
       v[u] = us4[n];
       if (MODE == 1) {
         const float4 f = fib4[n];
@@ -619,6 +622,7 @@ __global__ void __launch_bounds__(kMdf3Threads, 2) ibm_interp3_kernel(IbmArgs A,
       }
       if (!ok) continue;  // beyond a wall: zero
       const long long n = (long long)gx + (long long)nn[0] * ((long long)gy + (long long)nn[1] * gz);
+      if (!IBMLBM_CHK(n, A.g.N)) continue;
       v[u] = us4[n];
       if (MODE == 1) {
         const float4 f = fib4[n];
@@ -796,8 +800,9 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_spread3_kernel(IbmArgs A) {
       const int c = lx + Py * ly + Pz * lz;
       const int v0 = boxi[c], v1 = boxi[cells + c], v2 = boxi[2 * cells + c];
       if ((v0 | v1 | v2) == 0) continue;
-      atomicAdd(fib4 + n0 + box3_goff(A.g, lx, ly, lz),
-                make_float4((float)v0 * inv, (float)v1 * inv, (float)v2 * inv, 0.0f));
+      const long long n = n0 + box3_goff(A.g, lx, ly, lz);
+      if (IBMLBM_CHK(n, A.g.N))
+        atomicAdd(fib4 + n, make_float4((float)v0 * inv, (float)v1 * inv, (float)v2 * inv, 0.0f));
     }
     return;
   }
@@ -815,7 +820,7 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_spread3_kernel(IbmArgs A) {
     if (gy < 0 || gy >= nn[1]) gy = ((gy % nn[1]) + nn[1]) % nn[1];
     if (gz < 0 || gz >= nn[2]) gz = ((gz % nn[2]) + nn[2]) % nn[2];
     const long long n = (long long)gx + (long long)nn[0] * ((long long)gy + (long long)nn[1] * gz);
-    atomicAdd(fib4 + n, make_float4((float)v0 * inv, (float)v1 * inv, (float)v2 * inv, 0.0f));
+    if (IBMLBM_CHK(n, A.g.N)) atomicAdd(fib4 + n, make_float4((float)v0 * inv, (float)v1 * inv, (float)v2 * inv, 0.0f));
   }
 }
 
@@ -879,6 +884,7 @@ __global__ void __launch_bounds__(256) ibm_interp3g_kernel(IbmArgs A, int m) {
         const float w = wxy * S.wz[sz];
         if (gz < 0 || w == 0.0f) continue;
         const long long n = (long long)gx + (long long)A.g.nx * ((long long)gy + (long long)A.g.ny * gz);
+        if (!IBMLBM_CHK(n, A.g.N)) continue;
         float4 v = us4[n];
         if (MODE == 1) {
           const float4 f = fib4[n];
@@ -931,7 +937,7 @@ __global__ void __launch_bounds__(256) ibm_spread3g_kernel(IbmArgs A) {
     const float w = wxy * S.wz[sz];
     if (gz < 0 || w == 0.0f) continue;
     const long long n = (long long)gx + (long long)A.g.nx * ((long long)gy + (long long)A.g.ny * gz);
-    atomicAdd(fib4 + n, make_float4(w * f0, w * f1, w * f2, 0.0f));
+    if (IBMLBM_CHK(n, A.g.N)) atomicAdd(fib4 + n, make_float4(w * f0, w * f1, w * f2, 0.0f));
   }
 }
 
@@ -1074,6 +1080,7 @@ __global__ void __launch_bounds__(256) ibm_forces_kernel(IbmArgs A) {
     }
     if (!ok) continue;
     const long long nn = (long long)gc[0] + (long long)A.g.nx * ((long long)gc[1] + (long long)A.g.ny * gc[2]);
+    if (!IBMLBM_CHK(nn, A.g.N)) continue;
     const float4 us = reinterpret_cast<const float4*>(A.ustar)[nn];  // 3D: [N][4]
     const float4 fv = reinterpret_cast<const float4*>(A.fib)[nn];
     const float u[3] = {us.x + 0.5f * fv.x, us.y + 0.5f * fv.y, us.z + 0.5f * fv.z};
@@ -1144,6 +1151,7 @@ __device__ __forceinline__ void forces2_body(const IbmArgs& A, unsigned blk) {
       }
       const long long nn = (long long)gx + (long long)A.g.nx * gy;
       const int o = (cy + 2) * W + (cx + 2);  // the box starts two nodes before lox, loy
+      if (!IBMLBM_CHK(nn, A.g.N)) continue;
       const float2 us = ub[o], fv = fib2[nn];
       u0[q] = us.x + 0.5f * fv.x;
       u1[q] = us.y + 0.5f * fv.y;
@@ -1246,7 +1254,9 @@ __global__ void __launch_bounds__(256) regen_kernel(RegenArgs A0, int init, Fuse
     }
     const float h = sqrtf(rem);
     int x0 = an[0] + (int)ceilf(fr[0] - h), x1 = an[0] + (int)floorf(fr[0] + h);
-    uint32_t* row = A.mask + ((long long)gy + (long long)A.g.ny * gz) * A.g.wpr;
+    const long long ro = ((long long)gy + (long long)A.g.ny * gz) * A.g.wpr;
+    if (!IBMLBM_CHK(ro + A.g.wpr - 1, (long long)A.g.rows * A.g.wpr)) continue;
+    uint32_t* row = A.mask + ro;
     if (A.g.per[0] && (x0 < 0 || x1 >= A.g.nx)) {
       for (int x = x0; x <= x1; ++x) {
         const int wx = ((x % A.g.nx) + A.g.nx) % A.g.nx;
@@ -1440,4 +1450,8 @@ cudaError_t launch_regen_fused(const Fuse& F, unsigned blocks, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+}  // namespace ibmlbm
+
+namespace ibmlbm {
+unsigned long long check_fault_ibm() { return take_check_fault(); }
 }  // namespace ibmlbm

@@ -7,6 +7,11 @@
 
 namespace ibmlbm {
 
+// fault words of the bounds-checked build, per translation unit (0 in the ordinary build)
+unsigned long long check_fault_lbm();
+unsigned long long check_fault_ibm();
+unsigned long long check_fault_pairs();
+
 cudaError_t launch_lbm_step(const LbmArgs& A, int D, int parity, cudaStream_t s);
 int lbm_step_launches(const Geo& g, int D, int parity, int store);  // kernels launch_lbm_step launches
 bool lbm_step_vector(const Geo& g, int D, int store);  // launch_lbm_step uses the vector kernel

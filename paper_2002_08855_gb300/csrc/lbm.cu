@@ -27,15 +27,9 @@ __device__ __forceinline__ void put_pdfs(const Geo& g, void* __restrict__ f, int
   const long long N = g.Np;  // plane stride
 #pragma unroll
   for (int a = 0; a < L::Q; ++a) {
-    if (PARITY == 0 || a == 0) {
-      pdf_store<L, ST>(f, a * N + n, a, fa[a]);
-    } else {
-      long long src;
-      if (neighbour<L>(g, a, 1, x, y, z, n, src))
-        pdf_store<L, ST>(f, opp<L>(a) * N + src, a, fa[a]);
-      else
-        pdf_store<L, ST>(f, a * N + n, a, fa[a]);
-    }
+    long long idx = a * N + n, src;
+    if (PARITY == 1 && a != 0 && neighbour<L>(g, a, 1, x, y, z, n, src)) idx = opp<L>(a) * N + src;
+    if (IBMLBM_CHK(idx, L::Q * N)) pdf_store<L, ST>(f, idx, a, fa[a]);
   }
 }
 
@@ -47,19 +41,18 @@ __device__ __forceinline__ void store_post(const Geo& g, void* __restrict__ f, i
   const long long N = g.Np;  // plane stride
 #pragma unroll
   for (int a = 0; a < L::Q; ++a) {
+    long long idx;
     if (a == 0) {
-      pdf_store<L, ST, RAW>(f, n, 0, fa[0]);
+      idx = n;
     } else if (PARITY == 0) {
-      pdf_store<L, ST, RAW>(f, opp<L>(a) * N + n, a, fa[a]);
+      idx = opp<L>(a) * N + n;
     } else if (INNER) {
-      pdf_store<L, ST, RAW>(f, a * N + n + inner_offset<L>(g, a, -1), a, fa[a]);
+      idx = a * N + n + inner_offset<L>(g, a, -1);
     } else {
       long long dst;
-      if (neighbour<L>(g, a, -1, x, y, z, n, dst))
-        pdf_store<L, ST, RAW>(f, a * N + dst, a, fa[a]);
-      else
-        pdf_store<L, ST, RAW>(f, opp<L>(a) * N + n, a, fa[a]);
+      idx = neighbour<L>(g, a, -1, x, y, z, n, dst) ? a * N + dst : opp<L>(a) * N + n;
     }
+    if (IBMLBM_CHK(idx, L::Q * N)) pdf_store<L, ST, RAW>(f, idx, a, fa[a]);
   }
 }
 
@@ -260,11 +253,12 @@ __device__ __forceinline__ void ib_force(const LbmArgs& A, long long row, int x,
                                          float (&fv)[3]) {
   fv[0] = fv[1] = fv[2] = 0.0f;
   if (L::dim == 2) {
-    if (!A.fib) return;
+    if (!A.fib || !IBMLBM_CHK(n, A.g.N)) return;
     const float2 v = reinterpret_cast<const float2*>(A.fib)[n];
     fv[0] = v.x;
     fv[1] = v.y;
-  } else if ((A.mask[row * A.g.wpr + (x >> 5)] >> (x & 31)) & 1u) {
+  } else if (IBMLBM_CHK(row * A.g.wpr + (x >> 5), (long long)A.g.rows * A.g.wpr) &&
+             ((A.mask[row * A.g.wpr + (x >> 5)] >> (x & 31)) & 1u) && IBMLBM_CHK(n, A.g.N)) {
     const float4 v = reinterpret_cast<const float4*>(A.fib)[n];
     fv[0] = v.x;
     fv[1] = v.y;
@@ -548,7 +542,7 @@ __global__ void __launch_bounds__(32 * kVecWarps) lbm_step_vec_kernel(LbmArgs A,
   const int y = (int)(row - uz * (unsigned)g.ny), z = (int)uz;
   const int x0 = ((int)seg * 32 + lane) * K;
   const bool in = x0 < g.nx, first = x0 == 0, last = x0 + K == g.nx;
-  const long long n0 = (long long)x0 + (long long)g.nx * row, N = g.Np;
+  const long long n0 = (long long)x0 + (long long)g.nx * row, N = g.Np, QN = L::Q * N;
 
   // loads: the PDFs of the K nodes under the layout of this parity (zero on lanes past
   // the row end, which only take part in the shuffles).  Every load, the boundary
@@ -564,22 +558,26 @@ __global__ void __launch_bounds__(32 * kVecWarps) lbm_step_vec_kernel(LbmArgs A,
     edge[a] = 0u;
     shifted[a] = false;
     if (PARITY == 0 || a == 0) {
-      if (in) pvec_load<ST, K>(h[a], A.f, a * N + n0);
+      if (in && IBMLBM_CHK(a * N + n0 + K - 1, QN)) pvec_load<ST, K>(h[a], A.f, a * N + n0);
       continue;
     }
     const long long rs = nb_row<L>(g, a, -1, y, z);  // row of the source x - e_a
     if (rs < 0) {  // beyond a y / z wall: bounce-back, the node's own slot
-      if (in) pvec_load<ST, K>(h[a], A.f, a * N + n0);
+      if (in && IBMLBM_CHK(a * N + n0 + K - 1, QN)) pvec_load<ST, K>(h[a], A.f, a * N + n0);
       continue;
     }
     shifted[a] = true;
     const long long rb = opp<L>(a) * N + (long long)g.nx * rs, src = rb + x0;
-    if (in) pvec_load<ST, K>(h[a], A.f, src);
+    if (in && IBMLBM_CHK(src, QN) && IBMLBM_CHK(src + K - 1, QN)) pvec_load<ST, K>(h[a], A.f, src);
     const int ex = L::e(a, 0);
-    if (ex == 1 && in && (first || lane == 0))  // f_a of node x0 sits at x0 - 1
-      edge[a] = elem_load<ST>(A.f, !first ? src - 1 : g.per[0] ? rb + g.nx - 1 : a * N + n0);
-    if (ex == -1 && in && (last || lane == 31))  // f_a of node x0 + K - 1 sits at x0 + K
-      edge[a] = elem_load<ST>(A.f, !last ? src + K : g.per[0] ? rb : a * N + n0 + K - 1);
+    if (ex == 1 && in && (first || lane == 0)) {  // f_a of node x0 sits at x0 - 1
+      const long long e = !first ? src - 1 : g.per[0] ? rb + g.nx - 1 : a * N + n0;
+      if (IBMLBM_CHK(e, QN)) edge[a] = elem_load<ST>(A.f, e);
+    }
+    if (ex == -1 && in && (last || lane == 31)) {  // f_a of node x0 + K - 1 sits at x0 + K
+      const long long e = !last ? src + K : g.per[0] ? rb : a * N + n0 + K - 1;
+      if (IBMLBM_CHK(e, QN)) edge[a] = elem_load<ST>(A.f, e);
+    }
   }
   if (PARITY == 1) {
 #pragma unroll
@@ -603,7 +601,7 @@ __global__ void __launch_bounds__(32 * kVecWarps) lbm_step_vec_kernel(LbmArgs A,
 #pragma unroll
   for (int j = 0; j < K; ++j) fv[j][0] = fv[j][1] = fv[j][2] = 0.0f;
   if (L::dim == 2) {
-    if (A.fib && in) {
+    if (A.fib && in && IBMLBM_CHK(n0 + K - 1, g.N)) {
       const float4* fb = reinterpret_cast<const float4*>(A.fib) + (n0 >> 1);
 #pragma unroll
       for (int j = 0; j < K; j += 2) {
@@ -611,7 +609,7 @@ __global__ void __launch_bounds__(32 * kVecWarps) lbm_step_vec_kernel(LbmArgs A,
         fv[j][0] = t.x, fv[j][1] = t.y, fv[j + 1][0] = t.z, fv[j + 1][1] = t.w;
       }
     }
-  } else if (in) {
+  } else if (in && IBMLBM_CHK(row * g.wpr + (x0 >> 5), (long long)g.rows * g.wpr) && IBMLBM_CHK(n0 + K - 1, g.N)) {
     const uint32_t bits = (A.mask[row * g.wpr + (x0 >> 5)] >> (x0 & 31)) & ((1u << K) - 1);
     if (bits) {
 #pragma unroll
@@ -651,51 +649,44 @@ __global__ void __launch_bounds__(32 * kVecWarps) lbm_step_vec_kernel(LbmArgs A,
 #pragma unroll
   for (int a = 0; a < L::Q; ++a) {
     if (PARITY == 0 || a == 0) {  // even step: f*_a to a[opp(a)][x] (local)
-      if (in) pvec_store<ST, K>(h[a], A.f, opp<L>(a) * N + n0);
+      if (in && IBMLBM_CHK(opp<L>(a) * N + n0 + K - 1, QN)) pvec_store<ST, K>(h[a], A.f, opp<L>(a) * N + n0);
       continue;
     }
     const long long rt = nb_row<L>(g, a, 1, y, z);  // row of the target x + e_a
     if (rt < 0) {  // beyond a y / z wall: bounce-back into a[opp(a)][x]
-      if (in) pvec_store<ST, K>(h[a], A.f, opp<L>(a) * N + n0);
+      if (in && IBMLBM_CHK(opp<L>(a) * N + n0 + K - 1, QN)) pvec_store<ST, K>(h[a], A.f, opp<L>(a) * N + n0);
       continue;
     }
     const long long rb = a * N + (long long)g.nx * rt, dst = rb + x0;
+    const bool ok = in && IBMLBM_CHK(dst, QN) && IBMLBM_CHK(dst + K - 1, QN);  // (shuffles stay warp-wide)
     const int ex = L::e(a, 0);
     if (ex == 0) {
-      if (in) pvec_store<ST, K>(h[a], A.f, dst);
+      if (ok) pvec_store<ST, K>(h[a], A.f, dst);
     } else if (ex == 1) {  // f*_a(x) goes to x + 1: element j holds node j - 1
       const uint32_t lw = __shfl_up_sync(FULL, h[a].w[NW - 1], 1);
       const V sh = pvec_up<ST, K>(h[a], B2 ? (lw >> 16) : lw);
-      if (in) {
+      if (ok) {
         if (lane == 0) pvec_store_skip<ST, K>(sh, A.f, dst, true);
         else pvec_store<ST, K>(sh, A.f, dst);
         const uint32_t mine = pvec_get<ST, K>(h[a], K - 1);  // node x0 + K - 1
-        if (last) {
-          if (g.per[0]) elem_store<ST>(A.f, rb, mine);
-          else elem_store<ST>(A.f, opp<L>(a) * N + n0 + K - 1, mine);
-        } else if (lane == 31) {
-          elem_store<ST>(A.f, dst + K, mine);
-        }
+        const long long e = last ? (g.per[0] ? rb : opp<L>(a) * N + n0 + K - 1) : dst + K;
+        if ((last || lane == 31) && IBMLBM_CHK(e, QN)) elem_store<ST>(A.f, e, mine);
       }
     } else {  // f*_a(x) goes to x - 1: element j holds node j + 1
       const uint32_t fw = __shfl_down_sync(FULL, h[a].w[0], 1);
       const V sh = pvec_down<ST, K>(h[a], B2 ? (fw & 0xffffu) : fw);
-      if (in) {
+      if (ok) {
         if (lane == 31 || last) pvec_store_skip<ST, K>(sh, A.f, dst, false);
         else pvec_store<ST, K>(sh, A.f, dst);
         const uint32_t mine = pvec_get<ST, K>(h[a], 0);  // node x0
-        if (first) {
-          if (g.per[0]) elem_store<ST>(A.f, rb + g.nx - 1, mine);
-          else elem_store<ST>(A.f, opp<L>(a) * N + n0, mine);
-        } else if (lane == 0) {
-          elem_store<ST>(A.f, dst - 1, mine);
-        }
+        const long long e = first ? (g.per[0] ? rb + g.nx - 1 : opp<L>(a) * N + n0) : dst - 1;
+        if ((first || lane == 0) && IBMLBM_CHK(e, QN)) elem_store<ST>(A.f, e, mine);
       }
     }
   }
 
   // the IB force is cleared where it was not zero
-  if (!in) return;
+  if (!in || !IBMLBM_CHK(n0 + K - 1, g.N)) return;
   if (L::dim == 2) {
     if (A.fib) {
       float4* fb = reinterpret_cast<float4*>(A.fib) + (n0 >> 1);
@@ -908,6 +899,7 @@ __global__ void __launch_bounds__(kMomBlock) lbm_moments_kernel(LbmArgs A) {
   const unsigned nx = (unsigned)A.g.nx;
   const unsigned row = (unsigned)(n / nx);
   const int x = (int)(n - (long long)row * nx);
+  if (!IBMLBM_CHK((long long)row * A.g.wpr + (x >> 5), (long long)A.g.rows * A.g.wpr)) return;
   const uint32_t word = A.mask[(long long)row * A.g.wpr + (x >> 5)];
   if (!((word >> (x & 31)) & 1u)) return;
   const unsigned uny = (unsigned)A.g.ny;
@@ -1264,4 +1256,8 @@ cudaError_t launch_lbm_equilibrium(const LbmArgs& A, int D, int parity, const do
   return cudaGetLastError();
 }
 
+}  // namespace ibmlbm
+
+namespace ibmlbm {
+unsigned long long check_fault_lbm() { return take_check_fault(); }
 }  // namespace ibmlbm

@@ -43,6 +43,7 @@ __global__ void pair_insert_kernel(PairArgs A0, Fuse FU) {
   const int i = (int)(blk * blockDim.x + threadIdx.x);
   if (i >= A.n) return;
   const int c = cell_of<D>(A, i);
+  if (!IBMLBM_CHK(c, (long long)A.nc[0] * A.nc[1] * A.nc[2])) return;
   const int slot = atomicAdd(&A.cell_count[c], 1);
   if (slot < A.cell_cap)
     A.cell_ids[(long long)c * A.cell_cap + slot] = i;
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(256) pair_search_kernel(PairArgs A0, Fuse FU) 
       cell += stride * c;
       stride *= A.nc[k];
     }
-    if (ok) cnt_c = min(A.cell_count[cell], A.cell_cap);
+    if (ok && IBMLBM_CHK(cell, (long long)A.nc[0] * A.nc[1] * A.nc[2])) cnt_c = min(A.cell_count[cell], A.cell_cap);
   }
   int incl = cnt_c;
 #pragma unroll
@@ -549,4 +550,8 @@ cudaError_t launch_pair_compact(const PairArgs& A, int* pairs, long long cap, cu
   return cudaGetLastError();
 }
 
+}  // namespace ibmlbm
+
+namespace ibmlbm {
+unsigned long long check_fault_pairs() { return take_check_fault(); }
 }  // namespace ibmlbm

@@ -111,17 +111,23 @@ __device__ __forceinline__ void load_pdfs(const Geo& g, const void* __restrict__
   const long long N = g.Np;  // plane stride
 #pragma unroll
   for (int a = 0; a < L::Q; ++a) {
+    long long idx;
+    int s = a;  // direction whose slot is read
     if (PARITY == 0 || a == 0) {
-      fa[a] = pdf_load<L, ST, RAW>(f, a * N + n, a);
+      idx = a * N + n;
     } else if (INNER) {
-      fa[a] = pdf_load<L, ST, RAW>(f, opp<L>(a) * N + n + inner_offset<L>(g, a, 1), opp<L>(a));
+      idx = opp<L>(a) * N + n + inner_offset<L>(g, a, 1);
+      s = opp<L>(a);
     } else {
       long long src;
-      if (neighbour<L>(g, a, 1, x, y, z, n, src))
-        fa[a] = pdf_load<L, ST, RAW>(f, opp<L>(a) * N + src, opp<L>(a));
-      else
-        fa[a] = pdf_load<L, ST, RAW>(f, a * N + n, a);
+      if (neighbour<L>(g, a, 1, x, y, z, n, src)) {
+        idx = opp<L>(a) * N + src;
+        s = opp<L>(a);
+      } else {
+        idx = a * N + n;
+      }
     }
+    fa[a] = IBMLBM_CHK(idx, L::Q * N) ? pdf_load<L, ST, RAW>(f, idx, s) : 0.0f;
   }
 }
 

@@ -30,6 +30,14 @@ def test_every_declared_function_is_exported(lib):
     assert sorted(binding.SIGNATURES) == names
 
 
+def test_bounds_checked_library_exports_the_same_calls(lib):
+    build.build(checked=True)
+    L = binding.lib(checked=True)
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    assert L is not lib
+
+
 def test_config_struct_matches_header(lib):
     text = open(binding.HEADER).read()
     body = text[text.index("typedef struct ibm_lbm_config"):text.index("} ibm_lbm_config;")]
