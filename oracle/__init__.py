@@ -23,21 +23,25 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ibmlbm_oracle.c")
 _HDR = os.path.join(_HERE, "ibmlbm_oracle.h")
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_OUT_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_build/liboracle.so`` (no fused multiply-add)."""
-    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (no fused multiply-add);
+    omp: the same source with -fopenmp (``liboracle_omp.so``), whose parallel loops
+    write disjoint data, so it gives the same bits on all host cores."""
+    out = _OUT_OMP if omp else _OUT
+    os.makedirs(os.path.dirname(out), exist_ok=True)
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
-    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < newest:
-        tmp = _OUT + f".{os.getpid()}.tmp"
+    if force or not os.path.exists(out) or os.path.getmtime(out) < newest:
+        tmp = out + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-o", tmp, _SRC, "-lm"]
+               *(["-fopenmp"] if omp else []), "-shared", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _OUT)
-    return _OUT
+        os.replace(tmp, out)
+    return out
 
 
 class Params(C.Structure):
@@ -92,12 +96,11 @@ _ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _PP = C.POINTER(Params)
 
 
-def lib():
-    """Load (building first if needed) the oracle shared library."""
-    global _lib
+def lib(omp: bool = False):
+    """Load (building first if needed) the oracle shared library (omp: the OpenMP build)."""
     with _lock:
-        if _lib is None:
-            L = C.CDLL(build())
+        if omp not in _libs:
+            L = C.CDLL(build(omp=omp))
             sig = {
                 "or_lattice": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), _ip, _dp]),
                 "or_feq": (None, [C.c_int32, C.c_double, _dp, _dp]),
@@ -130,8 +133,8 @@ def lib():
                 fn = getattr(L, name)
                 fn.restype = res
                 fn.argtypes = args
-            _lib = L
-    return _lib
+            _libs[omp] = L
+    return _libs[omp]
 
 
 def _vec3(a, n=None):
@@ -272,7 +275,8 @@ def contact_forces(cfg, X) -> np.ndarray:
 class Sim:
     """The oracle's time stepper (macro -> MDF -> collide -> stream -> pairs -> update)."""
 
-    def __init__(self, cfg, xc=None):
+    def __init__(self, cfg, xc=None, omp: bool = False):
+        self.L = lib(omp)  # omp: the same oracle on all host cores (identical bits)
         self.P = make_params(cfg)
         self.dim = self.P.dim
         self.q = 9 if self.dim == 2 else 19
@@ -281,46 +285,46 @@ class Sim:
         self.nl = self.P.n_lag
         xc3 = _vec3(xc) if (xc is not None and self.np > 0) else np.zeros((max(self.np, 1), 3))
         self._xc = xc3
-        self.h = lib().or_create(C.byref(self.P), xc3.ctypes.data_as(C.c_void_p))
+        self.h = self.L.or_create(C.byref(self.P), xc3.ctypes.data_as(C.c_void_p))
         if not self.h:
             raise MemoryError("oracle allocation failed")
 
     def close(self):
         if getattr(self, "h", None):
-            lib().or_destroy(self.h)
+            self.L.or_destroy(self.h)
             self.h = None
 
     def __del__(self):
         self.close()
 
     def step(self, n: int = 1):
-        lib().or_step(self.h, int(n))
+        self.L.or_step(self.h, int(n))
 
     def get_pdfs(self) -> np.ndarray:
         f = np.zeros((self.q, self.N))
-        lib().or_get_pdfs(self.h, f.reshape(-1))
+        self.L.or_get_pdfs(self.h, f.reshape(-1))
         return f
 
     def set_pdfs(self, f):
-        lib().or_set_pdfs(self.h, np.ascontiguousarray(f, dtype=np.float64).reshape(-1))
+        self.L.or_set_pdfs(self.h, np.ascontiguousarray(f, dtype=np.float64).reshape(-1))
 
     def set_fields(self, p, u):
         u3 = np.zeros((3, self.N))
         u = np.asarray(u, dtype=np.float64).reshape(-1, self.N)
         u3[: u.shape[0]] = u
-        lib().or_set_fields(self.h, np.ascontiguousarray(p, dtype=np.float64).reshape(-1),
+        self.L.or_set_fields(self.h, np.ascontiguousarray(p, dtype=np.float64).reshape(-1),
                             u3.reshape(-1))
 
     def get_fields(self):
         p = np.zeros(self.N)
         u = np.zeros((3, self.N))
-        lib().or_get_fields(self.h, p, u.reshape(-1))
+        self.L.or_get_fields(self.h, p, u.reshape(-1))
         return p, u[: self.dim]
 
     def get_particles(self):
         n = max(self.np, 1)
         arrs = [np.zeros((n, 3)) for _ in range(6)]
-        lib().or_get_particles(self.h, *[a.reshape(-1) for a in arrs])
+        self.L.or_get_particles(self.h, *[a.reshape(-1) for a in arrs])
         X, U, Om, Fh, Th, Fc = [a[: self.np] for a in arrs]
         d = self.dim
         om = Om[:, 2:3] if d == 2 else Om
@@ -338,12 +342,12 @@ class Sim:
                 Om3[:, 2] = om[:, 0]
             else:
                 Om3[:] = om
-        lib().or_set_particles(self.h, X3.reshape(-1), U3.reshape(-1), Om3.reshape(-1))
+        self.L.or_set_particles(self.h, X3.reshape(-1), U3.reshape(-1), Om3.reshape(-1))
 
     def get_lagrangian(self):
         n = max(self.np * self.nl, 1)
         arrs = [np.zeros((n, 3)) for _ in range(4)]
-        lib().or_get_lagrangian(self.h, *[a.reshape(-1) for a in arrs])
+        self.L.or_get_lagrangian(self.h, *[a.reshape(-1) for a in arrs])
         d = self.dim
         m = self.np * self.nl
         Xb, Ub, Fb, us = [a[:m, :d] for a in arrs]
@@ -352,10 +356,10 @@ class Sim:
     def get_interior_momentum(self):
         n = max(self.np, 1)
         P, L = np.zeros((n, 3)), np.zeros((n, 3))
-        lib().or_get_interior_momentum(self.h, P.reshape(-1), L.reshape(-1))
+        self.L.or_get_interior_momentum(self.h, P.reshape(-1), L.reshape(-1))
         return P[: self.np, : self.dim], (L[: self.np, 2:3] if self.dim == 2 else L[: self.np])
 
     def get_mdf_residual(self):
         r, m = C.c_double(0.0), C.c_double(0.0)
-        lib().or_get_mdf_residual(self.h, C.byref(r), C.byref(m))
+        self.L.or_get_mdf_residual(self.h, C.byref(r), C.byref(m))
         return r.value, m.value

@@ -228,6 +228,7 @@ void or_stream_push(int32_t dim, int32_t nx, int32_t ny, int32_t nz, const int32
   long N = (long)nx * ny * nz;
   int x, y, z, a;
   lattice_init(dim, &L);
+#pragma omp parallel for collapse(2) private(x, a)
   for (z = 0; z < nz; ++z)
     for (y = 0; y < ny; ++y)
       for (x = 0; x < nx; ++x) {
@@ -312,6 +313,7 @@ static int axis_support(int kind, double X, int n, int periodic, int* idx, doubl
 void or_interp(const or_params* P, const double* g, int64_t npts, const double* X, double* ub) {
   long N = (long)P->nx * P->ny * P->nz;
   int64_t b;
+#pragma omp parallel for
   for (b = 0; b < npts; ++b) {
     int ix[4], iy[4], iz[4], cx, cy, cz, i, j, k, c;
     double wx[4], wy[4], wz[4];
@@ -677,6 +679,7 @@ static void lagrangian_points(or_sim* S) {
 static void compute_ustar(or_sim* S) {
   long n;
   int a, k;
+#pragma omp parallel for private(a, k)
   for (n = 0; n < S->N; ++n) {
     double u[3] = {0.0, 0.0, 0.0};
     for (a = 0; a < S->L.q; ++a)
@@ -706,6 +709,7 @@ static void ibm_mdf(or_sim* S) {
       }
     memset(S->dfib, 0, vbytes);
     or_spread(&S->P, S->npts, S->xb, S->dfb, S->dV, S->dfib);
+#pragma omp parallel for
     for (n = 0; n < 3 * S->N; ++n) {
       S->fib[n] += S->dfib[n];
       S->um[n] += S->dfib[n] / (2.0 * RHO0);
@@ -730,6 +734,7 @@ static void ibm_mdf(or_sim* S) {
 static void collide(or_sim* S) {
   long n;
   int a, k;
+#pragma omp parallel for private(a, k)
   for (n = 0; n < S->N; ++n) {
     double fn[19], feq[19], Fa[19], F[3], us[3], u[3], p;
     for (a = 0; a < S->L.q; ++a) fn[a] = S->f[(long)a * S->N + n];
@@ -807,6 +812,7 @@ static void move_particles(or_sim* S) {
   double Kr = Kt * R * R * (P->dim == 2 ? 1.0 : 2.0 / 3.0);
   int i, k, c;
   or_contact_forces(P, S->np, S->xc, S->fc);
+#pragma omp parallel for private(k, c)
   for (i = 0; i < S->np; ++i) {
     double Fh[3] = {0, 0, 0}, Th[3] = {0, 0, 0}, Pn[3], Ln[3];
     for (k = 0; k < S->nl; ++k) {
@@ -859,6 +865,7 @@ static void extrapolation_boundaries(or_sim* S) {
   const or_params* P = &S->P;
   const int n[3] = {P->nx, P->ny, P->nz};
   int x, y, z, k, a;
+#pragma omp parallel for collapse(2) private(x, k, a)
   for (z = 0; z < n[2]; ++z)
     for (y = 0; y < n[1]; ++y)
       for (x = 0; x < n[0]; ++x) {

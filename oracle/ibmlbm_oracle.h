@@ -18,6 +18,10 @@
  *   - Sec. 2.3, Eq. 14-16 Newton-Euler particle motion and pair force
  * Readings where the paper is silent or garbled are listed at each function.
  *
+ * Built with -fopenmp (liboracle_omp.so) the loops over nodes, points and particles
+ * whose iterations write disjoint data run on all host cores; nothing is summed
+ * across iterations, so both builds give identical bits.
+ *
  * Units: dh = dt = c = 1, cs^2 = 1/3, rho_0 = rho_f = 1 (lattice units).
  * Node (x, y, z) has integer coordinates 0..n-1 on each axis; node index
  * n = x + nx*(y + ny*z).  PDF arrays are [q][N]; vector fields are [3][N]
