@@ -69,6 +69,33 @@ def test_headline_cavity_2048x4096_four_steps():
     sim.close()
 
 
+def test_headline_cavity_2048x4096_fp16_storage_four_steps():
+    """The same four steps with FP16 storage (h = f / w, the chosen form's storage; the
+    vector lbm_step kernel): velocity and displacement within the storage's stated
+    error, the Lagrangian forces within the same bound."""
+    require_gpu()
+    from paper_2002_08855_gb300.binding import Simulation
+
+    w = inputs.cavity_2d_large(0.1)
+    X0 = inputs.place_particles(w)
+    U0, Om0 = _seeded_motion(len(X0), 2, seed=2048)
+    sim = Simulation(w.with_(pdf_storage=1), X0)
+    sim.set_particles(X0, U=U0, Omega=Om0)
+    ref = oracle.Sim(w.as_dict(), X0)
+    ref.set_particles(X0, U=U0, Omega=Om0)
+    sim.step(4)
+    ref.step(4)
+    _, ug = sim.get_fields()
+    _, uo = ref.get_fields()
+    pg, po = sim.get_particles(), ref.get_particles()
+    lg, lo = sim.get_lagrangian(), ref.get_lagrangian()
+    e = dict(u=rel_l2(ug.cpu().numpy(), uo), dX=rel_l2(pg["X"] - X0, po["X"] - X0),
+             F_b=rel_l2(lg["F_b"], lo["F_b"]), F_h=rel_l2(pg["F_h"], po["F_h"]))
+    print("FP16 storage, relative L2 against the oracle:", {k: f"{v:.2e}" for k, v in e.items()})
+    assert e["u"] < 2e-3 and e["dX"] < 2e-3 and e["F_b"] < 2e-3 and e["F_h"] < 2e-3
+    sim.close()
+
+
 NX, NY, NZ = 384, 384, 768
 PLANE = NX * NY
 
