@@ -51,6 +51,8 @@ extern "C" {
 #define IBMLBM_ERR_CAPACITY (-7)      /* a fixed-capacity list overflowed */
 #define IBMLBM_ERR_BOUNDS (-8)        /* bounds-checked build (libibmlbm_checked.so) only: a
                                          kernel's index check failed; the access was skipped */
+#define IBMLBM_ERR_TIMEOUT (-9)       /* a grid barrier of a persistent batch kernel gave up
+                                         waiting; its kernel returned early */
 
 /* Problem statement of one run (Sec. 2, Sec. 6.2 and Table 7 of the paper). */
 typedef struct ibm_lbm_config {
@@ -351,8 +353,30 @@ int ibm_lbm_batch_init(const ibm_lbm_config* cfgs, int32_t n, void* d_workspace,
 /* Enqueue n_steps steps of every member; returns after enqueueing. */
 int ibm_lbm_batch_step(ibm_lbm_batch* b, int32_t n_steps);
 
-/* Wait for the stream and report the first member status (as ibm_lbm_sync). */
+/* Wait for the stream and report the first member status (as ibm_lbm_sync), or
+ * IBMLBM_ERR_TIMEOUT when a grid barrier of the persistent mode gave up (the steps from
+ * that one on are not valid; the barriers are reset and the batch can be stepped again
+ * after new states are set).  Clears every status it reports. */
 int ibm_lbm_batch_sync(ibm_lbm_batch* b);
+
+/* Persistent mode (on = 1; a new batch has on = 0).  A step is then three kernel
+ * launches: one cooperative kernel for the immersed-boundary phases (regeneration of
+ * the Lagrangian points, Eq. 9-10; the mdf_iters interpolation and spreading
+ * iterations, Eq. 11-13; the sums of the hydrodynamic force and torque, Eq. 14-15), one
+ * cooperative kernel for the contact phases and the particle update (Eq. 16-18, beside
+ * the collision), and the collide-stream launch (Eq. 1-8; tile shape 0 steps every
+ * node, edges included, in one launch; other shapes add an edge launch in odd steps).
+ * The phases inside a kernel are separated by grid barriers.  Every wait is bounded:
+ * a block that polls a barrier more than barrier_limit times (about 0.2 us each;
+ * 0 = the default, 10^7) gives up, sets the batch's TIMEOUT status and its kernel
+ * returns; so does every other block at that barrier or the next.  The kernels' blocks
+ * must all be resident at once (a cooperative launch fails otherwise, reported as
+ * CUDA); nothing else may wait on them.  The arithmetic is that of the ordinary mode,
+ * block for block.  Takes effect from the next step (graphs are captured again).
+ * Errors: INVALID_ARG for on other than 0 or 1 or a negative barrier_limit; CUDA if the
+ * IBM kernel's shared memory cannot be granted. */
+int ibm_lbm_batch_set_persistent(ibm_lbm_batch* b, int32_t on, int64_t barrier_limit);
+int ibm_lbm_batch_get_persistent(const ibm_lbm_batch* b, int32_t* on);
 
 /* Member i as a run handle, for the field and particle calls (get_fields,
  * get_particles, get_pdfs, ...).  Owned by the batch; do not step or destroy it. */

@@ -21,7 +21,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "ibmlbm.h")
 OK = 0
 ERRORS = {
     -1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "WORKSPACE", -4: "CUDA", -5: "NONFINITE",
-    -6: "OUT_OF_DOMAIN", -7: "CAPACITY", -8: "BOUNDS",
+    -6: "OUT_OF_DOMAIN", -7: "CAPACITY", -8: "BOUNDS", -9: "TIMEOUT",
 }
 PARTS = ("macro", "ibm", "collide_stream", "pairs", "particles")
 
@@ -139,6 +139,8 @@ SIGNATURES = {
     "ibm_lbm_batch_set_tile_shape": (C.c_int, [_vp, C.c_int32]),
     "ibm_lbm_batch_get_tile_shape": (C.c_int, [_vp, _ip]),
     "ibm_lbm_batch_autotune": (C.c_int, [_vp, C.c_int32, _fp]),
+    "ibm_lbm_batch_set_persistent": (C.c_int, [_vp, C.c_int32, C.c_int64]),
+    "ibm_lbm_batch_get_persistent": (C.c_int, [_vp, _ip]),
     "ibm_lbm_batch_destroy": (None, [_vp]),
 }
 
@@ -461,6 +463,17 @@ class Batch:
         v = C.c_int32(0)
         _check(self.L.ibm_lbm_batch_get_tile_shape(self.h, C.byref(v)), "batch_get_tile_shape", self.L)
         return v.value
+
+    def set_persistent(self, on: bool = True, barrier_limit: int = 0):
+        """Three launches a step: the IBM phases and the contact phases each as one
+        cooperative kernel with bounded grid barriers (barrier_limit polls; 0 = default)."""
+        _check(self.L.ibm_lbm_batch_set_persistent(self.h, int(bool(on)), int(barrier_limit)),
+               "batch_set_persistent", self.L)
+
+    def persistent(self) -> bool:
+        v = C.c_int32(0)
+        _check(self.L.ibm_lbm_batch_get_persistent(self.h, C.byref(v)), "batch_get_persistent", self.L)
+        return bool(v.value)
 
     def autotune(self, steps_per_shape: int = 2) -> tuple:
         """Time every tile shape on steps_per_shape real steps; keep the fastest.

@@ -1399,6 +1399,11 @@ struct BatchPlan {
 // (BK_CW0 + c: the interpolation and spreading blocks of the members of box-size
 // class c, launched with that class's shared memory)
 constexpr int kMaxBoxClasses = 8;
+// the batch's own device words: the grid barriers of its persistent kernels (count,
+// generation) and its status word (ST_TIMEOUT), each on its own 128-byte line
+constexpr int kBatchWords = 96, kBarIbm = 0, kBarPairs = 32, kBatchStatus = 64;
+// polls (about 0.2 us each) before a persistent kernel's grid barrier gives up
+constexpr unsigned long long kDefaultBarrierLimit = 10000000ull;
 enum { BK_LBM, BK_EDGE, BK_WARP, BK_LANE, BK_PCLEAR, BK_PINS, BK_PSEARCH, BK_PFORCE, BK_CW0,
        BK_COUNT = BK_CW0 + kMaxBoxClasses };
 
@@ -1483,7 +1488,7 @@ size_t batch_table_bytes(const ibm_lbm_config* cfgs, int32_t n) {
   const size_t args = (size_t)n * (2 * sizeof(LbmArgs) + 2 * sizeof(IbmArgs) + 2 * sizeof(RegenArgs) +
                                    4 * sizeof(PairArgs));
   const size_t tiles = (size_t)tile_shape_count() * (sizeof(int) * (n + 1) + 16);
-  return args + sizeof(int) * (blocks + (size_t)BK_COUNT * n) + tiles + 4096;
+  return args + sizeof(int) * (blocks + (size_t)BK_COUNT * n) + tiles + kBatchWords * sizeof(unsigned) + 4096;
 }
 
 BatchPlan plan_batch(const ibm_lbm_config* cfgs, int32_t n) {
@@ -1540,6 +1545,10 @@ struct ibm_lbm_batch {
   bool graph_ok[2], graph_tried[2];
   cudaGraphExec_t graph[2];
   int graph_kernels[2];
+  // persistent mode: the IBM phases and the contact phases as one cooperative kernel each
+  bool persistent;
+  unsigned long long barrier_limit;
+  unsigned* words;  // kBatchWords device words (barriers, status)
 };
 
 namespace {
@@ -1576,7 +1585,40 @@ int enqueue_batch_step(ibm_lbm_batch* b, int parity, int have_prev, int* nk, cud
       if (B[BK_CW0 + c]) CUDA_TRY(cudaStreamWaitEvent(s, b->cev[c], 0));
     return IBMLBM_OK;
   };
-  if (B[BK_WARP]) {
+  if (B[BK_WARP] && b->persistent) {
+    // regeneration of this step's points, the MDF iterations and the force sums in one
+    // kernel; the contacts and the particle update in one kernel beside the collision
+    IbmBatch P{};
+    P.regen = fuse(b, BK_LANE, b->regen_args[parity]);
+    P.warp = fuse(b, BK_WARP, ia);
+    P.lane = fuse(b, BK_LANE, ia);
+    P.nwarp = B[BK_WARP];
+    P.nlane = B[BK_LANE];
+    P.mdf = b->mdf;
+    P.bar = b->words + kBarIbm;
+    P.limit = b->barrier_limit;
+    P.status = b->words + kBatchStatus;
+    CUDA_TRY(launch_ibm_batch(P, parity, b->store, b->smem, s, false));
+    ++k;
+    CUDA_TRY(cudaEventRecord(b->fork, s));
+    CUDA_TRY(cudaStreamWaitEvent(b->side, b->fork, 0));
+    const void* pa = b->pair_args[parity][have_prev];
+    PairBatch Q{};
+    Q.clear = fuse(b, BK_PCLEAR, pa);
+    Q.ins = fuse(b, BK_PINS, pa);
+    Q.search = fuse(b, BK_PSEARCH, pa);
+    Q.force = fuse(b, BK_PFORCE, pa);
+    Q.nclear = B[BK_PCLEAR];
+    Q.nins = B[BK_PINS];
+    Q.nsearch = B[BK_PSEARCH];
+    Q.nforce = B[BK_PFORCE];
+    Q.bar = b->words + kBarPairs;
+    Q.limit = b->barrier_limit;
+    Q.status = b->words + kBatchStatus;
+    CUDA_TRY(launch_pairs_batch(Q, b->side));
+    ++k;
+    CUDA_TRY(cudaEventRecord(b->join, b->side));
+  } else if (B[BK_WARP]) {
     int rc;
     if (b->mdf == 0 && (rc = phase(false, 0)) != IBMLBM_OK) return rc;
     for (int m = 1; m <= b->mdf; ++m) {
@@ -1606,7 +1648,7 @@ int enqueue_batch_step(ibm_lbm_batch* b, int parity, int have_prev, int* nk, cud
     CUDA_TRY(launch_lbm_step_tiles(b->shape, b->lbm_args[parity], b->tile_first[b->shape], b->n,
                                    b->tile_total[b->shape], fuse(b, BK_EDGE, la), B[BK_EDGE], b->store, parity, s));
   if (ev) CUDA_TRY(cudaEventRecord(ev[1], s));
-  k += (parity == 1 && B[BK_EDGE]) ? 2 : 1;
+  k += (parity == 1 && B[BK_EDGE] && b->shape != 0) ? 2 : 1;  // shape 0: one launch
   if (B[BK_WARP]) CUDA_TRY(cudaStreamWaitEvent(s, b->join, 0));
   *nk = k;
   return IBMLBM_OK;
@@ -1694,6 +1736,9 @@ int ibm_lbm_batch_init(const ibm_lbm_config* cfgs, int32_t n, void* d_workspace,
   b->have_prev = 0;
   b->launches = 0;
   b->graph_ok[0] = b->graph_ok[1] = b->graph_tried[0] = b->graph_tried[1] = false;
+  b->persistent = false;
+  b->barrier_limit = kDefaultBarrierLimit;
+  b->words = nullptr;
   char* ws = static_cast<char*>(d_workspace);
   auto bail = [&](int code) {
     const std::string msg = g_err;
@@ -1780,6 +1825,8 @@ int ibm_lbm_batch_init(const ibm_lbm_config* cfgs, int32_t n, void* d_workspace,
     o_first[t] = put(first.data(), sizeof(int) * n);
     o_cav[t] = cav.empty() ? o : put(cav.data(), sizeof(int) * cav.size());
   }
+  std::vector<unsigned> words(kBatchWords, 0u);
+  const size_t o_words = put(words.data(), sizeof(unsigned) * kBatchWords);
   size_t o_tile[kMaxTileShapes] = {};
   b->shape = 0;
   for (int sh = 1; sh < tile_shape_count(); ++sh) {
@@ -1809,6 +1856,7 @@ int ibm_lbm_batch_init(const ibm_lbm_config* cfgs, int32_t n, void* d_workspace,
     b->cav[t] = reinterpret_cast<int*>(dt + o_cav[t]);
   }
   for (int sh = 1; sh < tile_shape_count(); ++sh) b->tile_first[sh] = reinterpret_cast<int*>(dt + o_tile[sh]);
+  b->words = reinterpret_cast<unsigned*>(dt + o_words);
 #undef BATCH_TRY
   *out = b;
   return IBMLBM_OK;
@@ -1938,12 +1986,39 @@ int ibm_lbm_batch_autotune(ibm_lbm_batch* b, int32_t steps_per_shape, float* h_m
 int ibm_lbm_batch_sync(ibm_lbm_batch* b) {
   if (!b) return fail(IBMLBM_ERR_INVALID_ARG, "batch is NULL");
   CUDA_TRY(cudaStreamSynchronize(b->s));
+  uint32_t st = 0;
+  CUDA_TRY(cudaMemcpy(&st, b->words + kBatchStatus, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st) {
+    // a barrier gave up: its count may be left short, so both barriers start afresh
+    CUDA_TRY(cudaMemset(b->words, 0, sizeof(unsigned) * kBatchWords));
+  }
   int first_rc = IBMLBM_OK;
   for (ibm_lbm_handle* h : b->m) {
     const int rc = ibm_lbm_sync(h);
     if (rc && !first_rc) first_rc = rc;
   }
+  if (st & ST_TIMEOUT) return fail(IBMLBM_ERR_TIMEOUT, "a grid barrier of a persistent batch kernel timed out");
   return first_rc;
+}
+
+int ibm_lbm_batch_set_persistent(ibm_lbm_batch* b, int32_t on, int64_t barrier_limit) {
+  if (!b) return fail(IBMLBM_ERR_INVALID_ARG, "batch is NULL");
+  if (on != 0 && on != 1) return fail(IBMLBM_ERR_INVALID_ARG, "on must be 0 or 1");
+  if (barrier_limit < 0) return fail(IBMLBM_ERR_INVALID_ARG, "barrier_limit < 0");
+  if (on) {
+    // the shared memory of the IBM kernel is granted before any capture
+    for (int p = 0; p < 2; ++p) CUDA_TRY(launch_ibm_batch(IbmBatch{}, p, b->store, b->smem, b->s, true));
+  }
+  b->persistent = on != 0;
+  b->barrier_limit = barrier_limit ? (unsigned long long)barrier_limit : kDefaultBarrierLimit;
+  drop_batch_graphs(b);  // captured in the other mode or with the old limit
+  return IBMLBM_OK;
+}
+
+int ibm_lbm_batch_get_persistent(const ibm_lbm_batch* b, int32_t* on) {
+  if (!b || !on) return fail(IBMLBM_ERR_INVALID_ARG, "batch or on is NULL");
+  *on = b->persistent ? 1 : 0;
+  return IBMLBM_OK;
 }
 
 ibm_lbm_handle* ibm_lbm_batch_member(ibm_lbm_batch* b, int32_t i) {

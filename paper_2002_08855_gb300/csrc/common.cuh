@@ -62,6 +62,7 @@ enum : uint32_t {
   ST_NONFINITE = 1u,
   ST_OUT_OF_DOMAIN = 2u,
   ST_CAPACITY = 4u,
+  ST_TIMEOUT = 8u,  // a grid barrier of a persistent kernel gave up waiting
 };
 
 // ------------------------------------------------------------------ lattices
@@ -317,6 +318,48 @@ struct Fuse {
   const int* first;   // [members]
 };
 
+// The argument struct of virtual block vb of a fused block map, and (blk) the block's
+// index in its member's grid (the persistent kernels walk the virtual blocks).
+template <class T>
+__device__ __forceinline__ T fused_args(const Fuse& F, unsigned vb, unsigned& blk) {
+  const int m = F.cav[vb];
+  blk = vb - (unsigned)F.first[m];
+  return static_cast<const T*>(F.args)[m];
+}
+
+// Grid-wide barrier of a persistent kernel launched cooperatively (every block of the
+// grid is resident).  bar[0] counts the blocks that arrived, bar[1] is the generation;
+// the host zeroes both before each launch.  The wait is bounded: after `limit` polls
+// (a short sleep each) the block sets ST_TIMEOUT in *status and the barrier returns
+// false, and the caller returns (every other block then gives up at the same barrier
+// or the next).  Writes before the barrier are visible to every block after it.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned long long limit, uint32_t* status) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned long long polls = 0;
+      while (*gen == g) {
+        if (++polls > limit) {
+          atomicOr(status, ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(200);
+      }
+    }
+    __threadfence();
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
 // In a kernel templated on bool FUSED: A = this block's argument struct (the kernel
 // parameter A0 for a single run; for a member, a local copy, so the fields the kernel
 // uses are loaded once instead of at every use), BLK = the block's index in its
@@ -368,6 +411,28 @@ struct PairArgs {
   int integrate;        // 1: advance the particles (PartState) after the contact force
   int have_prev;        // a previous step exists (history terms of the update)
   PartState ps;
+};
+
+// The persistent kernels of a batched step: the fused block maps of their phases, the
+// number of virtual blocks of each, and the bounded grid barrier's state.
+struct PairBatch {
+  Fuse clear, ins, search, force;
+  unsigned nclear, nins, nsearch, nforce;  // virtual blocks (force: 128 threads each)
+  unsigned* bar;
+  unsigned long long limit;
+  uint32_t* status;
+};
+
+struct IbmBatch {
+  Fuse regen;     // RegenArgs: this step's points (Lagrangian regeneration)
+  Fuse warp;      // IbmArgs: interpolation and spreading, one warp per particle
+  Fuse lane;      // IbmArgs: the sums of the hydrodynamic force and interior momentum
+  unsigned nwarp, nlane;
+  int mdf;
+  int wfloats;    // shared-memory floats per warp (set by the launcher)
+  unsigned* bar;
+  unsigned long long limit;
+  uint32_t* status;
 };
 
 }  // namespace ibmlbm

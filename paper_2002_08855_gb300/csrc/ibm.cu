@@ -144,14 +144,17 @@ __device__ __forceinline__ bool box_node(const Geo& g, int ox, int oy, int r, in
 //     last iteration only records the residual U_b - D_I u^(M).
 // Lane k then interpolates point k from shared memory.  Box nodes beyond a wall hold
 // zero, which drops them from the sum.
+// wf: floats of shared memory per warp (0: this mode's need for the box).  A kernel
+// whose warps go on to other particles independently passes one stride for all.
 template <int SC, int PARITY, int MODE, int ST>
-__device__ __forceinline__ void interp2_body(const IbmArgs& A, int m, unsigned blk) {
+__device__ __forceinline__ void interp2_body(const IbmArgs& A, int m, unsigned blk, int wf = 0) {
   extern __shared__ __align__(16) float smem_i[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int i = (int)blk * (int)(blockDim.x >> 5) + wib;  // warps per block: blockDim
   if (i >= A.np) return;  // whole warp
   const int S = SC ? SC : A.box, P = box_pitch(S), cells = S * P;
-  float2* box = reinterpret_cast<float2*>(smem_i + (size_t)wib * interp2_warp_floats(MODE, S));
+  __syncwarp();  // the warp's shared memory is free (a particle before may have used it)
+  float2* box = reinterpret_cast<float2*>(smem_i + (size_t)wib * (wf ? wf : interp2_warp_floats(MODE, S)));
   float2* aux = box + cells;
   float2* ub = reinterpret_cast<float2*>(A.ubox) + (size_t)i * cells;
   // the first point of this lane is loaded before the box, so both latencies overlap
@@ -305,13 +308,14 @@ __global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A0,
 // of an instruction touch one cell and plain read-add-write is exact.  Finally the warp
 // adds the non-zero box cells to f_IB with one global vector atomic per cell.
 template <int SC>
-__device__ __forceinline__ void spread2_body(const IbmArgs& A, unsigned blk) {
+__device__ __forceinline__ void spread2_body(const IbmArgs& A, unsigned blk, int wf = 0) {
   extern __shared__ __align__(16) float smem2[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int i = (int)blk * (int)(blockDim.x >> 5) + wib;  // warps per block: blockDim
   if (i >= A.np) return;  // whole warp
   const int S = SC ? SC : A.box, P = box_pitch(S), cells = S * P;
-  float* base = smem2 + (size_t)wib * spread2_warp_floats(S);
+  __syncwarp();  // the warp's shared memory is free (a particle before may have used it)
+  float* base = smem2 + (size_t)wib * (wf ? wf : spread2_warp_floats(S));
   float2* box = reinterpret_cast<float2*>(base);
   float* tw = base + 2 * cells;                                   // [32][kTw]
   float4* tp = reinterpret_cast<float4*>(tw + 32 * kTw);          // [32]
@@ -1190,10 +1194,9 @@ __global__ void __launch_bounds__(256, (FUSED || SC == 0) ? 3 : 5) ibm_forces2_k
 // and (3D) mark the nodes within mark_radius of the centre in the next step's node mask.
 // init != 0 first refreshes the fixed-point centre and the single-precision
 // velocities from the double-precision state (initial state, new particle state).
-template <int D, bool FUSED>
-__global__ void __launch_bounds__(256) regen_kernel(RegenArgs A0, int init, Fuse FU) {
-  IBMLBM_BIND(FUSED, RegenArgs, A, A0, FU, blk);
-  const int i = (int)((blk * blockDim.x + threadIdx.x) >> 5);
+template <int D>
+__device__ __forceinline__ void regen_body(const RegenArgs& A, int init, unsigned blk) {
+  const int i = (int)((blk * 256u + threadIdx.x) >> 5);  // 256-thread blocks
   const int lane = threadIdx.x & 31;
   if (i >= A.np) return;
   const long long pi = i;
@@ -1274,6 +1277,94 @@ __global__ void __launch_bounds__(256) regen_kernel(RegenArgs A0, int init, Fuse
       atomicOr(row + wd, bits);
       x = end + 1;
     }
+  }
+}
+
+template <int D, bool FUSED>
+__global__ void __launch_bounds__(256) regen_kernel(RegenArgs A0, int init, Fuse FU) {
+  IBMLBM_BIND(FUSED, RegenArgs, A, A0, FU, blk);
+  regen_body<D>(A, init, blk);
+}
+
+// ---------------------------------------------- persistent kernel of a batched step
+// The IBM phases of a batched step (2D) in one persistent kernel (cooperative launch,
+// kIbmWarps warps a block, shared memory for the largest particle box of the batch):
+// regenerate this step's Lagrangian points from the updated particle state, then for
+// each MDF iteration the interpolation and the spreading, then the sums of the
+// hydrodynamic force and interior momentum, with a bounded grid barrier after each
+// phase (Jacobi across particles, as with separate launches).  Two blocks an SM: with
+// every phase's code in one kernel it takes 128 registers a thread (the separate
+// launches 40 to 77).
+template <int PARITY, int ST>
+__device__ __forceinline__ void interp2_fused(const IbmArgs& A, int m, unsigned blk, int wf) {
+  if (m == 0 || m == 1) {
+    switch (A.box) {
+      case 14: interp2_body<14, PARITY, 0, ST>(A, m, blk, wf); return;
+      case 16: interp2_body<16, PARITY, 0, ST>(A, m, blk, wf); return;
+      case 18: interp2_body<18, PARITY, 0, ST>(A, m, blk, wf); return;
+      case 20: interp2_body<20, PARITY, 0, ST>(A, m, blk, wf); return;
+      case 22: interp2_body<22, PARITY, 0, ST>(A, m, blk, wf); return;
+      default: interp2_body<0, PARITY, 0, ST>(A, m, blk, wf); return;
+    }
+  }
+  switch (A.box) {
+    case 14: interp2_body<14, 0, 1, STORE_F32>(A, m, blk, wf); return;
+    case 16: interp2_body<16, 0, 1, STORE_F32>(A, m, blk, wf); return;
+    case 18: interp2_body<18, 0, 1, STORE_F32>(A, m, blk, wf); return;
+    case 20: interp2_body<20, 0, 1, STORE_F32>(A, m, blk, wf); return;
+    case 22: interp2_body<22, 0, 1, STORE_F32>(A, m, blk, wf); return;
+    default: interp2_body<0, 0, 1, STORE_F32>(A, m, blk, wf); return;
+  }
+}
+
+__device__ __forceinline__ void spread2_fused(const IbmArgs& A, unsigned blk, int wf) {
+  switch (A.box) {
+    case 14: spread2_body<14>(A, blk, wf); return;
+    case 16: spread2_body<16>(A, blk, wf); return;
+    case 18: spread2_body<18>(A, blk, wf); return;
+    case 20: spread2_body<20>(A, blk, wf); return;
+    case 22: spread2_body<22>(A, blk, wf); return;
+    default: spread2_body<0>(A, blk, wf); return;
+  }
+}
+
+__device__ __forceinline__ void forces2_fused(const IbmArgs& A, unsigned blk) {
+  switch (A.box) {
+    case 14: forces2_body<14>(A, blk); return;
+    case 16: forces2_body<16>(A, blk); return;
+    case 18: forces2_body<18>(A, blk); return;
+    case 20: forces2_body<20>(A, blk); return;
+    case 22: forces2_body<22>(A, blk); return;
+    default: forces2_body<0>(A, blk); return;
+  }
+}
+
+template <int PARITY, int ST>
+__global__ void __launch_bounds__(kIbmWarps * 32, 2) ibm_batch_kernel(IbmBatch P) {
+  unsigned blk;
+  // a barrier of an earlier launch gave up: its counts are stale until the host resets them
+  if (__syncthreads_or(threadIdx.x == 0 && (*(volatile uint32_t*)P.status & ST_TIMEOUT))) return;
+  for (unsigned vb = blockIdx.x; vb < P.nlane; vb += gridDim.x) {
+    const RegenArgs A = fused_args<RegenArgs>(P.regen, vb, blk);
+    regen_body<2>(A, 0, blk);
+  }
+  if (!grid_barrier(P.bar, P.limit, P.status)) return;
+  for (int m = P.mdf == 0 ? 0 : 1; m <= P.mdf; ++m) {
+    for (unsigned vb = blockIdx.x; vb < P.nwarp; vb += gridDim.x) {
+      const IbmArgs A = fused_args<IbmArgs>(P.warp, vb, blk);
+      interp2_fused<PARITY, ST>(A, m, blk, P.wfloats);
+    }
+    if (!grid_barrier(P.bar, P.limit, P.status)) return;
+    if (m == 0) break;
+    for (unsigned vb = blockIdx.x; vb < P.nwarp; vb += gridDim.x) {
+      const IbmArgs A = fused_args<IbmArgs>(P.warp, vb, blk);
+      spread2_fused(A, blk, P.wfloats);
+    }
+    if (!grid_barrier(P.bar, P.limit, P.status)) return;
+  }
+  for (unsigned vb = blockIdx.x; vb < P.nlane; vb += gridDim.x) {
+    const IbmArgs A = fused_args<IbmArgs>(P.lane, vb, blk);
+    forces2_fused(A, blk);
   }
 }
 
@@ -1448,6 +1539,42 @@ cudaError_t launch_ibm_forces_fused(const Fuse& F, unsigned blocks, cudaStream_t
 cudaError_t launch_regen_fused(const Fuse& F, unsigned blocks, cudaStream_t s) {
   regen_kernel<2, true><<<blocks, 256, 0, s>>>(RegenArgs{}, 0, F);
   return cudaGetLastError();
+}
+
+template <int PARITY, int ST>
+static cudaError_t ibm_batch_go(const IbmBatch& P0, size_t smem, cudaStream_t s, bool prepare) {
+  auto kern = ibm_batch_kernel<PARITY, ST>;
+  if (prepare) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kIbmWarps * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+  IbmBatch P = P0;
+  // one shared-memory stride per warp for every member: a block's warps move on to
+  // particles of other members (other box sizes) each at its own pace
+  P.wfloats = (int)(smem / (sizeof(float) * kIbmWarps));
+  const unsigned need = max(max(P.nwarp, P.nlane), 1u);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(min(need, (unsigned)(per_sm * sms)));
+  cfg.blockDim = dim3(kIbmWarps * 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, P);
+}
+
+// prepare (once, before any capture): allow the shared memory; otherwise launch
+cudaError_t launch_ibm_batch(const IbmBatch& P, int parity, int store, size_t smem, cudaStream_t s,
+                             bool prepare) {
+  if (store == STORE_F32)
+    return parity == 0 ? ibm_batch_go<0, STORE_F32>(P, smem, s, prepare) : ibm_batch_go<1, STORE_F32>(P, smem, s, prepare);
+  return parity == 0 ? ibm_batch_go<0, STORE_F16>(P, smem, s, prepare) : ibm_batch_go<1, STORE_F16>(P, smem, s, prepare);
 }
 
 }  // namespace ibmlbm

@@ -64,6 +64,13 @@ unsigned pair_warp_blocks(int n);
 cudaError_t launch_pairs_fused(const Fuse& Fc, unsigned bc, const Fuse& Fi, unsigned bi,
                                const Fuse& Fs, unsigned bs, const Fuse& Ff, unsigned bf,
                                cudaStream_t s);
+// persistent (cooperative) kernels of a batched step, phases separated by bounded grid
+// barriers: the IBM phases (regeneration, MDF iterations, forces) and the contact
+// phases (clear, insert, search, force and update).  prepare: only raise the kernel's
+// shared-memory limit (once, before any stream capture).
+cudaError_t launch_ibm_batch(const IbmBatch& P, int parity, int store, size_t smem, cudaStream_t s,
+                             bool prepare);
+cudaError_t launch_pairs_batch(const PairBatch& P, cudaStream_t s);
 
 // sets the calling thread's text for ibm_lbm_last_error()
 void set_last_error(const std::string& msg);

@@ -341,16 +341,21 @@ __device__ __forceinline__ void step_row_nodes(const LbmArgs& A, long long row, 
 // row (spr blocks per row).  Blocks per SM the registers must allow: D2Q9 10 (48
 // registers a thread); D3Q19 7 (72 registers, a few bytes spilled: more PDF loads in
 // flight than at the 80 registers it takes unbounded).
-template <class L, int PARITY, int ST, int K, bool FUSED>
-__global__ void __launch_bounds__(kLbmBlock, L::dim == 3 ? 7 : 10) lbm_step_kernel(LbmArgs A0, int spr0, Fuse FU) {
-  IBMLBM_BIND(FUSED, LbmArgs, A, A0, FU, blk);
+template <class L, int PARITY, int ST, int K>
+__device__ __forceinline__ void step_tile_body(const LbmArgs& A, int spr, unsigned blk) {
   const Geo& g = A.g;
-  const int spr = FUSED ? (g.nx + K * kLbmBlock - 1) / (K * kLbmBlock) : spr0;
   const unsigned b = blk, uspr = (unsigned)spr, uny = (unsigned)g.ny;
   const unsigned row = b / uspr, seg = b - row * uspr;
   const unsigned uz = row / uny;
   step_row_nodes<L, PARITY, ST, K>(A, row, (int)(row - uz * uny), (int)uz,
                                    K * ((int)seg * kLbmBlock + (int)threadIdx.x));
+}
+
+template <class L, int PARITY, int ST, int K, bool FUSED>
+__global__ void __launch_bounds__(kLbmBlock, L::dim == 3 ? 7 : 10) lbm_step_kernel(LbmArgs A0, int spr0, Fuse FU) {
+  IBMLBM_BIND(FUSED, LbmArgs, A, A0, FU, blk);
+  const int spr = FUSED ? (A.g.nx + K * kLbmBlock - 1) / (K * kLbmBlock) : spr0;
+  step_tile_body<L, PARITY, ST, K>(A, spr, blk);
 }
 
 // ------------------------------------------------------------ vector row kernel
@@ -747,13 +752,10 @@ __host__ __device__ inline void edge_counts(const Geo& g, int dim, long long& nf
   nends = inner * (g.nx > 1 ? 2 : 1);
 }
 
-template <class L, int ST, bool FUSED>
-__global__ void __launch_bounds__(kLbmBlock) lbm_step_edge_kernel(LbmArgs A0, long long nface0,
-                                                                 long long nends0, Fuse FU) {
-  IBMLBM_BIND(FUSED, LbmArgs, A, A0, FU, blk);
+template <class L, int ST>
+__device__ __forceinline__ void step_edge_body(const LbmArgs& A, long long nface, long long nends,
+                                               unsigned blk) {
   const Geo& g = A.g;
-  long long nface = nface0, nends = nends0;
-  if (FUSED) edge_counts(g, L::dim, nface, nends);
   const long long t = blk * (long long)kLbmBlock + threadIdx.x;
   int x, y, z;
   if (t < nface * g.nx) {  // face rows
@@ -789,6 +791,33 @@ __global__ void __launch_bounds__(kLbmBlock) lbm_step_edge_kernel(LbmArgs A0, lo
   }
   const long long row = (long long)y + (long long)g.ny * z;
   step_node<L, 1, ST>(A, row, x, y, z, (long long)x + (long long)g.nx * row);
+}
+
+template <class L, int ST, bool FUSED>
+__global__ void __launch_bounds__(kLbmBlock) lbm_step_edge_kernel(LbmArgs A0, long long nface0,
+                                                                 long long nends0, Fuse FU) {
+  IBMLBM_BIND(FUSED, LbmArgs, A, A0, FU, blk);
+  long long nface = nface0, nends = nends0;
+  if (FUSED) edge_counts(A.g, L::dim, nface, nends);
+  step_edge_body<L, ST>(A, nface, nends, blk);
+}
+
+// An odd step of a 2D batch in one launch: blocks [0, blocks) are the members' row
+// tiles, the rest their face rows and row ends.  No node of one set reads or writes a
+// slot of the other (an AA step swaps each node's own slots), so both run together.
+template <int ST>
+__global__ void __launch_bounds__(kLbmBlock, 10) lbm_step_odd_batch_kernel(Fuse F, unsigned blocks, Fuse FE) {
+  unsigned blk;
+  if (blockIdx.x < blocks) {
+    const LbmArgs A = fused_args<LbmArgs>(F, blockIdx.x, blk);
+    constexpr int K = ST == STORE_F32 ? 1 : 2;
+    step_tile_body<Lat<2>, 1, ST, K>(A, (A.g.nx + K * kLbmBlock - 1) / (K * kLbmBlock), blk);
+  } else {
+    const LbmArgs A = fused_args<LbmArgs>(FE, blockIdx.x - blocks, blk);
+    long long nface, nends;
+    edge_counts(A.g, 2, nface, nends);
+    step_edge_body<Lat<2>, ST>(A, nface, nends, blk);
+  }
 }
 
 // Boundary nodes of the extrapolation boundaries: the nodes on a face of a
@@ -1071,8 +1100,10 @@ cudaError_t launch_lbm_step_fused(const Fuse& F, unsigned blocks, const Fuse& FE
   const LbmArgs none{};
 #define IBMLBM_STEPF(P, ST)                                                                        \
   do {                                                                                               \
-    lbm_step_kernel<Lat<2>, P, ST, step_k<ST>(), true><<<blocks, kLbmBlock, 0, s>>>(none, 0, F);   \
-    if (P == 1 && eblocks) lbm_step_edge_kernel<Lat<2>, ST, true><<<eblocks, kLbmBlock, 0, s>>>(none, 0, 0, FE); \
+    if (P == 1 && eblocks)                                                                           \
+      lbm_step_odd_batch_kernel<ST><<<blocks + eblocks, kLbmBlock, 0, s>>>(F, blocks, FE);           \
+    else                                                                                             \
+      lbm_step_kernel<Lat<2>, P, ST, step_k<ST>(), true><<<blocks, kLbmBlock, 0, s>>>(none, 0, F);  \
   } while (0)
   if (store == STORE_F32) {
     if (parity == 0) IBMLBM_STEPF(0, STORE_F32); else IBMLBM_STEPF(1, STORE_F32);

@@ -15,6 +15,8 @@
 // the new centre to the other centre buffer, so neighbours still read old centres.
 #include <cmath>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "launch.h"
 
@@ -37,10 +39,10 @@ __device__ __forceinline__ int cell_of(const PairArgs& A, int i) {
   return c;
 }
 
-template <int D, bool FUSED>
-__global__ void pair_insert_kernel(PairArgs A0, Fuse FU) {
-  IBMLBM_BIND(FUSED, PairArgs, A, A0, FU, blk);
-  const int i = (int)(blk * blockDim.x + threadIdx.x);
+// one thread per particle (thread tid of a block of nthr): its cell's next bucket slot
+template <int D>
+__device__ __forceinline__ void pair_insert_body(const PairArgs& A, unsigned blk, int tid, int nthr) {
+  const int i = (int)(blk * nthr + tid);
   if (i >= A.n) return;
   const int c = cell_of<D>(A, i);
   if (!IBMLBM_CHK(c, (long long)A.nc[0] * A.nc[1] * A.nc[2])) return;
@@ -49,6 +51,12 @@ __global__ void pair_insert_kernel(PairArgs A0, Fuse FU) {
     A.cell_ids[(long long)c * A.cell_cap + slot] = i;
   else
     atomicOr(A.status, ST_CAPACITY);
+}
+
+template <int D, bool FUSED>
+__global__ void pair_insert_kernel(PairArgs A0, Fuse FU) {
+  IBMLBM_BIND(FUSED, PairArgs, A, A0, FU, blk);
+  pair_insert_body<D>(A, blk, (int)threadIdx.x, (int)blockDim.x);
 }
 
 // X_i - X_j with the nearest image on periodic axes
@@ -187,15 +195,16 @@ __device__ __forceinline__ bool is_partner(const PairArgs& A, const double (&Xi)
 // tests occupied slots l, l+32, ... of the concatenated buckets.  Accepted partners
 // are appended in lane order and sorted by index.  Writes the sorted list, its length
 // and the number of partners j > i.
-template <int D, bool FUSED>
-__global__ void __launch_bounds__(256) pair_search_kernel(PairArgs A0, Fuse FU) {
-  IBMLBM_BIND(FUSED, PairArgs, A, A0, FU, blk);
+// (256-thread blocks: eight warps, one particle each)
+template <int D>
+__device__ __forceinline__ void pair_search_body(const PairArgs& A, unsigned blk) {
   __shared__ int s_list[8][kMaxNeighbors];
   __shared__ int s_cell[8][32];
   __shared__ int s_off[8][33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int i = (int)((blk * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int i = (int)((blk * 256ll + threadIdx.x) >> 5);
   if (i >= A.n) return;  // whole warp
+  __syncwarp();  // the warp's lists are free (a particle before may have used them)
   int* list = s_list[w];
   int* sc = s_cell[w];
   int* so = s_off[w];
@@ -260,6 +269,12 @@ __global__ void __launch_bounds__(256) pair_search_kernel(PairArgs A0, Fuse FU) 
     cnt += __popc(m);
   }
   store_partners(A, i, lane, list, cnt);
+}
+
+template <int D, bool FUSED>
+__global__ void __launch_bounds__(256) pair_search_kernel(PairArgs A0, Fuse FU) {
+  IBMLBM_BIND(FUSED, PairArgs, A, A0, FU, blk);
+  pair_search_body<D>(A, blk);
 }
 
 // ---------------------------------------------------------------- grid search
@@ -360,10 +375,9 @@ __global__ void __launch_bounds__(256) grid_search_kernel(PairArgs A) {
 
 // Eq. 16 contact force on particle i from its sorted partner list (summed in index
 // order) and from one mirror image per wall, then (in a time step) the particle update.
-template <int D, bool FUSED>
-__global__ void __launch_bounds__(128) pair_force_kernel(PairArgs A0, Fuse FU) {
-  IBMLBM_BIND(FUSED, PairArgs, A, A0, FU, blk);
-  const int i = (int)(blk * blockDim.x + threadIdx.x);
+template <int D>
+__device__ __forceinline__ void pair_force_body(const PairArgs& A, unsigned blk, int tid, int nthr) {
+  const int i = (int)(blk * nthr + tid);
   if (i >= A.n) return;
   double Xi[3] = {0.0, 0.0, 0.0};
   for (int k = 0; k < D; ++k) Xi[k] = A.X[(long long)i * D + k];
@@ -393,6 +407,12 @@ __global__ void __launch_bounds__(128) pair_force_kernel(PairArgs A0, Fuse FU) {
   }
   for (int k = 0; k < D; ++k) A.Fc[(long long)i * D + k] = F[k];
   if (A.integrate) advance_particle<D>(A, i, Xi, F);
+}
+
+template <int D, bool FUSED>
+__global__ void __launch_bounds__(128) pair_force_kernel(PairArgs A0, Fuse FU) {
+  IBMLBM_BIND(FUSED, PairArgs, A, A0, FU, blk);
+  pair_force_body<D>(A, blk, (int)threadIdx.x, (int)blockDim.x);
 }
 
 // exclusive scan of n ints into out[0..n] (out[n] = total); one block of 1024 threads
@@ -515,10 +535,14 @@ cudaError_t launch_pair_contacts(const PairArgs& A, cudaStream_t s) {
 
 // ---------------------------------------------- fused over the members of a 2D batch
 // zero each member's cell counts (one thread per cell)
+__device__ __forceinline__ void pair_clear_body(const PairArgs& A, unsigned blk, int tid, int nthr) {
+  const long long c = blk * (long long)nthr + tid;
+  if (c < (long long)A.nc[0] * A.nc[1] * A.nc[2]) A.cell_count[c] = 0;
+}
+
 __global__ void pair_clear_kernel(Fuse FU) {
   IBMLBM_BIND(true, PairArgs, A, PairArgs{}, FU, blk);
-  const long long c = blk * (long long)blockDim.x + threadIdx.x;
-  if (c < (long long)A.nc[0] * A.nc[1] * A.nc[2]) A.cell_count[c] = 0;
+  pair_clear_body(A, blk, (int)threadIdx.x, (int)blockDim.x);
 }
 
 unsigned pair_clear_blocks(const PairArgs& A) { return blocks_for((long long)A.nc[0] * A.nc[1] * A.nc[2], 256); }
@@ -535,6 +559,61 @@ cudaError_t launch_pairs_fused(const Fuse& Fc, unsigned bc, const Fuse& Fi, unsi
   if (bs) pair_search_kernel<2, true><<<bs, 256, 0, s>>>(PairArgs{}, Fs);
   if (bf) pair_force_kernel<2, true><<<bf, 128, 0, s>>>(PairArgs{}, Ff);
   return cudaGetLastError();
+}
+
+// The contact phases of a batched step in one persistent kernel (cooperative launch,
+// 256 threads a block): clear the members' cell counts, insert, search, then the
+// contact force and particle update (128-thread virtual blocks, two per block), with a
+// bounded grid barrier between the phases.
+__global__ void __launch_bounds__(256, 2) pairs_batch_kernel(PairBatch P) {
+  unsigned blk;
+  // a barrier of an earlier launch gave up: its counts are stale until the host resets them
+  if (__syncthreads_or(threadIdx.x == 0 && (*(volatile uint32_t*)P.status & ST_TIMEOUT))) return;
+  for (unsigned vb = blockIdx.x; vb < P.nclear; vb += gridDim.x) {
+    const PairArgs A = fused_args<PairArgs>(P.clear, vb, blk);
+    pair_clear_body(A, blk, (int)threadIdx.x, 256);
+  }
+  if (!grid_barrier(P.bar, P.limit, P.status)) return;
+  for (unsigned vb = blockIdx.x; vb < P.nins; vb += gridDim.x) {
+    const PairArgs A = fused_args<PairArgs>(P.ins, vb, blk);
+    pair_insert_body<2>(A, blk, (int)threadIdx.x, 256);
+  }
+  if (!grid_barrier(P.bar, P.limit, P.status)) return;
+  for (unsigned vb = blockIdx.x; vb < P.nsearch; vb += gridDim.x) {
+    const PairArgs A = fused_args<PairArgs>(P.search, vb, blk);
+    pair_search_body<2>(A, blk);
+  }
+  if (!grid_barrier(P.bar, P.limit, P.status)) return;
+  for (unsigned vb = blockIdx.x; 2 * vb < P.nforce; vb += gridDim.x) {
+    const unsigned v = 2 * vb + (threadIdx.x >> 7);
+    if (v >= P.nforce) continue;
+    const PairArgs A = fused_args<PairArgs>(P.force, v, blk);
+    pair_force_body<2>(A, blk, (int)(threadIdx.x & 127), 128);
+  }
+}
+
+cudaError_t launch_pairs_batch(const PairBatch& P, cudaStream_t s) {
+  static int per_sm = 0, sms = 0;
+  if (per_sm == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pairs_batch_kernel, 256, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+  }
+  const unsigned need = std::max({P.nclear, P.nins, P.nsearch, (P.nforce + 1) / 2, 1u});
+  const unsigned grid = std::min(need, (unsigned)(per_sm * sms));
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, pairs_batch_kernel, P);
 }
 
 cudaError_t launch_pair_compact(const PairArgs& A, int* pairs, long long cap, cudaStream_t s) {
