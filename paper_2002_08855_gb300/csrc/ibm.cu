@@ -428,12 +428,15 @@ __global__ void __launch_bounds__(kIbmWarps * 32) ibm_spread2_kernel(IbmArgs A0,
 // the interpolation stages u^(m-1) of the sphere's node box in shared memory and
 // interpolates every point from it; the spreading accumulates dF_b dV into the box and
 // adds its non-zero cells to f_IB.  Box rows are box3_pitch(S) cells apart (4 modulo
-// 8), so the 16 columns of a support fall on 16 banks.  Each point's row of the table
-// holds its 12 weights, its first box cell and u_b or dF_b dV.
+// 8), so the 16 columns of a support fall on 16 banks, and box planes box3_plane(S)
+// cells apart (8 modulo 16), so the 4 z levels of a support column fall on the 4 banks
+// of one residue class modulo 8.  Each point's row of the table holds its 12 weights,
+// its first box cell and u_b or dF_b dV.
 constexpr int kMdf3Threads = 512;
 constexpr int kMdf3Warps = kMdf3Threads / 32;
-constexpr int kTab3 = 17;  // table floats per point: 16 used; an odd stride keeps the rows
-                            // a thread-per-point loop touches on distinct banks
+constexpr int kTab3 = 17;  // table floats per point (12 weights, first cell, u_b or dF_b dV,
+                            // the interpolation's residue and rank); an odd stride keeps the
+                            // rows a thread-per-point loop touches on distinct banks
 constexpr int kRows3 = 2;  // box rows each warp stages per round
 
 __host__ __device__ inline int box3_pitch(int S) {
@@ -441,9 +444,16 @@ __host__ __device__ inline int box3_pitch(int S) {
   while ((p & 7) != 4) ++p;
   return p;
 }
+__host__ __device__ inline int box3_plane(int S) {
+  int p = box3_pitch(S) * S;
+  while ((p & 15) != 8) ++p;
+  return p;
+}
+// box [3][plane][S], table [nl][kTab3], the interpolation's point order [nl] and its
+// residue counts (or the spreading's reduction scratch) [32]
 size_t ibm_mdf3_smem(int nl, int box) {
-  const size_t plane = (size_t)box3_pitch(box) * box;
-  return sizeof(float) * (3 * plane * box + (size_t)kTab3 * nl + 32);
+  const size_t plane = (size_t)box3_plane(box);
+  return sizeof(float) * (3 * plane * box + (size_t)(kTab3 + 1) * nl + 32);
 }
 
 // box origin of sphere i (two nodes before its support reach) and the fixed-point
@@ -460,9 +470,11 @@ __device__ __forceinline__ void mdf3_origin(const IbmArgs& A, int i, int (&an)[3
 }
 
 // table row of every point of sphere i: its 12 weights and first box cell (zero
-// weights, and CAPACITY, for a support outside the box)
+// weights, and CAPACITY, for a support outside the box).  BIN: also count the points
+// by the residue of the first cell modulo 8 (cnt[8]) and keep (residue, rank) in row[16].
+template <bool BIN>
 __device__ __forceinline__ void mdf3_table(const IbmArgs& A, int i, const int (&org)[3], int S, int Py,
-                                           int Pz, float* tab) {
+                                           int Pz, float* tab, int* cnt) {
   const int nn[3] = {A.g.nx, A.g.ny, A.g.nz};
   for (int k = threadIdx.x; k < A.nl; k += kMdf3Threads) {
     const long long b = (long long)i * A.nl + k;
@@ -491,6 +503,10 @@ __device__ __forceinline__ void mdf3_table(const IbmArgs& A, int i, const int (&
       for (int t = 0; t < 12; ++t) row[t] = 0.0f;
     }
     row[12] = __int_as_float(base);
+    if (BIN) {
+      const int r = base & 7;
+      row[16] = __int_as_float(r | (atomicAdd(&cnt[r], 1) << 3));
+    }
   }
 }
 
@@ -568,9 +584,11 @@ template <int SC, int MODE>
 __global__ void __launch_bounds__(kMdf3Threads, 2) ibm_interp3_kernel(IbmArgs A, int m) {
   extern __shared__ __align__(16) float sm3[];
   const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int S = SC ? SC : A.box, Py = box3_pitch(S), Pz = Py * S, cells = Pz * S;
+  const int S = SC ? SC : A.box, Py = box3_pitch(S), Pz = box3_plane(S), cells = Pz * S;
   float* box = sm3;                          // [3][cells]
   float* tab = sm3 + 3 * cells;              // [nl][kTab3]
+  int* perm = reinterpret_cast<int*>(tab + (size_t)kTab3 * A.nl);  // [nl] points by residue
+  int* cnt = perm + A.nl;                    // [8] points per residue
   const float4* us4 = reinterpret_cast<const float4*>(A.ustar);
   const float4* fib4 = reinterpret_cast<const float4*>(A.fib);
   const int nn[3] = {A.g.nx, A.g.ny, A.g.nz};
@@ -591,11 +609,12 @@ __global__ void __launch_bounds__(kMdf3Threads, 2) ibm_interp3_kernel(IbmArgs A,
   // 1. stage the box: from the staging list where the box lies inside the domain, else
   //    the marked ball of the box, kRows3 rows per warp and round.  The 3-point delta's
   //    fourth (zero-weight) node is staged by neither: the box starts from zero then.
+  if (tid < 8) cnt[tid] = 0;
   if (A.delta_kind == 3) {
     const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     for (int q = tid; q < 3 * cells / 4; q += kMdf3Threads) reinterpret_cast<float4*>(box)[q] = z4;
-    __syncthreads();
   }
+  __syncthreads();
   if (inside) {
     const float cen[3] = {(float)(an[0] - org[0]) + fr[0], (float)(an[1] - org[1]) + fr[1],
                           (float)(an[2] - org[2]) + fr[2]};
@@ -643,15 +662,43 @@ __global__ void __launch_bounds__(kMdf3Threads, 2) ibm_interp3_kernel(IbmArgs A,
         box[2 * cells + cell[u]] = v[u].z;
       }
   }
-  mdf3_table(A, i, org, S, Py, Pz, tab);
+  mdf3_table<true>(A, i, org, S, Py, Pz, tab, cnt);
   __syncthreads();
 
-  // 2. interpolation: warp w takes points 8 (w + kMdf3Warps j) + slot, four lanes a
-  //    point, lane sz of the point the 16 support nodes of z level sz
+  // 2. interpolation, four lanes a point (lane sz: the 16 support nodes of z level sz)
+  //    and eight points a warp.  Lanes sz of a point read the banks of one residue
+  //    class modulo 8, the residue of its first cell, so the eight points of a warp come
+  //    one from each residue: round j takes the j-th point of every residue's list (the
+  //    lists in point order; a residue with fewer points leaves its lanes idle), and
+  //    every shared-memory load of the round falls on 32 distinct banks.
+  int first_r = 0, rounds = 0;  // this lane's residue list: start, and the most points of any
   const int slot = lane >> 2, sz = lane & 3;
-  for (int p0 = 8 * warp; p0 < A.nl; p0 += 8 * kMdf3Warps) {
-    const int p = p0 + slot;
-    const bool act = p < A.nl;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int c = cnt[r];
+    first_r += r < slot ? c : 0;
+    rounds = max(rounds, c);
+  }
+  {
+    int start[8], acc = 0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      start[r] = acc;
+      acc += cnt[r];
+    }
+    for (int k = tid; k < A.nl; k += kMdf3Threads) {
+      const int v = __float_as_int(tab[(size_t)k * kTab3 + 16]);
+      int at = v >> 3;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) at += (v & 7) == r ? start[r] : 0;
+      perm[at] = k;
+    }
+  }
+  const int n_r = cnt[slot];
+  __syncthreads();
+  for (int j = warp; j < rounds; j += kMdf3Warps) {
+    const bool act = j < n_r;
+    const int p = act ? perm[first_r + j] : 0;
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
     if (act) {
       const float* row = tab + (size_t)p * kTab3;
@@ -683,7 +730,7 @@ __global__ void __launch_bounds__(kMdf3Threads, 2) ibm_interp3_kernel(IbmArgs A,
       a2 += __shfl_xor_sync(0xffffffffu, a2, o);
     }
     if (act && sz == 0) {  // u_b into the table
-      float* row = tab + (size_t)p * kTab3;
+      float* row = tab + (size_t)p * kTab3;  // (row[16] is not read again)
       row[13] = a0;
       row[14] = a1;
       row[15] = a2;
@@ -730,7 +777,7 @@ template <int SC>
 __global__ void __launch_bounds__(kMdf3Threads) ibm_spread3_kernel(IbmArgs A) {
   extern __shared__ __align__(16) float sm3[];
   const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int S = SC ? SC : A.box, Py = box3_pitch(S), Pz = Py * S, cells = Pz * S;
+  const int S = SC ? SC : A.box, Py = box3_pitch(S), Pz = box3_plane(S), cells = Pz * S;
   int* boxi = reinterpret_cast<int*>(sm3);   // [3][cells]
   float* tab = sm3 + 3 * cells;              // [nl][kTab3]
   float* red = tab + (size_t)kTab3 * A.nl;   // [32] reduction scratch
@@ -744,7 +791,7 @@ __global__ void __launch_bounds__(kMdf3Threads) ibm_spread3_kernel(IbmArgs A) {
     const int4 z = make_int4(0, 0, 0, 0);
     for (int q = tid; q < 3 * cells / 4; q += kMdf3Threads) b4[q] = z;
   }
-  mdf3_table(A, i, org, S, Py, Pz, tab);
+  mdf3_table<false>(A, i, org, S, Py, Pz, tab, nullptr);
   float mx = 0.0f;
   for (int k = tid; k < A.nl; k += kMdf3Threads) {
     const long long b = (long long)i * A.nl + k;

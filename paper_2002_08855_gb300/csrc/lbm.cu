@@ -802,6 +802,22 @@ __global__ void __launch_bounds__(kLbmBlock) lbm_step_edge_kernel(LbmArgs A0, lo
   step_edge_body<L, ST>(A, nface, nends, blk);
 }
 
+// An odd step of one run in one launch: the row tiles of lbm_step_kernel and the edge
+// nodes (face rows, row ends), with the edge blocks spread evenly through the grid
+// (one every `stride` blocks from block 0), so their scattered, latency-bound accesses
+// run beside the bandwidth-bound row tiles instead of after them.  No node of one set
+// reads or writes a slot of the other (an AA step swaps each node's own slots).
+template <class L, int ST, int K>
+__global__ void __launch_bounds__(kLbmBlock, L::dim == 3 ? 7 : 10)
+    lbm_step_odd_kernel(LbmArgs A, int spr, unsigned eblocks, unsigned stride, long long nface, long long nends) {
+  const unsigned b = blockIdx.x, q = b / stride;
+  if (b - q * stride == 0 && q < eblocks) {
+    step_edge_body<L, ST>(A, nface, nends, q);
+    return;
+  }
+  step_tile_body<L, 1, ST, K>(A, spr, b - min(eblocks, q + 1));
+}
+
 // An odd step of a 2D batch in one launch: blocks [0, blocks) are the members' row
 // tiles, the rest their face rows and row ends.  No node of one set reads or writes a
 // slot of the other (an AA step swaps each node's own slots), so both run together.
@@ -1084,16 +1100,6 @@ static void launch_step_main(const LbmArgs& A, cudaStream_t s) {
   lbm_step_kernel<L, PARITY, ST, K, false><<<grid, kLbmBlock, 0, s>>>(A, spr, Fuse{});
 }
 
-template <class L, int ST>
-static void launch_step_edge(const LbmArgs& A, cudaStream_t s) {
-  long long nface, nends;
-  edge_counts(A.g, L::dim, nface, nends);
-  const long long total = nface * A.g.nx + nends;
-  if (total == 0) return;
-  const dim3 grid((unsigned)((total + kLbmBlock - 1) / kLbmBlock));
-  lbm_step_edge_kernel<L, ST, false><<<grid, kLbmBlock, 0, s>>>(A, nface, nends, Fuse{});
-}
-
 // fused over the members of a 2D batch (FP32 or FP16 storage, one for all members)
 cudaError_t launch_lbm_step_fused(const Fuse& F, unsigned blocks, const Fuse& FE, unsigned eblocks,
                                   int store, int parity, cudaStream_t s) {
@@ -1207,20 +1213,27 @@ cudaError_t launch_lbm_nee(const LbmArgs& A, int D, int parity, cudaStream_t s) 
   return cudaGetLastError();
 }
 
-// kernels launch_lbm_step launches: the vector kernel alone, or the row kernel and in
-// an odd step the edge kernel
-int lbm_step_launches(const Geo& g, int D, int parity, int store) {
-  if (parity == 0 || lbm_step_vector(g, D, store)) return 1;
-  const long long faces = D == 2 ? (g.ny > 1 ? 2 : 1)
-                                 : (long long)g.ny * (g.nz > 1 ? 2 : 1) +
-                                       (long long)(g.nz > 2 ? g.nz - 2 : 0) * (g.ny > 1 ? 2 : 1);
-  return faces * g.nx > 0 ? 2 : 1;
-}
+// kernels launch_lbm_step launches: one (the vector kernel, the row kernel, or in an odd
+// step the row kernel with the edge nodes)
+int lbm_step_launches(const Geo&, int, int, int) { return 1; }
 
 template <class L, int PARITY, int ST>
 static void launch_step_one(const LbmArgs& A, cudaStream_t s) {
+  if (PARITY == 1 && !use_vec<L, ST>(A.g)) {
+    long long nface, nends;
+    edge_counts(A.g, L::dim, nface, nends);
+    const long long total = nface * A.g.nx + nends;
+    if (total > 0) {
+      constexpr int K = step_k<ST>();
+      const int spr = (A.g.nx + K * kLbmBlock - 1) / (K * kLbmBlock);
+      const unsigned main = (unsigned)((long long)spr * A.g.rows);
+      const unsigned eb = (unsigned)((total + kLbmBlock - 1) / kLbmBlock);
+      const unsigned stride = (main + eb) / eb;
+      lbm_step_odd_kernel<L, ST, K><<<main + eb, kLbmBlock, 0, s>>>(A, spr, eb, stride, nface, nends);
+      return;
+    }
+  }
   launch_step_main<L, PARITY, ST>(A, s);
-  if (PARITY == 1 && !use_vec<L, ST>(A.g)) launch_step_edge<L, ST>(A, s);
 }
 
 template <class L, int PARITY>
