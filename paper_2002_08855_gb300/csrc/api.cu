@@ -89,7 +89,7 @@ struct Layout {
   size_t f, ustar, fib, mask;
   size_t X0, X1, U, Om, Fh, Th, FhN, ThN, acc, alp, Pint, Lint, Pprev, Lprev, Fc;
   size_t Uf, Omf, ref_fix, ref_f, Xcf, Xb0, Xb1, Ub0, Ub1, Fb, dFb, ubs, ubox, res, mlp, mlp_img;
-  size_t frame3, nbr3, slist;
+  size_t frame3, nbr3, slist, order;
   size_t cell_count, cell_ids, nbr, nbr_count, gt, pairs, status;
   size_t grid, over, over_count;
   size_t total;
@@ -290,6 +290,7 @@ Layout carve(const ibm_lbm_config* c, const Derived& d) {
   l.slist = cv.take(sizeof(int) * (size_t)d.slen);  // 3D staging list of the node box
   // 2D: u* of each particle's node box (box rows of box_pitch(box) float2 cells)
   l.ubox = cv.take(D == 2 ? sizeof(float) * np * 2 * (size_t)d.box * box_pitch(d.box) : 0);
+  l.order = cv.take(D == 2 ? sizeof(int) * np : 0);  // 2D IBM processing order
   const size_t ncells = (size_t)d.nc[0] * d.nc[1] * d.nc[2];
   l.cell_count = cv.take(sizeof(int) * ncells);
   l.cell_ids = cv.take(sizeof(int) * ncells * cell_capacity(c->n_particles, (long long)ncells));
@@ -447,6 +448,7 @@ struct ibm_lbm_handle {
     a.store = cfg.pdf_storage;
     a.parity = parity;
     a.ubox = at<float>(l.ubox);
+    a.order = at<int>(l.order);
     a.Xb = at<long long>(parity ? l.Xb1 : l.Xb0);
     a.Ub = at<float>(parity ? l.Ub1 : l.Ub0);
     a.Fb = at<float>(l.Fb);
@@ -679,8 +681,32 @@ int capture_graph(ibm_lbm_handle* h, int parity) {
 }
 
 // points and node marks of the current state (after init or a new particle state)
+// 2D: the order in which the IBM kernels' warps take the particles, by centre height
+// from the top.  lbm_step walks the rows upwards, so the top rows are the last it
+// wrote and the likeliest to be still in L2 when the next step's first interpolation
+// reads the PDFs around the particles (the next lbm_step then starts on the bottom rows
+// that the interpolation read last).  Set from the centres whenever they are set; the
+// particles move little between settings, and any order gives the same results.
+int refresh_order(ibm_lbm_handle* h) {
+  const int np = h->cfg.n_particles;
+  if (h->d.D != 2 || np == 0) return IBMLBM_OK;
+  std::vector<double> X((size_t)np * 2);
+  CUDA_TRY(cudaMemcpyAsync(X.data(), h->X((int)(h->step & 1)), sizeof(double) * X.size(),
+                           cudaMemcpyDeviceToHost, h->s));
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  std::vector<int> order((size_t)np);
+  for (int i = 0; i < np; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return X[2 * (size_t)a + 1] > X[2 * (size_t)b + 1]; });
+  CUDA_TRY(cudaMemcpyAsync(h->at<int>(h->l.order), order.data(), sizeof(int) * order.size(),
+                           cudaMemcpyHostToDevice, h->s));
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  return IBMLBM_OK;
+}
+
 int regenerate_points(ibm_lbm_handle* h) {
   if (h->cfg.n_particles == 0) return IBMLBM_OK;
+  const int rc = refresh_order(h);
+  if (rc) return rc;
   CUDA_TRY(clear_mask(h, (int)(h->step & 1), h->s));
   CUDA_TRY(launch_regen(h->regen((int)(h->step & 1)), 1, h->s));
   h->launches += 1;

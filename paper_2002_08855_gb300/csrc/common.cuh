@@ -214,6 +214,7 @@ struct IbmArgs {
   int store;             // their storage (STORE_F32, STORE_F16, STORE_BF16)
   int parity;            // 2D: AA parity of the PDFs
   float* ubox;           // 2D: [np][box][box_pitch(box)] float2, u* of each particle's box
+  const int* order;      // 2D: the particle each warp slot of the IBM kernels takes
   const long long* Xb;  // [npts][D] fixed point
   const float* Ub;   // [npts][D]
   float* Fb;         // [npts][D] sum of MDF increments

@@ -150,8 +150,9 @@ template <int SC, int PARITY, int MODE, int ST>
 __device__ __forceinline__ void interp2_body(const IbmArgs& A, int m, unsigned blk, int wf = 0) {
   extern __shared__ __align__(16) float smem_i[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int i = (int)blk * (int)(blockDim.x >> 5) + wib;  // warps per block: blockDim
-  if (i >= A.np) return;  // whole warp
+  const int slot = (int)blk * (int)(blockDim.x >> 5) + wib;  // warps per block: blockDim
+  if (slot >= A.np) return;  // whole warp
+  const int i = A.order[slot];
   const int S = SC ? SC : A.box, P = box_pitch(S), cells = S * P;
   __syncwarp();  // the warp's shared memory is free (a particle before may have used it)
   float2* box = reinterpret_cast<float2*>(smem_i + (size_t)wib * (wf ? wf : interp2_warp_floats(MODE, S)));
@@ -311,8 +312,9 @@ template <int SC>
 __device__ __forceinline__ void spread2_body(const IbmArgs& A, unsigned blk, int wf = 0) {
   extern __shared__ __align__(16) float smem2[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int i = (int)blk * (int)(blockDim.x >> 5) + wib;  // warps per block: blockDim
-  if (i >= A.np) return;  // whole warp
+  const int slot = (int)blk * (int)(blockDim.x >> 5) + wib;  // warps per block: blockDim
+  if (slot >= A.np) return;  // whole warp
+  const int i = A.order[slot];
   const int S = SC ? SC : A.box, P = box_pitch(S), cells = S * P;
   __syncwarp();  // the warp's shared memory is free (a particle before may have used it)
   float* base = smem2 + (size_t)wib * (wf ? wf : spread2_warp_floats(S));
@@ -1158,11 +1160,11 @@ __device__ __forceinline__ void forces2_body(const IbmArgs& A, unsigned blk) {
   constexpr int NB = LP == 16 ? (SC ? 5 : 9) : kForceBatch;
   const unsigned gt = blk * blockDim.x + threadIdx.x;
   if ((int)((gt & ~31u) / LP) >= A.np) return;  // the warp's first particle: whole warp
-  const int i = (int)(gt / LP);
+  const int slot = (int)(gt / LP);
   const int lane = (int)(gt & (LP - 1));
-  const bool valid = i < A.np;  // (the second half-warp of the last warp may have none)
+  const bool valid = slot < A.np;  // (the second half-warp of the last warp may have none)
   const int S = SC ? SC : A.box, W = box_pitch(S), cells = S * W, ext = S - 4;  // ext = 2 rcell + 2
-  const int ic = valid ? i : 0;
+  const int i = valid ? A.order[slot] : 0, ic = i;
   const long long vx = A.Xcf[(long long)ic * 2], vy = A.Xcf[(long long)ic * 2 + 1];
   const int anx = fix_anchor(vx), any = fix_anchor(vy);
   const float frx = fix_frac(vx), fry = fix_frac(vy);
