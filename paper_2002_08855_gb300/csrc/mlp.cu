@@ -242,6 +242,104 @@ __device__ __forceinline__ void mlp_rows(const InferSmem& S, const __half* xs, i
   }
 }
 
+// The three layers for 32 feature rows (two m16 tiles, rows t * 16 + r of xs): every B
+// fragment read from shared memory feeds both tiles.  The first layer's outputs are
+// packed to the second layer's A fragments right away (half the registers of the FP32
+// accumulators), and the third layer takes the second layer's columns two n-tiles at a
+// time, so the second layer's accumulators are never all live.  o[t]: the outputs of
+// rows t * 16 + gid and t * 16 + gid + 8 at columns 2 tig, 2 tig + 1.
+__device__ __forceinline__ void mlp_rows32(const WeightImage& W, const __half* xs, int lane, float (&o)[2][4]) {
+  const int gid = lane >> 2, tig = lane & 3;
+  uint32_t a2[2][kK2 / 16][4];  // layer 2 A fragments (ReLU of layer 1, FP16)
+  {
+    float h[2][8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const float c0 = W.b1[nt * 8 + tig * 2], c1 = W.b1[nt * 8 + tig * 2 + 1];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        h[t][nt][0] = c0;
+        h[t][nt][1] = c1;
+        h[t][nt][2] = c0;
+        h[t][nt][3] = c1;
+      }
+    }
+#pragma unroll
+    for (int kb = 0; kb < kK1 / 16; ++kb) {
+      uint32_t a[2][4];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const __half* r0 = xs + (t * 16 + gid) * kXP + kb * 16 + tig * 2;
+        const __half* r1 = r0 + 8 * kXP;
+        a[t][0] = *reinterpret_cast<const uint32_t*>(r0);
+        a[t][1] = *reinterpret_cast<const uint32_t*>(r1);
+        a[t][2] = *reinterpret_cast<const uint32_t*>(r0 + 8);
+        a[t][3] = *reinterpret_cast<const uint32_t*>(r1 + 8);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        uint32_t b0, b1;
+        b_frag(W.w1, kP1, kb, nt, lane, b0, b1);
+#pragma unroll
+        for (int t = 0; t < 2; ++t) mma16816(h[t][nt], a[t][0], a[t][1], a[t][2], a[t][3], b0, b1);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+      for (int kb = 0; kb < kK2 / 16; ++kb) {
+        a2[t][kb][0] = pack_half2(fmaxf(h[t][2 * kb][0], 0.f), fmaxf(h[t][2 * kb][1], 0.f));
+        a2[t][kb][1] = pack_half2(fmaxf(h[t][2 * kb][2], 0.f), fmaxf(h[t][2 * kb][3], 0.f));
+        a2[t][kb][2] = pack_half2(fmaxf(h[t][2 * kb + 1][0], 0.f), fmaxf(h[t][2 * kb + 1][1], 0.f));
+        a2[t][kb][3] = pack_half2(fmaxf(h[t][2 * kb + 1][2], 0.f), fmaxf(h[t][2 * kb + 1][3], 0.f));
+      }
+  }
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    o[t][0] = W.b3[tig * 2];
+    o[t][1] = W.b3[tig * 2 + 1];
+    o[t][2] = o[t][0];
+    o[t][3] = o[t][1];
+  }
+  // layer 2 by pairs of n-tiles (2 k3, 2 k3 + 1), each pair then one k-block of layer 3
+#pragma unroll
+  for (int k3 = 0; k3 < kK2 / 16; ++k3) {
+    float g[2][2][4];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int nt = 2 * k3 + q;
+      const float c0 = W.b2[nt * 8 + tig * 2], c1 = W.b2[nt * 8 + tig * 2 + 1];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        g[t][q][0] = c0;
+        g[t][q][1] = c1;
+        g[t][q][2] = c0;
+        g[t][q][3] = c1;
+      }
+    }
+#pragma unroll
+    for (int kb = 0; kb < kK2 / 16; ++kb)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        uint32_t b0, b1;
+        b_frag(W.w2, kP2, kb, 2 * k3 + q, lane, b0, b1);
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+          mma16816(g[t][q], a2[t][kb][0], a2[t][kb][1], a2[t][kb][2], a2[t][kb][3], b0, b1);
+      }
+    uint32_t b0, b1;
+    b_frag(W.w3, kP2, k3, 0, lane, b0, b1);
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const uint32_t x0 = pack_half2(fmaxf(g[t][0][0], 0.f), fmaxf(g[t][0][1], 0.f));
+      const uint32_t x1 = pack_half2(fmaxf(g[t][0][2], 0.f), fmaxf(g[t][0][3], 0.f));
+      const uint32_t x2 = pack_half2(fmaxf(g[t][1][0], 0.f), fmaxf(g[t][1][1], 0.f));
+      const uint32_t x3 = pack_half2(fmaxf(g[t][1][2], 0.f), fmaxf(g[t][1][3], 0.f));
+      mma16816(o[t], x0, x1, x2, x3, b0, b1);
+    }
+  }
+}
+
 // Inference on an array of feature rows X [n][27] -> Y [n][3] (testing the kernel).
 __global__ void __launch_bounds__(kInferWarps * 32) mlp_infer_kernel(const float* __restrict__ P,
                                                                     const float* __restrict__ X, long long n,
@@ -280,15 +378,18 @@ __global__ void __launch_bounds__(kInferWarps * 32) mlp_infer_kernel(const float
 // In a time step, after the first interpolation: the first MDF force of every point is
 // the network's prediction from its deficit stencil (replacing 2 (U_b - u_b*)).  One
 // warp per particle: the particle's deficits are staged in shared memory once, then
-// its points go through the network 16 at a time.
+// its points go through the network 32 at a time (two m16 tiles sharing every weight
+// fragment), lane r building the feature row of point r of the pass and storing it as
+// four 16-byte words.
 constexpr int kMaxNl = 256;  // points per particle the step kernel stages
 
 __global__ void __launch_bounds__(kInferWarps * 32) mlp_step_kernel(IbmArgs A, const float* __restrict__ P,
                                                                    const WeightImage* __restrict__ img) {
-  __shared__ InferSmem S;
+  __shared__ WeightImage W;
+  __shared__ __align__(16) __half xs32[kInferWarps][32 * kXP];  // the 32 feature rows of a pass
   __shared__ float dsm[kInferWarps][2 * kMaxNl];
   __shared__ float frame[2 * kMaxNl];
-  copy_image(S.W, img);
+  copy_image(W, img);
   for (int k = threadIdx.x; k < A.nl; k += blockDim.x) {
     float nx, ny;
     point_frame(A.ref_f, k, nx, ny);
@@ -300,54 +401,82 @@ __global__ void __launch_bounds__(kInferWarps * 32) mlp_step_kernel(IbmArgs A, c
   const int gid = lane >> 2, tig = lane & 3;
   const float ins = P[oInS], outs = P[oOutS];
   const int nl = A.nl;
-  __half* xs = S.x[w];
+  __half* xs = xs32[w];
   float* d = dsm[w];
-  for (int i = blockIdx.x * kInferWarps + w; i < A.np; i += gridDim.x * kInferWarps) {
+  // up to 32 points a particle: lane k holds point k's deficit of the warp's next
+  // particle, loaded while the network runs on the current one
+  const int stride = gridDim.x * kInferWarps;
+  const bool pre = nl <= 32;
+  float nxt[2] = {0.0f, 0.0f};
+  auto fetch = [&](int i) {
+    if (!pre || i >= A.np || lane >= nl) return;
+    const long long b = (long long)i * nl + lane;
+    const float2 U = reinterpret_cast<const float2*>(A.Ub)[b], u = reinterpret_cast<const float2*>(A.ubs)[b];
+    nxt[0] = U.x - u.x;
+    nxt[1] = U.y - u.y;
+  };
+  fetch(blockIdx.x * kInferWarps + w);
+  for (int i = blockIdx.x * kInferWarps + w; i < A.np; i += stride) {
     const long long base = (long long)i * nl;
-    for (int k = lane; k < nl; k += 32) {
-      const long long b = base + k;
-      d[2 * k] = A.Ub[2 * b] - A.ubs[2 * b];
-      d[2 * k + 1] = A.Ub[2 * b + 1] - A.ubs[2 * b + 1];
+    if (pre) {
+      if (lane < nl) {
+        d[2 * lane] = nxt[0];
+        d[2 * lane + 1] = nxt[1];
+      }
+      fetch(i + stride);
+    } else {
+      for (int k = lane; k < nl; k += 32) {
+        const long long b = base + k;
+        d[2 * k] = A.Ub[2 * b] - A.ubs[2 * b];
+        d[2 * k + 1] = A.Ub[2 * b + 1] - A.ubs[2 * b + 1];
+      }
     }
     __syncwarp();
-    for (int r0 = 0; r0 < nl; r0 += 16) {
-      if (lane < 16) {
+    for (int r0 = 0; r0 < nl; r0 += 32) {
+      {
         const int k = r0 + lane;
+        uint32_t wd[kK1 / 2];  // the row as 16 words of two halves
+#pragma unroll
+        for (int q = 0; q < kK1 / 2; ++q) wd[q] = 0u;
         if (k < nl) {
           const float nx = frame[2 * k], ny = frame[2 * k + 1];
+          float x[kIn];
 #pragma unroll
           for (int j = 0; j < 9; ++j) {
             int kk = k + j - 4;
             kk = kk < 0 ? kk + nl : (kk >= nl ? kk - nl : kk);
             const float dx = d[2 * kk], dy = d[2 * kk + 1];
-            xs[lane * kXP + 3 * j] = __float2half_rn((dx * nx + dy * ny) * ins);
-            xs[lane * kXP + 3 * j + 1] = __float2half_rn((-dx * ny + dy * nx) * ins);
-            xs[lane * kXP + 3 * j + 2] = __float2half_rn(0.0f);
+            x[3 * j] = (dx * nx + dy * ny) * ins;
+            x[3 * j + 1] = (-dx * ny + dy * nx) * ins;
+            x[3 * j + 2] = 0.0f;
           }
 #pragma unroll
-          for (int c = kIn; c < kK1; ++c) xs[lane * kXP + c] = __float2half_rn(0.0f);
-        } else {
-#pragma unroll
-          for (int c = 0; c < kK1; ++c) xs[lane * kXP + c] = __float2half_rn(0.0f);
+          for (int q = 0; q < kK1 / 2; ++q)
+            wd[q] = pack_half2(2 * q < kIn ? x[2 * q] : 0.0f, 2 * q + 1 < kIn ? x[2 * q + 1] : 0.0f);
         }
+        uint4* row = reinterpret_cast<uint4*>(xs + lane * kXP);
+#pragma unroll
+        for (int q = 0; q < kK1 / 8; ++q) row[q] = make_uint4(wd[4 * q], wd[4 * q + 1], wd[4 * q + 2], wd[4 * q + 3]);
       }
       __syncwarp();
-      float o[4];
-      mlp_rows(S, xs, lane, o);
+      float o[2][4];
+      mlp_rows32(W, xs, lane, o);
       if (tig == 0) {  // columns 0 and 1: normal and tangential force
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          const int k = r0 + gid + 8 * half;
-          if (k >= nl) continue;
-          const long long b = base + k;
-          const float nx = frame[2 * k], ny = frame[2 * k + 1];
-          const float fn = o[2 * half] * outs, ft = o[2 * half + 1] * outs;
-          const float Fx = fn * nx - ft * ny, Fy = fn * ny + ft * nx;
-          A.dFb[2 * b] = Fx;
-          A.dFb[2 * b + 1] = Fy;
-          A.Fb[2 * b] = Fx;
-          A.Fb[2 * b + 1] = Fy;
-        }
+        for (int t = 0; t < 2; ++t)
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            const int k = r0 + t * 16 + gid + 8 * half;
+            if (k >= nl) continue;
+            const long long b = base + k;
+            const float nx = frame[2 * k], ny = frame[2 * k + 1];
+            const float fn = o[t][2 * half] * outs, ft = o[t][2 * half + 1] * outs;
+            const float Fx = fn * nx - ft * ny, Fy = fn * ny + ft * nx;
+            A.dFb[2 * b] = Fx;
+            A.dFb[2 * b + 1] = Fy;
+            A.Fb[2 * b] = Fx;
+            A.Fb[2 * b + 1] = Fy;
+          }
       }
       __syncwarp();
     }
@@ -548,7 +677,16 @@ cudaError_t launch_mlp_step(const IbmArgs& A, const float* P, const void* img, c
     return cudaGetLastError();
   }
   if (A.np == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)min((A.np + kInferWarps - 1) / kInferWarps, 152 * 4);
+  static int resident = 0;  // blocks the GPU holds at once: each warp then walks its particles
+  if (resident == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_step_kernel, kInferWarps * 32, 0);
+    if (e != cudaSuccess) return e;
+    resident = std::max(1, sms * per_sm);
+  }
+  const unsigned grid = (unsigned)std::min((A.np + kInferWarps - 1) / kInferWarps, resident);
   mlp_step_kernel<<<grid, kInferWarps * 32, 0, s>>>(A, P, static_cast<const WeightImage*>(img));
   return cudaGetLastError();
 }

@@ -109,6 +109,30 @@ def test_initializer_lowers_the_mdf_residual():
     assert res[1] < res[0]
 
 
+@pytest.mark.parametrize("n_lag", [31, 50, 12])
+def test_step_2d_starts_from_the_network_prediction(n_lag):
+    """With mdf_iters = 1 and the learned start, F_b of the step is the prediction of the
+    tensor-core network (FP16 operands) from the step's stencils, rotated from each
+    point's (normal, tangent) frame: 31 points fill the two 16-row tiles of a pass but
+    one row, 50 take a second, ragged pass, 12 leave most rows empty."""
+    require_gpu()
+    from paper_2002_08855_gb300 import mlp
+    from paper_2002_08855_gb300.binding import Simulation
+
+    w = _workload(33, n=20, mlp_init=1, fixed_particles=1).with_(n_lag=n_lag, mdf_iters=1)
+    p = mlp.init_params(7)
+    p[-2], p[-1] = 200.0, 1e-3  # in_scale, out_scale of the deficits' size
+    sim = Simulation(w, place_particles(w))
+    sim.set_mlp(p)
+    sim.step(2)
+    lg = sim.get_lagrangian()
+    Fl = mlp_ref.predict(p, mlp_ref.features_2d(lg["U_b"], lg["u_b_star"], w.n_lag))
+    th = 2 * np.pi * (np.arange(len(Fl)) % w.n_lag) / w.n_lag
+    F = np.stack([Fl[:, 0] * np.cos(th) - Fl[:, 1] * np.sin(th), Fl[:, 0] * np.sin(th) + Fl[:, 1] * np.cos(th)], 1)
+    assert rel_l2(lg["F_b"], F) < 2e-2
+    sim.close()
+
+
 # ---------------------------------------------------------------- spheres (3D)
 def _workload3(seed, n=12, side=56, **kw):
     kw = {"mdf_iters": 3, **kw}
