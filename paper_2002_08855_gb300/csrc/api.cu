@@ -390,9 +390,9 @@ struct ibm_lbm_handle {
   char* ws;
   cudaStream_t s;
   // second stream for the particle work that runs beside lbm_step, and the events
-  // that fork it from and join it back into s
+  // that fork it from and join it back into s (fork0: at the start of a step)
   cudaStream_t side;
-  cudaEvent_t fork, join;
+  cudaEvent_t fork0, fork, join;
   bool mlp_set;     // learned-initializer parameters copied in
   bool track_res;   // residual pass after the last MDF iteration
   long long res_step;  // step whose residual the buffer holds (-1: none)
@@ -578,7 +578,18 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
   int k = 0;
   const LbmArgs la = h->lbm(parity);
   const IbmArgs ia = h->ibm(parity);
+  const PairArgs pa = h->pairs(parity, have_prev);
   if (ev) CUDA_TRY(cudaEventRecord(ev[0], s));
+  if (particles && !ev) {
+    // The cell lists and partner lists need only this step's centres: they are built
+    // on the side stream beside the IBM kernels (all latency-bound, so they share the
+    // SMs well), which leaves only the forces and the update beside lbm_step.
+    CUDA_TRY(cudaEventRecord(h->fork0, s));
+    CUDA_TRY(cudaStreamWaitEvent(h->side, h->fork0, 0));
+    CUDA_TRY(launch_pair_cells(pa, h->side));
+    CUDA_TRY(launch_pair_search_lists(pa, h->side));
+    k += 2;
+  }
   if (particles && h->d.D == 3) {  // 2D computes u* per particle box in the first interpolation
     CUDA_TRY(launch_lbm_moments(la, h->d.D, parity, s));
     ++k;
@@ -614,10 +625,8 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
     // lbm_step streams the PDFs.
     CUDA_TRY(cudaEventRecord(h->fork, s));
     CUDA_TRY(cudaStreamWaitEvent(h->side, h->fork, 0));
-    const PairArgs pa = h->pairs(parity, have_prev);
-    CUDA_TRY(launch_pair_cells(pa, h->side));
-    CUDA_TRY(launch_pair_contacts(pa, h->side));
-    k += 3;
+    CUDA_TRY(launch_pair_forces(pa, h->side));
+    k += 1;
     CUDA_TRY(clear_mask(h, 1 - parity, h->side));
     CUDA_TRY(launch_regen(h->regen(1 - parity), 0, h->side));
     ++k;
@@ -637,7 +646,6 @@ int enqueue_step(ibm_lbm_handle* h, int parity, int have_prev, cudaEvent_t* ev, 
   k += h->cfg.boundary ? 1 : 0;
   if (ev) CUDA_TRY(cudaEventRecord(ev[3], s));
   if (particles) {
-    const PairArgs pa = h->pairs(parity, have_prev);
     CUDA_TRY(launch_pair_cells(pa, s));
     CUDA_TRY(launch_pair_contacts(pa, s));
     k += 3;
@@ -781,12 +789,13 @@ int ibm_lbm_init(const ibm_lbm_config* cfg, void* d_workspace, size_t bytes, voi
   h->graph_ok[0] = h->graph_ok[1] = false;
   h->graph_tried[0] = h->graph_tried[1] = false;
   h->side = nullptr;
-  h->fork = h->join = nullptr;
+  h->fork0 = h->fork = h->join = nullptr;
   h->mlp_set = false;
   h->track_res = false;
   h->res_step = -1;
   auto bail = [&](int code) {
     if (h->side) cudaStreamDestroy(h->side);
+    if (h->fork0) cudaEventDestroy(h->fork0);
     if (h->fork) cudaEventDestroy(h->fork);
     if (h->join) cudaEventDestroy(h->join);
     delete h;
@@ -807,6 +816,7 @@ int ibm_lbm_init(const ibm_lbm_config* cfg, void* d_workspace, size_t bytes, voi
     INIT_TRY(cudaDeviceGetStreamPriorityRange(&lo_, &hi_));
     INIT_TRY(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi_));
   }
+  INIT_TRY(cudaEventCreateWithFlags(&h->fork0, cudaEventDisableTiming));
   INIT_TRY(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
   INIT_TRY(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
   if (cfg->n_particles > 0) {
@@ -1296,6 +1306,7 @@ void ibm_lbm_destroy(ibm_lbm_handle* h) {
     cudaStreamSynchronize(h->side);
     cudaStreamDestroy(h->side);
   }
+  if (h->fork0) cudaEventDestroy(h->fork0);
   if (h->fork) cudaEventDestroy(h->fork);
   if (h->join) cudaEventDestroy(h->join);
   delete h;

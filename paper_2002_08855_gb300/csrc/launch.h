@@ -35,6 +35,8 @@ cudaError_t launch_regen(const RegenArgs& A, int init, cudaStream_t s);
 // pair search: cell buckets, neighbour lists, contact forces (and the particle update)
 cudaError_t launch_pair_cells(const PairArgs& A, cudaStream_t s);   // memset + 1 kernel
 cudaError_t launch_pair_contacts(const PairArgs& A, cudaStream_t s);
+cudaError_t launch_pair_search_lists(const PairArgs& A, cudaStream_t s);  // partner lists only
+cudaError_t launch_pair_forces(const PairArgs& A, cudaStream_t s);        // forces (and update)
 cudaError_t launch_pair_compact(const PairArgs& A, int* pairs, long long cap, cudaStream_t s);
 cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t s);
 

@@ -510,6 +510,25 @@ cudaError_t launch_pair_cells(const PairArgs& A, cudaStream_t s) {
 
 // neighbour lists (warp per particle), then, when A.Fc is set, contact forces and the
 // particle update (thread per particle)
+// the partner lists alone (no force): they need only this step's centres, so a step
+// can search beside its IBM kernels and leave the forces for later
+cudaError_t launch_pair_search_lists(const PairArgs& A, cudaStream_t s) {
+  PairArgs L = A;
+  L.Fc = nullptr;
+  return launch_pair_contacts(L, s);
+}
+
+// the forces of the partner lists (and, in a step, the particle update)
+cudaError_t launch_pair_forces(const PairArgs& A, cudaStream_t s) {
+  if (A.n == 0 || !A.Fc) return cudaSuccess;
+  const unsigned g = blocks_for(A.n, 128);
+  if (A.D == 2)
+    pair_force_kernel<2, false><<<g, 128, 0, s>>>(A, Fuse{});
+  else
+    pair_force_kernel<3, false><<<g, 128, 0, s>>>(A, Fuse{});
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pair_contacts(const PairArgs& A, cudaStream_t s) {
   if (A.n == 0) return cudaSuccess;
   const unsigned gw = blocks_for((long long)A.n * 32, 256);
