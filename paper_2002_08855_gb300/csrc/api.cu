@@ -1550,7 +1550,7 @@ struct ibm_lbm_batch {
   std::vector<ibm_lbm_handle*> m;
   cudaStream_t s;
   cudaStream_t side;
-  cudaEvent_t fork, join;
+  cudaEvent_t fork0, fork, join;
   bool mlp_set;     // learned-initializer parameters copied in
   bool track_res;   // residual pass after the last MDF iteration
   long long res_step;  // step whose residual the buffer holds (-1: none)
@@ -1656,6 +1656,13 @@ int enqueue_batch_step(ibm_lbm_batch* b, int parity, int have_prev, int* nk, cud
     ++k;
     CUDA_TRY(cudaEventRecord(b->join, b->side));
   } else if (B[BK_WARP]) {
+    // cell and partner lists beside the IBM kernels (they need only the step's centres)
+    const void* pa = b->pair_args[parity][have_prev];
+    CUDA_TRY(cudaEventRecord(b->fork0, s));
+    CUDA_TRY(cudaStreamWaitEvent(b->side, b->fork0, 0));
+    CUDA_TRY(launch_pairs_fused(fuse(b, BK_PCLEAR, pa), B[BK_PCLEAR], fuse(b, BK_PINS, pa), B[BK_PINS],
+                                fuse(b, BK_PSEARCH, pa), B[BK_PSEARCH], fuse(b, BK_PFORCE, pa), 0, b->side));
+    k += 3;
     int rc;
     if (b->mdf == 0 && (rc = phase(false, 0)) != IBMLBM_OK) return rc;
     for (int m = 1; m <= b->mdf; ++m) {
@@ -1664,14 +1671,13 @@ int enqueue_batch_step(ibm_lbm_batch* b, int parity, int have_prev, int* nk, cud
     }
     CUDA_TRY(launch_ibm_forces_fused(fuse(b, BK_LANE, ia), B[BK_LANE], s));
     ++k;
-    // contacts, particle update and regeneration beside the collision (as in a single run)
+    // contact forces, particle update and regeneration beside the collision (as in a
+    // single run)
     CUDA_TRY(cudaEventRecord(b->fork, s));
     CUDA_TRY(cudaStreamWaitEvent(b->side, b->fork, 0));
-    const void* pa = b->pair_args[parity][have_prev];
-    CUDA_TRY(launch_pairs_fused(fuse(b, BK_PCLEAR, pa), B[BK_PCLEAR], fuse(b, BK_PINS, pa), B[BK_PINS],
-                                fuse(b, BK_PSEARCH, pa), B[BK_PSEARCH], fuse(b, BK_PFORCE, pa),
-                                B[BK_PFORCE], b->side));
-    k += 4;
+    CUDA_TRY(launch_pairs_fused(fuse(b, BK_PCLEAR, pa), 0, fuse(b, BK_PINS, pa), 0, fuse(b, BK_PSEARCH, pa), 0,
+                                fuse(b, BK_PFORCE, pa), B[BK_PFORCE], b->side));
+    k += 1;
     CUDA_TRY(launch_regen_fused(fuse(b, BK_LANE, b->regen_args[1 - parity]), B[BK_LANE], b->side));
     ++k;
     CUDA_TRY(cudaEventRecord(b->join, b->side));
@@ -1726,6 +1732,7 @@ void destroy_batch(ibm_lbm_batch* b) {
     cudaStreamSynchronize(b->side);
     cudaStreamDestroy(b->side);
   }
+  if (b->fork0) cudaEventDestroy(b->fork0);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->join) cudaEventDestroy(b->join);
   for (int c = 0; c < kMaxBoxClasses; ++c) {
@@ -1766,7 +1773,7 @@ int ibm_lbm_batch_init(const ibm_lbm_config* cfgs, int32_t n, void* d_workspace,
   b->n = n;
   b->s = static_cast<cudaStream_t>(stream);
   b->side = nullptr;
-  b->fork = b->join = nullptr;
+  b->fork0 = b->fork = b->join = nullptr;
   b->store = cfgs[0].pdf_storage;
   b->mdf = cfgs[0].mdf_iters;
   b->step = 0;
@@ -1797,6 +1804,7 @@ int ibm_lbm_batch_init(const ibm_lbm_config* cfgs, int32_t n, void* d_workspace,
     BATCH_TRY(cudaDeviceGetStreamPriorityRange(&lo_, &hi_));
     BATCH_TRY(cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, hi_));
   }
+  BATCH_TRY(cudaEventCreateWithFlags(&b->fork0, cudaEventDisableTiming));
   BATCH_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
   BATCH_TRY(cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming));
   int maxbox = 0;
