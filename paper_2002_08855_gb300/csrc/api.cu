@@ -1441,7 +1441,7 @@ constexpr int kMaxBoxClasses = 8;
 constexpr int kBatchWords = 96, kBarIbm = 0, kBarPairs = 32, kBatchStatus = 64;
 // polls (about 0.2 us each) before a persistent kernel's grid barrier gives up
 constexpr unsigned long long kDefaultBarrierLimit = 10000000ull;
-enum { BK_LBM, BK_EDGE, BK_WARP, BK_LANE, BK_PCLEAR, BK_PINS, BK_PSEARCH, BK_PFORCE, BK_CW0,
+enum { BK_LBM, BK_EDGE, BK_WARP, BK_LANE, BK_HALF, BK_PCLEAR, BK_PINS, BK_PSEARCH, BK_PFORCE, BK_CW0,
        BK_COUNT = BK_CW0 + kMaxBoxClasses };
 
 // Box-size classes of a batch: the distinct particle-box sizes of the members with
@@ -1484,6 +1484,7 @@ unsigned member_blocks(int type, const Derived& d, const ibm_lbm_config& c, int 
     case BK_EDGE: return lbm_edge_blocks(d.g, 2);
     case BK_WARP: return np > 0 ? ibm_warp_blocks(np) : 0;
     case BK_LANE: return np > 0 ? ibm_lane_blocks(np) : 0;
+    case BK_HALF: return np > 0 ? ibm_half_blocks(np) : 0;
     case BK_PCLEAR: {
       if (np == 0) return 0;
       PairArgs a{};
@@ -1669,7 +1670,7 @@ int enqueue_batch_step(ibm_lbm_batch* b, int parity, int have_prev, int* nk, cud
       if ((rc = phase(false, m)) != IBMLBM_OK) return rc;
       if ((rc = phase(true, m)) != IBMLBM_OK) return rc;
     }
-    CUDA_TRY(launch_ibm_forces_fused(fuse(b, BK_LANE, ia), B[BK_LANE], s));
+    CUDA_TRY(launch_ibm_forces_fused(fuse(b, BK_HALF, ia), B[BK_HALF], s));
     ++k;
     // contact forces, particle update and regeneration beside the collision (as in a
     // single run)

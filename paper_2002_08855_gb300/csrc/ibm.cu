@@ -1227,12 +1227,12 @@ __global__ void __launch_bounds__(256, (FUSED || SC == 0) ? 3 : 5) ibm_forces2_k
   IBMLBM_BIND(FUSED, IbmArgs, A, A0, FU, blk);
   if constexpr (FUSED) {  // members differ in box size: run the code compiled for this one
     switch (A.box) {
-      case 14: forces2_body<14>(A, blk); return;
-      case 16: forces2_body<16>(A, blk); return;
-      case 18: forces2_body<18>(A, blk); return;
-      case 20: forces2_body<20>(A, blk); return;
-      case 22: forces2_body<22>(A, blk); return;
-      default: forces2_body<0>(A, blk); return;
+      case 14: forces2_body<14, 16>(A, blk); return;
+      case 16: forces2_body<16, 16>(A, blk); return;
+      case 18: forces2_body<18, 16>(A, blk); return;
+      case 20: forces2_body<20, 16>(A, blk); return;
+      case 22: forces2_body<22, 16>(A, blk); return;
+      default: forces2_body<0, 16>(A, blk); return;
     }
   }
   forces2_body<SC, 16>(A, blk);  // a single run: half-warp per particle
@@ -1557,6 +1557,7 @@ cudaError_t launch_regen(const RegenArgs& A, int init, cudaStream_t s) {
 // blocks of each 2D IBM kernel for one run of np particles
 unsigned ibm_warp_blocks(int np) { return (unsigned)((np + kIbmWarps - 1) / kIbmWarps); }
 unsigned ibm_lane_blocks(int np) { return (unsigned)(((long long)np * 32 + 255) / 256); }
+unsigned ibm_half_blocks(int np) { return (unsigned)(((long long)np * 16 + 255) / 256); }
 
 cudaError_t launch_ibm_interp_fused(const Fuse& F, unsigned blocks, size_t smem, int m, int parity,
                                     int store, cudaStream_t s) {

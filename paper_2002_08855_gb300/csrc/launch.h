@@ -55,6 +55,7 @@ cudaError_t launch_lbm_step_fused(const Fuse& F, unsigned blocks, const Fuse& FE
 size_t ibm_box2_smem(int box);
 unsigned ibm_warp_blocks(int np);
 unsigned ibm_lane_blocks(int np);
+unsigned ibm_half_blocks(int np);  // interior sums: a half-warp per particle
 cudaError_t launch_ibm_interp_fused(const Fuse& F, unsigned blocks, size_t smem, int m, int parity,
                                     int store, cudaStream_t s);
 cudaError_t launch_ibm_spread_fused(const Fuse& F, unsigned blocks, size_t smem, cudaStream_t s);
