@@ -92,6 +92,11 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
+// 16 bytes, or 16 zero bytes when pred is false
+__device__ __forceinline__ void cp_async16z(void* dst, const void* src, bool pred) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(pred ? 16 : 0) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // floats of shared memory per warp: the box [S][P] float2, then
@@ -171,6 +176,7 @@ __device__ __forceinline__ void interp2_body(const IbmArgs& A, int m, unsigned b
   }
   const int ox = fix_anchor(A.Xcf[(long long)i * 2 + 0]) - A.rcell - 2;
   const int oy = fix_anchor(A.Xcf[(long long)i * 2 + 1]) - A.rcell - 2;
+  int ash = 0;  // MODE 1: offset of the f_IB rows in the buffer (aux[r P + c + ash] is node (ox + c, oy + r))
   if (MODE == 0) {
     // Only the nodes within R + 2 sqrt(2) of the centre are needed: every support node
     // of a point on the circle (at most 2 nodes from it along each axis) and the
@@ -219,12 +225,32 @@ __device__ __forceinline__ void interp2_body(const IbmArgs& A, int m, unsigned b
   } else {
     for (int q = lane; q < cells / 2; q += 32) cp_async16(box + 2 * q, ub + 2 * q);
     const float2* fib2 = reinterpret_cast<const float2*>(A.fib);
-    for (int t = lane; t < S * S; t += 32) {
-      const int r = t / S, c = t - r * S;
-      int gx, gy;
-      const bool ok = box_node(A.g, ox, oy, r, c, gx, gy);
-      const long long n = ok ? (long long)gx + (long long)A.g.nx * gy : 0;
-      cp_async8(aux + r * P + c, fib2 + n, ok && IBMLBM_CHK(n, A.g.N));
+    // Where the box's rows lie inside the domain along x (and rows hold an even number
+    // of nodes, so that a pair of nodes starting at an even node is 16-byte aligned),
+    // f_IB comes two nodes per copy; a box starting at an odd node keeps its rows one
+    // cell on in the buffer (ash), the spare cells of the row pitch taking the extra node.
+    if (A.g.nx % 2 == 0 && P >= S + 2 && ox >= 0 && ox + S <= A.g.nx - 1) {
+      ash = ox & 1;
+      const int base = ox - ash, nch = (S + ash + 1) / 2;
+      for (int t = lane; t < S * nch; t += 32) {
+        const int r = t / nch, j = t - r * nch;
+        int gy = oy + r;
+        bool ok = true;
+        if (gy < 0 || gy >= A.g.ny) {
+          if (A.g.per[1]) gy = ((gy % A.g.ny) + A.g.ny) % A.g.ny;
+          else ok = false;
+        }
+        const long long n = ok ? (long long)(base + 2 * j) + (long long)A.g.nx * gy : 0;
+        cp_async16z(aux + r * P + 2 * j, fib2 + n, ok && IBMLBM_CHK(n + 1, A.g.N));
+      }
+    } else {
+      for (int t = lane; t < S * S; t += 32) {
+        const int r = t / S, c = t - r * S;
+        int gx, gy;
+        const bool ok = box_node(A.g, ox, oy, r, c, gx, gy);
+        const long long n = ok ? (long long)gx + (long long)A.g.nx * gy : 0;
+        cp_async8(aux + r * P + c, fib2 + n, ok && IBMLBM_CHK(n, A.g.N));
+      }
     }
     cp_async_wait_all();
     __syncwarp();
@@ -252,7 +278,7 @@ __device__ __forceinline__ void interp2_body(const IbmArgs& A, int m, unsigned b
         for (int sx = 0; sx < 4; ++sx) {
           float2 v = box[o + sx];
           if (MODE == 1) {
-            const float2 h = aux[o + sx];
+            const float2 h = aux[o + ash + sx];
             v.x += 0.5f * h.x;
             v.y += 0.5f * h.y;
           }
