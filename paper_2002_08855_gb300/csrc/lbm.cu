@@ -818,16 +818,80 @@ __global__ void __launch_bounds__(kLbmBlock, L::dim == 3 ? 7 : 10)
   step_tile_body<L, 1, ST, K>(A, spr, b - min(eblocks, q + 1));
 }
 
-// An odd step of a 2D batch in one launch: blocks [0, blocks) are the members' row
+// Flat tiles of a 2D batch member: block b takes the K kLbmBlock consecutive nodes from
+// b K kLbmBlock on (row-major), a thread its nodes threadIdx.x + k kLbmBlock, so every
+// load and store instruction of a warp covers consecutive nodes whatever the member's
+// row length: short rows leave no thread idle, and the block's copy of its member's
+// arguments serves K kLbmBlock nodes.  The even step is local everywhere; an odd step
+// leaves the face rows and row ends to the edge blocks and reads the other nodes' slots
+// at fixed offsets, as step_row_nodes does.
+constexpr int kFlatK32 = 4;  // nodes per thread, FP32 storage
+constexpr int kFlatK16 = 2;  // nodes per thread, 16-bit storages
+template <int ST>
+__host__ __device__ constexpr int flat_k() { return ST == STORE_F32 ? kFlatK32 : kFlatK16; }
+
+template <int PARITY, int ST, int K>
+__device__ __forceinline__ void step_flat_body(const LbmArgs& A, unsigned blk) {
+  using L = Lat<2>;
+  constexpr bool H = ST != STORE_F32;  // 16-bit storages collide the stored h = f / w
+  const Geo& g = A.g;
+  const long long n0 = (long long)blk * (K * kLbmBlock) + threadIdx.x;
+  const bool small = g.N < (1LL << 31);  // 32-bit division where it fits
+  float fa[K][L::Q], fv[K][3];
+  int xs[K], ys[K];
+  bool act[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const long long n = n0 + (long long)k * kLbmBlock;
+    act[k] = n < g.N;
+    xs[k] = ys[k] = 0;
+    if (!act[k]) continue;
+    if (small) {
+      const unsigned un = (unsigned)n, uy = un / (unsigned)g.nx;
+      ys[k] = (int)uy;
+      xs[k] = (int)(un - uy * (unsigned)g.nx);
+    } else {
+      ys[k] = (int)(n / g.nx);
+      xs[k] = (int)(n - (long long)ys[k] * g.nx);
+    }
+    if (PARITY == 1 && (xs[k] == 0 || xs[k] == g.nx - 1 || ys[k] == 0 || ys[k] == g.ny - 1)) {
+      act[k] = false;
+      continue;
+    }
+    load_pdfs<L, PARITY, ST, PARITY == 1, H>(g, A.f, xs[k], ys[k], 0, n, fa[k]);
+    ib_force<L>(A, ys[k], xs[k], n, fv[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (!act[k]) continue;
+    const long long n = n0 + (long long)k * kLbmBlock;
+    float F[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) F[c] = A.body[c] + fv[k][c];
+    if constexpr (H) collide_h<L>(fa[k], F, A.omega, A.kforce);
+    else collide<L>(fa[k], F, A.omega, A.kforce);
+    store_post<L, PARITY, ST, PARITY == 1, H>(g, A.f, xs[k], ys[k], 0, n, fa[k]);
+    ib_force_clear<L>(A, n, fv[k]);
+  }
+}
+
+// the even step of a 2D batch (or an odd step with no edge blocks), flat tiles
+template <int PARITY, int ST>
+__global__ void __launch_bounds__(kLbmBlock) lbm_step_flat_kernel(Fuse F) {
+  unsigned blk;
+  const LbmArgs A = fused_args<LbmArgs>(F, blockIdx.x, blk);
+  step_flat_body<PARITY, ST, flat_k<ST>()>(A, blk);
+}
+
+// An odd step of a 2D batch in one launch: blocks [0, blocks) are the members' flat
 // tiles, the rest their face rows and row ends.  No node of one set reads or writes a
 // slot of the other (an AA step swaps each node's own slots), so both run together.
 template <int ST>
-__global__ void __launch_bounds__(kLbmBlock, 10) lbm_step_odd_batch_kernel(Fuse F, unsigned blocks, Fuse FE) {
+__global__ void __launch_bounds__(kLbmBlock) lbm_step_odd_batch_kernel(Fuse F, unsigned blocks, Fuse FE) {
   unsigned blk;
   if (blockIdx.x < blocks) {
     const LbmArgs A = fused_args<LbmArgs>(F, blockIdx.x, blk);
-    constexpr int K = ST == STORE_F32 ? 1 : 2;
-    step_tile_body<Lat<2>, 1, ST, K>(A, (A.g.nx + K * kLbmBlock - 1) / (K * kLbmBlock), blk);
+    step_flat_body<1, ST, flat_k<ST>()>(A, blk);
   } else {
     const LbmArgs A = fused_args<LbmArgs>(FE, blockIdx.x - blocks, blk);
     long long nface, nends;
@@ -1055,10 +1119,10 @@ static dim3 lbm_grid(const Geo& g, int& cpr) {
 template <int ST>
 constexpr int step_k() { return ST == STORE_F32 ? 1 : 2; }
 
-// blocks of lbm_step_kernel (2D) and of the odd-step edge kernel for one run
+// blocks of a batch member's flat tiles (2D) and of its odd-step edge blocks
 unsigned lbm_step_blocks(const Geo& g, int store) {
-  const int K = store == STORE_F32 ? 1 : 2;
-  return (unsigned)((long long)((g.nx + K * kLbmBlock - 1) / (K * kLbmBlock)) * g.rows);
+  const int K = store == STORE_F32 ? flat_k<STORE_F32>() : flat_k<STORE_F16>();
+  return (unsigned)((g.N + K * kLbmBlock - 1) / (K * kLbmBlock));
 }
 unsigned lbm_edge_blocks(const Geo& g, int D) {
   long long nface, nends;
@@ -1103,13 +1167,12 @@ static void launch_step_main(const LbmArgs& A, cudaStream_t s) {
 // fused over the members of a 2D batch (FP32 or FP16 storage, one for all members)
 cudaError_t launch_lbm_step_fused(const Fuse& F, unsigned blocks, const Fuse& FE, unsigned eblocks,
                                   int store, int parity, cudaStream_t s) {
-  const LbmArgs none{};
 #define IBMLBM_STEPF(P, ST)                                                                        \
   do {                                                                                               \
     if (P == 1 && eblocks)                                                                           \
       lbm_step_odd_batch_kernel<ST><<<blocks + eblocks, kLbmBlock, 0, s>>>(F, blocks, FE);           \
     else                                                                                             \
-      lbm_step_kernel<Lat<2>, P, ST, step_k<ST>(), true><<<blocks, kLbmBlock, 0, s>>>(none, 0, F);  \
+      lbm_step_flat_kernel<P, ST><<<blocks, kLbmBlock, 0, s>>>(F);                                   \
   } while (0)
   if (store == STORE_F32) {
     if (parity == 0) IBMLBM_STEPF(0, STORE_F32); else IBMLBM_STEPF(1, STORE_F32);
