@@ -818,10 +818,10 @@ __global__ void __launch_bounds__(kLbmBlock, L::dim == 3 ? 7 : 10)
   step_tile_body<L, 1, ST, K>(A, spr, b - min(eblocks, q + 1));
 }
 
-// Flat tiles of a 2D batch member: block b takes the K kLbmBlock consecutive nodes from
-// b K kLbmBlock on (row-major), a thread its nodes threadIdx.x + k kLbmBlock, so every
-// load and store instruction of a warp covers consecutive nodes whatever the member's
-// row length: short rows leave no thread idle, and the block's copy of its member's
+// Flat tiles: block b takes the K kLbmBlock consecutive nodes from b K kLbmBlock on
+// (row-major), a thread its nodes threadIdx.x + k kLbmBlock, so every load and store
+// instruction of a warp covers consecutive nodes whatever the row length: a batch
+// member's short rows leave no thread idle, and the block's copy of its member's
 // arguments serves K kLbmBlock nodes.  The even step is local everywhere; an odd step
 // leaves the face rows and row ends to the edge blocks and reads the other nodes' slots
 // at fixed offsets, as step_row_nodes does.
@@ -830,36 +830,46 @@ constexpr int kFlatK16 = 2;  // nodes per thread, 16-bit storages
 template <int ST>
 __host__ __device__ constexpr int flat_k() { return ST == STORE_F32 ? kFlatK32 : kFlatK16; }
 
-template <int PARITY, int ST, int K>
+template <class L, int PARITY, int ST, int K>
 __device__ __forceinline__ void step_flat_body(const LbmArgs& A, unsigned blk) {
-  using L = Lat<2>;
   constexpr bool H = ST != STORE_F32;  // 16-bit storages collide the stored h = f / w
   const Geo& g = A.g;
   const long long n0 = (long long)blk * (K * kLbmBlock) + threadIdx.x;
   const bool small = g.N < (1LL << 31);  // 32-bit division where it fits
   float fa[K][L::Q], fv[K][3];
-  int xs[K], ys[K];
+  int xs[K], ys[K], zs[K];
+  long long rows[K];
   bool act[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const long long n = n0 + (long long)k * kLbmBlock;
     act[k] = n < g.N;
-    xs[k] = ys[k] = 0;
+    xs[k] = ys[k] = zs[k] = 0;
+    rows[k] = 0;
     if (!act[k]) continue;
     if (small) {
-      const unsigned un = (unsigned)n, uy = un / (unsigned)g.nx;
-      ys[k] = (int)uy;
-      xs[k] = (int)(un - uy * (unsigned)g.nx);
+      const unsigned un = (unsigned)n, ur = un / (unsigned)g.nx;
+      xs[k] = (int)(un - ur * (unsigned)g.nx);
+      rows[k] = ur;
+      if (L::dim == 2) {
+        ys[k] = (int)ur;
+      } else {
+        const unsigned uz = ur / (unsigned)g.ny;
+        zs[k] = (int)uz;
+        ys[k] = (int)(ur - uz * (unsigned)g.ny);
+      }
     } else {
-      ys[k] = (int)(n / g.nx);
-      xs[k] = (int)(n - (long long)ys[k] * g.nx);
+      rows[k] = n / g.nx;
+      xs[k] = (int)(n - rows[k] * g.nx);
+      ys[k] = (int)(rows[k] % g.ny);
+      zs[k] = (int)(rows[k] / g.ny);
     }
-    if (PARITY == 1 && (xs[k] == 0 || xs[k] == g.nx - 1 || ys[k] == 0 || ys[k] == g.ny - 1)) {
+    if (PARITY == 1 && (xs[k] == 0 || xs[k] == g.nx - 1 || odd_edge_row<L>(g, ys[k], zs[k]))) {
       act[k] = false;
       continue;
     }
-    load_pdfs<L, PARITY, ST, PARITY == 1, H>(g, A.f, xs[k], ys[k], 0, n, fa[k]);
-    ib_force<L>(A, ys[k], xs[k], n, fv[k]);
+    load_pdfs<L, PARITY, ST, PARITY == 1, H>(g, A.f, xs[k], ys[k], zs[k], n, fa[k]);
+    ib_force<L>(A, rows[k], xs[k], n, fv[k]);
   }
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -870,7 +880,7 @@ __device__ __forceinline__ void step_flat_body(const LbmArgs& A, unsigned blk) {
     for (int c = 0; c < 3; ++c) F[c] = A.body[c] + fv[k][c];
     if constexpr (H) collide_h<L>(fa[k], F, A.omega, A.kforce);
     else collide<L>(fa[k], F, A.omega, A.kforce);
-    store_post<L, PARITY, ST, PARITY == 1, H>(g, A.f, xs[k], ys[k], 0, n, fa[k]);
+    store_post<L, PARITY, ST, PARITY == 1, H>(g, A.f, xs[k], ys[k], zs[k], n, fa[k]);
     ib_force_clear<L>(A, n, fv[k]);
   }
 }
@@ -880,7 +890,33 @@ template <int PARITY, int ST>
 __global__ void __launch_bounds__(kLbmBlock) lbm_step_flat_kernel(Fuse F) {
   unsigned blk;
   const LbmArgs A = fused_args<LbmArgs>(F, blockIdx.x, blk);
-  step_flat_body<PARITY, ST, flat_k<ST>()>(A, blk);
+  step_flat_body<Lat<2>, PARITY, ST, flat_k<ST>()>(A, blk);
+}
+
+// A single 2D run's FP32 step on flat tiles, kFlatRun nodes a thread.  Measured on the
+// 2048 x 4096 cavity (ms per collide-stream launch, mean of both parities): 0.1033 with
+// particles and 0.0925 without, against 0.1094 and 0.1004 on the row tiles (K = 2: 0.1045,
+// 0.0960); bit for bit the same nodes.  3D keeps the row tiles: with 19 directions four
+// (two) nodes a thread take 168 (119) registers, and the 384 x 384 x 768 cavity's
+// collide-stream measured 4.16 (3.75) against 3.39 ms.
+constexpr int kFlatRun = 4;
+
+template <class L, int PARITY, int K>
+__global__ void __launch_bounds__(kLbmBlock) lbm_step_flat1_kernel(LbmArgs A) {
+  step_flat_body<L, PARITY, STORE_F32, K>(A, blockIdx.x);
+}
+
+// the odd step of one run on flat tiles, with the edge blocks spread through the grid
+// as in lbm_step_odd_kernel
+template <class L, int K>
+__global__ void __launch_bounds__(kLbmBlock) lbm_step_odd_flat1_kernel(LbmArgs A, unsigned eblocks, unsigned stride,
+                                                                       long long nface, long long nends) {
+  const unsigned b = blockIdx.x, q = b / stride;
+  if (b - q * stride == 0 && q < eblocks) {
+    step_edge_body<L, STORE_F32>(A, nface, nends, q);
+    return;
+  }
+  step_flat_body<L, 1, STORE_F32, K>(A, b - min(eblocks, q + 1));
 }
 
 // An odd step of a 2D batch in one launch: blocks [0, blocks) are the members' flat
@@ -891,7 +927,7 @@ __global__ void __launch_bounds__(kLbmBlock) lbm_step_odd_batch_kernel(Fuse F, u
   unsigned blk;
   if (blockIdx.x < blocks) {
     const LbmArgs A = fused_args<LbmArgs>(F, blockIdx.x, blk);
-    step_flat_body<1, ST, flat_k<ST>()>(A, blk);
+    step_flat_body<Lat<2>, 1, ST, flat_k<ST>()>(A, blk);
   } else {
     const LbmArgs A = fused_args<LbmArgs>(FE, blockIdx.x - blocks, blk);
     long long nface, nends;
@@ -1282,6 +1318,21 @@ int lbm_step_launches(const Geo&, int, int, int) { return 1; }
 
 template <class L, int PARITY, int ST>
 static void launch_step_one(const LbmArgs& A, cudaStream_t s) {
+  if constexpr (ST == STORE_F32 && L::dim == 2) {
+    constexpr int K = kFlatRun;
+    const unsigned main = (unsigned)((A.g.N + K * kLbmBlock - 1) / (K * kLbmBlock));
+    if (PARITY == 1) {
+      long long nface, nends;
+      edge_counts(A.g, L::dim, nface, nends);
+      const long long total = nface * A.g.nx + nends;
+      const unsigned eb = (unsigned)((total + kLbmBlock - 1) / kLbmBlock);
+      const unsigned stride = eb ? (main + eb) / eb : 1;
+      lbm_step_odd_flat1_kernel<L, K><<<main + eb, kLbmBlock, 0, s>>>(A, eb, stride, nface, nends);
+    } else {
+      lbm_step_flat1_kernel<L, 0, K><<<main, kLbmBlock, 0, s>>>(A);
+    }
+    return;
+  }
   if (PARITY == 1 && !use_vec<L, ST>(A.g)) {
     long long nface, nends;
     edge_counts(A.g, L::dim, nface, nends);
