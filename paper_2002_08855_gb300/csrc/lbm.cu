@@ -1169,11 +1169,11 @@ unsigned lbm_edge_blocks(const Geo& g, int D) {
 // The vector kernel serves D2Q9 with a 16-bit storage, eight nodes (one 16-byte
 // vector per direction) per thread, on rows whose length is a multiple of 8.
 // Measured on the 2048 x 4096 lattice without particles (GB300, ms per step): FP16
-// 0.0616 against 0.0773 for the row kernel.  Everything else keeps the row kernel,
-// which measured faster there: FP32 0.0985 (0.104 vector, K = 4), and in 3D at
-// 384 x 384 x 768 3.17 FP32 / 2.28 FP16 (3.74 / 3.51 vector, K = 4): with 19
-// directions the vectors and their addresses take 130 to 200 registers a thread and
-// leave too few warps to cover the memory latency.
+// 0.0616 against 0.0773 for the row kernel.  2D FP32 takes the flat tiles (0.0925;
+// the row kernel 0.0985, the vector kernel with K = 4 0.104); 3D keeps the row kernel,
+// which measured faster there at 384 x 384 x 768: 3.17 FP32 / 2.28 FP16 (3.74 / 3.51
+// vector, K = 4): with 19 directions the vectors and their addresses take 130 to 200
+// registers a thread and leave too few warps to cover the memory latency.
 constexpr int kVecK = 8;
 template <class L, int ST>
 constexpr bool vec_form() { return L::dim == 2 && ST != STORE_F32; }
@@ -1312,8 +1312,8 @@ cudaError_t launch_lbm_nee(const LbmArgs& A, int D, int parity, cudaStream_t s) 
   return cudaGetLastError();
 }
 
-// kernels launch_lbm_step launches: one (the vector kernel, the row kernel, or in an odd
-// step the row kernel with the edge nodes)
+// kernels launch_lbm_step launches: one (the vector kernel, the flat or row tiles, or in
+// an odd step the tiles with the edge nodes)
 int lbm_step_launches(const Geo&, int, int, int) { return 1; }
 
 template <class L, int PARITY, int ST>
