@@ -101,8 +101,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // floats of shared memory per warp: the box [S][P] float2, then
 //   interpolation, mode 1: f_IB of the box [S][P] float2;
-//   spreading: the point table, weights [32][17] and (F_x, F_y, first cell) [32] float4.
-constexpr int kTw = 17;  // 16 node weights per point (+1 against bank conflicts)
+//   spreading: the point table, weights [32][kTw] and (F_x, F_y, first cell) [32] float4.
+constexpr int kTw = 9;  // the 4 + 4 one-dimensional weights of a point (+1 against bank conflicts)
 __host__ __device__ inline int interp2_warp_floats(int mode, int S) {
   return 2 * S * box_pitch(S) * (mode == 0 ? 1 : 2);
 }
@@ -329,9 +329,10 @@ __global__ void __launch_bounds__(kIbmWarps * 32) ibm_interp2_kernel(IbmArgs A0,
 }
 
 // Spreading (Eq. 48) without shared-memory atomics.  The point's owner lane writes a
-// table row (the 16 products delta_x delta_y dV of its support, its force, the box
-// cell of its first support node).  Then the 16 lanes of each half-warp take one point
-// each, one support node per lane: half 0 point j, half 1 point j + H (H = half the
+// table row (the four weights delta_x and the four delta_y of its support, its force
+// dF_b dV, the box cell of its first support node).  Then the 16 lanes of each
+// half-warp take one point each, one support node per lane (its weight the product of
+// its column's and its row's): half 0 point j, half 1 point j + H (H = half the
 // group), about a diameter apart on the circle.  Where the two supports could share a
 // node (anchors at most 3 apart on both axes) the halves take turns.  So no two lanes
 // of an instruction touch one cell and plain read-add-write is exact.  Finally the warp
@@ -380,7 +381,10 @@ __device__ __forceinline__ void spread2_body(const IbmArgs& A, unsigned blk, int
       }
       float* row = tw + lane * kTw;
 #pragma unroll
-      for (int t = 0; t < 16; ++t) row[t] = wx[t & 3] * wy[t >> 2];
+      for (int t = 0; t < 4; ++t) {
+        row[t] = wx[t];
+        row[4 + t] = wy[t];
+      }
       tp[lane] = make_float4(fx, fy, __int_as_float(valid ? lby * P + lbx : 0), 0.0f);
     }
     // the two supports of a pass could share a node: anchors at most 3 apart on both axes
@@ -397,7 +401,7 @@ __device__ __forceinline__ void spread2_body(const IbmArgs& A, unsigned blk, int
       float w = 0.0f;
       if (act) {
         pd = tp[p];
-        w = tw[p * kTw + (lane & 15)];
+        w = tw[p * kTw + sx] * tw[p * kTw + 4 + sy];
       }
       const int cell = __float_as_int(pd.z) + sy * P + sx;
       if ((cmask >> j) & 1u) {
