@@ -387,7 +387,8 @@ int64_t ibm_lbm_batch_launch_count(const ibm_lbm_batch* b);
 
 /* Tile shapes of a batch's fused collide-stream launch (Eq. 1, 4-8; the work items are
  * (member, tile) pairs).  Shape 0: a block of 128 threads takes 128 K consecutive nodes
- * of one row (K = 1 for FP32, 2 for FP16).  Shapes >= 1: the rows of each member are
+ * of a member in row-major order, across row ends, thread t its nodes t + 128 k
+ * (K = 4 for FP32, 2 for FP16).  Shapes >= 1: the rows of each member are
  * cut into segments of 32 K nodes, one per warp, and a block takes W consecutive
  * segments (a tile can span several short rows); a persistent shape launches as many
  * blocks as the GPU holds at once and walks the tiles with a grid stride, the others

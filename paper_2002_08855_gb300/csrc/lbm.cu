@@ -1219,9 +1219,10 @@ cudaError_t launch_lbm_step_fused(const Fuse& F, unsigned blocks, const Fuse& FE
   return cudaGetLastError();
 }
 
-// Tile shapes of a batch's fused lbm_step: shape 0 is the row-tile kernel above (K = 1
-// for FP32, 2 for FP16, kLbmBlock threads), shapes 1.. are warp tiles (K nodes per
-// thread, W warps per block, persistent grid or one block per tile).
+// Tile shapes of a batch's fused lbm_step: shape 0 is the flat-tile kernel above
+// (flat_k nodes per thread: 4 for FP32, 2 for FP16; kLbmBlock threads), shapes 1.. are
+// warp tiles (K nodes per thread, W warps per block, persistent grid or one block per
+// tile).
 struct TileShape {
   int k, w, persist;
 };
@@ -1233,7 +1234,7 @@ int tile_shape_count() { return kTileShapeCount; }
 
 void tile_shape(int s, int store, int* k, int* w, int* persist) {
   const TileShape& t = kTileShapes[s];
-  *k = s == 0 ? (store == STORE_F32 ? 1 : 2) : t.k;
+  *k = s == 0 ? (store == STORE_F32 ? flat_k<STORE_F32>() : flat_k<STORE_F16>()) : t.k;
   *w = s == 0 ? kLbmBlock / 32 : t.w;
   *persist = t.persist;
 }

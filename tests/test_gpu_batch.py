@@ -116,8 +116,9 @@ def _flow_members(storage):
 
 @pytest.mark.parametrize("storage", [0, 1])
 def test_tile_shapes_update_every_node_identically(storage):
-    """Every collide-stream tile shape (row tiles, warp tiles of 32 K nodes, W warps per
-    block, persistent or not) gives the same PDFs bit for bit, over both AA parities."""
+    """Every collide-stream tile shape (flat tiles of K x 128 consecutive nodes, warp
+    tiles of 32 K nodes, W warps per block, persistent or not) gives the same PDFs bit
+    for bit, over both AA parities."""
     require_gpu()
     from paper_2002_08855_gb300.binding import Batch, tile_shapes
 
