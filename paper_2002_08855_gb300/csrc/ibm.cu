@@ -1253,8 +1253,12 @@ __device__ __forceinline__ void forces2_body(const IbmArgs& A, unsigned blk) {
   forces_finish<2, LP>(A, i, lane, P, L, valid);
 }
 
+// Blocks per SM the registers must allow: a single run's box sizes 16 and 22 five (48
+// registers), its general box three; the fused batch kernel, which holds every box
+// size's body, four (64 registers, a little spilled: 0.800 -> 0.794 ms per 256-cavity
+// step against three)
 template <int SC, bool FUSED>
-__global__ void __launch_bounds__(256, (FUSED || SC == 0) ? 3 : 5) ibm_forces2_kernel(IbmArgs A0, Fuse FU) {
+__global__ void __launch_bounds__(256, FUSED ? 4 : (SC == 0 ? 3 : 5)) ibm_forces2_kernel(IbmArgs A0, Fuse FU) {
   pdl_enter();
   IBMLBM_BIND(FUSED, IbmArgs, A, A0, FU, blk);
   if constexpr (FUSED) {  // members differ in box size: run the code compiled for this one
