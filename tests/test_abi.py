@@ -151,3 +151,16 @@ def test_extrapolation_boundary_configurations_are_checked(lib, changes):
     with pytest.raises(binding.IbmLbmError) as e:
         binding.workspace_size(w)
     assert "INVALID_ARG" in str(e.value)
+
+
+def test_tile_shapes_reported_host_only(lib):
+    """Shape 0 of the batch's collide-stream launch is the flat tiles (128 threads, four
+    nodes a thread for FP32, two for the 16-bit storages); shapes 1.. are the warp tiles
+    (K, W, persistent), the same for both storages."""
+    s32, s16 = binding.tile_shapes(0), binding.tile_shapes(1)
+    assert len(s32) == len(s16) == lib.ibm_lbm_tile_shape_count() >= 2
+    assert s32[0] == (4, 4, 0) and s16[0] == (2, 4, 0)
+    assert s32[1:] == s16[1:]
+    assert all(k in (1, 2) and w in (4, 8) and p in (0, 1) for k, w, p in s32[1:])
+    with pytest.raises(binding.IbmLbmError):
+        binding.tile_shapes(3)  # no such storage
